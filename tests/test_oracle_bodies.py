@@ -1,0 +1,128 @@
+"""Pins for the oracle's work bodies: closed forms, invariants, and special
+cases that reduce to library routines (numpy, math.fsum).  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_01212_gb300 import synth
+
+
+def test_add_closed_forms(oracle_lib):
+    o = oracle_lib
+    n = 10007
+    a = np.arange(n, dtype=np.int32)
+    assert np.all(o.add_i32(a, -a) == 0)
+    assert np.all(o.add_i32(a, (n - 1 - a).astype(np.int32)) == n - 1)
+    # operand order matters for neither side, but a dropped or shifted operand does
+    b = np.arange(n, dtype=np.int32) * 3
+    assert np.array_equal(o.add_i32(a, b), (np.arange(n) * 4).astype(np.int32))
+
+
+def test_add_wraps_mod_2_32(oracle_lib):
+    o = oracle_lib
+    a = np.array([2**31 - 1, -(2**31), -1, 2**31 - 1], dtype=np.int32)
+    b = np.array([1, -1, 1, 2**31 - 1], dtype=np.int32)
+    assert o.add_i32(a, b).tolist() == [-(2**31), 2**31 - 1, 0, -2]
+
+
+def test_add_matches_python_integers_mod_2_32(oracle_lib):
+    a = synth.int32_uniform(1, 1, 5000, -(2**31), 2**31 - 1)
+    b = synth.int32_uniform(1, 2, 5000, -(2**31), 2**31 - 1)
+    got = oracle_lib.add_i32(a, b)
+    want = [((int(x) + int(y) + 2**31) % 2**32) - 2**31 for x, y in zip(a, b)]
+    assert got.tolist() == want
+
+
+def test_copy_identity(oracle_lib):
+    x = synth.int32_uniform(2, 1, 4099, -(2**31), 2**31 - 1)
+    assert np.array_equal(oracle_lib.copy_i32(x), x)
+    assert oracle_lib.copy_i32(np.zeros(0, np.int32)).size == 0
+
+
+def test_hist_closed_forms(oracle_lib):
+    o = oracle_lib
+    n = 256 * 41
+    x = (np.arange(n) % 256).astype(np.uint8)
+    assert np.all(o.hist_u8(x) == 41)
+    h = o.hist_u8(np.full(1000, 7, np.uint8))
+    assert h[7] == 1000 and h.sum() == 1000
+    # value v appears v+1 times: an off-by-one bin index cannot pass
+    x = np.concatenate([np.full(v + 1, v, np.uint8) for v in range(256)])
+    x = x[synth.permutation(3, 1, x.size)]
+    assert np.array_equal(o.hist_u8(x), np.arange(1, 257))
+    assert np.all(o.hist_u8(np.zeros(0, np.uint8)) == 0)
+
+
+def test_hist_matches_bincount(oracle_lib):
+    x = synth.bytes_uniform(4, 1, (1 << 20) + 13)
+    h = oracle_lib.hist_u8(x)
+    assert np.array_equal(h, np.bincount(x, minlength=256))
+    assert h.sum() == x.size
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 8, 9, 1000, 65536, (1 << 20) + 3])
+def test_sum_arange_exact(oracle_lib, n):
+    x = np.arange(n, dtype=np.float32)   # exact in binary32 below 2^24
+    assert oracle_lib.sum_f32(x) == n * (n - 1) / 2
+
+
+def test_sum_periodic_closed_form(oracle_lib):
+    n = 100003
+    x = ((np.arange(n) % 7) - 3).astype(np.float32)
+    full, rem = divmod(n, 7)
+    want = full * 0 + sum(r - 3 for r in range(rem))
+    assert oracle_lib.sum_f32(x) == want
+
+
+def test_sum_within_bound_of_correctly_rounded(oracle_lib):
+    x = synth.normal_f32(5, 1, (1 << 20) + 5)
+    s = oracle_lib.sum_f32(x)
+    exact = math.fsum(float(v) for v in x)
+    bound = 21 * 2.0**-53 * float(np.abs(x.astype(np.float64)).sum())
+    assert abs(s - exact) <= bound
+    assert oracle_lib.abs_sum_f32(x) == pytest.approx(float(np.abs(x.astype(np.float64)).sum()), rel=1e-12)
+
+
+def test_sum_sign_matters(oracle_lib):
+    x = np.array([1.0, -2.0, 3.0, -4.0, 5.0], dtype=np.float32)
+    assert oracle_lib.sum_f32(x) == 3.0
+    assert oracle_lib.abs_sum_f32(x) == 15.0
+
+
+def _tiles(t):
+    return np.zeros((t, 64, 64), np.float32)
+
+
+def test_gemm_identity_and_ones(oracle_lib):
+    o = oracle_lib
+    B = synth.normal_f32(6, 1, 3 * 4096).reshape(3, 64, 64)
+    I = np.broadcast_to(np.eye(64, dtype=np.float32), (3, 64, 64)).copy()
+    assert np.array_equal(o.gemm64_f32(I, B), B.astype(np.float64))
+    ones = np.ones((2, 64, 64), np.float32)
+    assert np.all(o.gemm64_f32(ones, ones) == 64.0)
+
+
+def test_gemm_diag_scales_rows(oracle_lib):
+    d = np.arange(1, 65, dtype=np.float32)
+    A = np.diag(d)[None].astype(np.float32)
+    B = synth.int32_uniform(7, 1, 4096, -50, 50).astype(np.float32).reshape(1, 64, 64)
+    assert np.array_equal(oracle_lib.gemm64_f32(A, B)[0], d[:, None].astype(np.float64) * B[0])
+
+
+def test_gemm_integer_matrices_match_numpy_exactly(oracle_lib):
+    # non-symmetric integer tiles: a transposed operand or swapped index fails
+    A = synth.int32_uniform(8, 1, 4 * 4096, -100, 100).reshape(4, 64, 64)
+    B = synth.int32_uniform(8, 2, 4 * 4096, -100, 100).reshape(4, 64, 64)
+    C = oracle_lib.gemm64_f32(A.astype(np.float32), B.astype(np.float32))
+    want = np.matmul(A.astype(np.int64), B.astype(np.int64))
+    assert np.array_equal(C, want.astype(np.float64))
+
+
+def test_gemm_abs_bound(oracle_lib):
+    A = synth.normal_f32(9, 1, 4096).reshape(1, 64, 64)
+    B = synth.normal_f32(9, 2, 4096).reshape(1, 64, 64)
+    bound = oracle_lib.gemm64_abs_bound(A, B)
+    want = np.abs(A[0].astype(np.float64))[:, :, None] * np.abs(B[0].astype(np.float64))[None, :, :]
+    assert np.allclose(bound[0], want.sum(axis=1), rtol=1e-13, atol=0)
+    assert np.all(bound >= np.abs(oracle_lib.gemm64_f32(A, B)))
