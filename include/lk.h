@@ -1,0 +1,288 @@
+/*
+ * lk.h -- LightKernel-GB300: persistent-thread work dispatch for one GPU.
+ *
+ * The method is Burgio, "Enabling predictable parallelism in single-GPU
+ * systems with persistent CUDA threads" (LightKernel, LK):
+ *   - Sec. II.C: one CUDA kernel is spawned once; it holds exactly one block
+ *     per SM, pinned at boot, and its threads spin-wait for work.
+ *   - Sec. I / II.A: the host sends a persistent thread "a descriptor of the
+ *     work and a reference to the in/out data items", and software maps work
+ *     and data onto a chosen cluster of SMs.
+ *   - Sec. II.D, Table 1: per-SM dual mailboxes (to_GPU / from_GPU) carry
+ *     integer status codes between host and device.
+ *   - Sec. III: the life cycle Init -> {Copyin, Trigger, Wait, Copyout}* ->
+ *     Dispose.  lk_init = Init, lk_submit = Trigger, lk_wait / lk_poll =
+ *     Wait, lk_dispose = Dispose.  Copyin / Copyout stay with the caller.
+ *
+ * A "cluster" here is a caller-chosen set of SMs (one pinned CTA each); the
+ * paper's own case is one SM per cluster.  It is not a CUDA thread-block
+ * cluster.
+ *
+ * Threading: lk_submit may be called from many host threads at once (each
+ * cluster's mailbox is a multi-producer ring; FIFO order = the order in which
+ * submissions obtained their ring ticket).  lk_poll / lk_wait / lk_status may
+ * be called from any thread.  lk_init and lk_dispose must not race with other
+ * calls on the same context.
+ *
+ * Errors: every call returns an int status (LK_OK or a negative LK_E* code);
+ * nothing throws or aborts across this boundary.  lk_strerror names a code.
+ *
+ * Memory: the caller owns every in/out buffer (device memory, e.g. torch
+ * tensors).  A buffer passed to lk_submit must stay allocated and untouched
+ * by other writers until lk_poll / lk_wait has returned LK_OK for that
+ * handle.  Outputs are complete and visible to device work the host issues
+ * after that return.  The library owns its mailboxes, status words, execution
+ * log and the persistent kernel; lk_dispose releases them.
+ *
+ * While a context runs, its CTAs occupy their SMs: a device-wide synchronise
+ * (cudaDeviceSynchronize, torch.cuda.synchronize) blocks until the context is
+ * disposed or its idle lease runs out.  Wait on other streams only.
+ */
+#ifndef LK_H
+#define LK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define LK_OK         0   /* success / descriptor finished                  */
+#define LK_PENDING    1   /* lk_poll: descriptor not finished yet           */
+#define LK_EINVAL    -1   /* bad argument (range, alignment, op, size)      */
+#define LK_EAGAIN    -2   /* cluster mailbox ring full; retry later         */
+#define LK_ETIMEDOUT -3   /* wait / dispose deadline passed                 */
+#define LK_EDEVICE   -4   /* the persistent kernel reported an error, or a CUDA call failed */
+#define LK_ESTATE    -5   /* context not running (exited, disposed, lease expired) */
+#define LK_ENOMEM    -6   /* host or device allocation failed               */
+#define LK_EBUSY     -7   /* lk_dispose: kernel still running after the abort; context kept */
+
+/* ---- from_GPU status codes (Table 1, Sec. II.D) ------------------------ */
+#define LK_ST_INIT      0  /* THREAD_INIT: booted, nothing run yet           */
+#define LK_ST_FINISHED  1  /* THREAD_FINISHED: last descriptor completed     */
+#define LK_ST_WORKING   2  /* THREAD_WORKING: a descriptor is running        */
+#define LK_ST_NOP       4  /* THREAD_NOP: idle acknowledgement (one-deep mailbox) */
+/* build-only statuses beyond Table 1 */
+#define LK_ST_EXITED    8  /* the cluster's CTAs returned after EXIT         */
+#define LK_ST_ERROR    32  /* the cluster stopped on a device-side error     */
+
+/* ---- to_GPU command codes (Table 1, Sec. II.D) ------------------------- */
+#define LK_CMD_NOP   4     /* THREAD_NOP                                      */
+#define LK_CMD_EXIT  8     /* THREAD_EXIT: run everything posted before, then return */
+#define LK_CMD_WORK 16     /* THREAD_WORK: 16 + operation code               */
+
+/* ---- operations (the "work" a descriptor names) ----------------------- */
+#define LK_OP_NOP        0 /* no data; measures the dispatch path alone      */
+#define LK_OP_ADD_I32    1 /* out[i] = in0[i] + in1[i], int32, wraps mod 2^32; n elements */
+#define LK_OP_HIST_U8    2 /* out[v] = #{i : in0[i] == v}; n bytes in, 256 int32 bins out (overwritten) */
+#define LK_OP_SUM_F32    3 /* out[0] = sum of n float32 (fixed order for a given n and cluster size) */
+#define LK_OP_GEMM64_F32 4 /* n tiles: out[t] = in0[t] x in1[t], 64x64 row-major float32 tiles, FFMA */
+#define LK_OP_COPY_I32   5 /* out[i] = in0[i], int32; n elements             */
+#define LK_OP_COUNT      6
+
+/* ---- device-side error reasons (lk_device_error) ---------------------- */
+#define LK_DERR_NONE     0
+#define LK_DERR_LEASE    1 /* no work and no heartbeat for idle_lease_ns: kernel returned */
+#define LK_DERR_ABORT    2 /* host set the abort word                        */
+#define LK_DERR_BOOT     3 /* boot barrier did not complete in time          */
+#define LK_DERR_STALL    4 /* a CTA waited too long for its cluster master   */
+#define LK_DERR_BADDESC  5 /* descriptor failed the device-side check        */
+#define LK_DERR_STAGING  6 /* a shared-memory staging copy did not complete in time */
+
+typedef struct lk_ctx lk_ctx;   /* opaque; owned by the library */
+
+/* A handle names one submitted descriptor: (cluster << 48) | seq, seq >= 1
+ * its 1-based position in the cluster's FIFO.  0 is never a valid handle. */
+typedef uint64_t lk_handle;
+
+/* lk_init parameters.  Zero-initialise, then set what you need. */
+typedef struct {
+  int device;                  /* CUDA device ordinal                                   */
+  int num_clusters;            /* >= 1                                                  */
+  const int* sms_per_cluster;  /* [num_clusters], each >= 1, total <= SM count           */
+  const int* smids;            /* optional: the SM ids of cluster 0, then cluster 1, ... */
+                               /* (total entries); NULL = clusters are cut from the     */
+                               /* observed SM ids sorted ascending                      */
+  int threads_per_cta;         /* multiple of 32 in [64, 1024]; 0 -> 256                 */
+  int ring_depth;              /* descriptors queued per cluster, power of two; 0 -> 1024 */
+  uint64_t backoff_base_ns;    /* first __nanosleep of a spin back-off (0 = pure spin)   */
+  uint64_t backoff_cap_ns;     /* back-off ceiling; 0 -> 256 ns                          */
+  uint64_t idle_lease_ns;      /* the kernel returns after this long with no work and    */
+                               /* no heartbeat (lk_submit, lk_poll, lk_wait, lk_sync and */
+                               /* lk_heartbeat beat); 0 -> 10 s                          */
+  uint64_t boot_timeout_ns;    /* lk_init fails if the CTAs are not all up; 0 -> 10 s    */
+  uint32_t exec_log_cap;       /* execution-log records kept per CTA (ring); 0 = no log  */
+  uint32_t flags;              /* reserved, 0                                           */
+} lk_init_params;
+
+/* A work descriptor.  The in/out pointers travel beside it. */
+typedef struct {
+  uint32_t op;      /* LK_OP_*                                            */
+  uint32_t flags;   /* reserved, 0                                        */
+  uint64_t n;       /* elements (ADD/COPY: int32, SUM: float32, HIST: bytes, GEMM: tiles) */
+  uint64_t aux;     /* reserved, 0                                        */
+} lk_desc;
+
+/* One execution-log record: one CTA's share of one descriptor. */
+typedef struct {
+  uint64_t seq;        /* descriptor's position in its cluster's FIFO (1-based)    */
+  uint32_t cluster;
+  uint32_t rank;       /* the CTA's rank inside its cluster (0 = master)           */
+  uint32_t smid;       /* %smid read by the CTA when it wrote this record          */
+  uint32_t op;         /* the operation it ran                                     */
+  uint64_t order;      /* how many descriptors this CTA ran before this one        */
+  uint64_t t_pick_ns;  /* %globaltimer: master took the descriptor from the ring   */
+  uint64_t t_start_ns; /* %globaltimer: this CTA started its share                 */
+  uint64_t t_end_ns;   /* %globaltimer: this CTA finished its share                */
+  uint64_t t_done_ns;  /* %globaltimer of the completion store if this CTA was the */
+                       /* last to arrive, else 0                                   */
+} lk_exec_rec;         /* 64 bytes */
+
+/* Init (Sec. III): allocate the mailboxes, launch the persistent kernel (one
+ * CTA per SM, cooperative launch, enough shared memory that no second CTA
+ * fits), and wait until every CTA has read its %smid and joined its cluster.
+ * On success *out owns a running context.
+ * Errors: LK_EINVAL (partition, sizes), LK_ENOMEM, LK_EDEVICE (CUDA failure,
+ * launch refused), LK_ETIMEDOUT (boot did not finish; everything is freed). */
+int lk_init(lk_ctx** out, const lk_init_params* p);
+
+/* Trigger (Sec. III): post descriptor d with its data items to `cluster`.
+ *   in[0..n_in-1]: device pointers to the inputs (ADD: 2, HIST/SUM/COPY: 1,
+ *   GEMM: 2 = A tiles, B tiles, NOP: 0); out: device pointer to the output.
+ *   Every non-null pointer must be 16-byte aligned.  No CUDA call is made:
+ *   the descriptor reaches the device through the mailbox ring only.
+ * On success *h names the descriptor.
+ * Errors: LK_EINVAL (cluster, op, n_in, alignment, n too large),
+ * LK_EAGAIN (ring full: nothing was posted), LK_ESTATE (context not running). */
+int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in, int n_in,
+              void* out, lk_handle* h);
+
+/* Wait (Sec. III), non-blocking: LK_OK if h finished, LK_PENDING if not.
+ * Errors: LK_EINVAL (bad handle), LK_EDEVICE (the cluster stopped on a device
+ * error before finishing h), LK_ESTATE (context gone before h finished). */
+int lk_poll(lk_ctx* ctx, lk_handle h);
+
+/* Wait (Sec. III), blocking: spin until h finished or timeout_ns elapsed.
+ * Returns LK_OK, LK_ETIMEDOUT, or lk_poll's errors. */
+int lk_wait(lk_ctx* ctx, lk_handle h, uint64_t timeout_ns);
+
+/* Refresh the idle lease without posting work.  LK_OK or LK_EINVAL. */
+int lk_heartbeat(lk_ctx* ctx);
+
+/* Wait until every descriptor submitted so far, on every cluster, finished.
+ * Returns LK_OK, LK_ETIMEDOUT, or lk_poll's errors. */
+int lk_sync(lk_ctx* ctx, uint64_t timeout_ns);
+
+/* Dispose (Sec. III): post EXIT (THREAD_EXIT, Table 1) behind everything
+ * already queued, wait for the kernel to return, free everything.  If the
+ * kernel has not returned after timeout_ns, set the abort word (every device
+ * wait checks it) and wait up to timeout_ns + 2 s more.
+ * Returns LK_OK (freed), LK_EDEVICE (kernel had reported an error; freed),
+ * LK_ETIMEDOUT (kernel returned only after the abort; freed), LK_EBUSY (the
+ * kernel is still running: nothing is freed under it and ctx stays valid, so
+ * lk_dispose may be called again), LK_EINVAL (null ctx). */
+int lk_dispose(lk_ctx* ctx, uint64_t timeout_ns);
+
+/* The SM ids of `cluster`'s CTAs by rank (Sec. II.C: blocks are pinned to
+ * SMs at boot).  Writes min(size, cap) ids; returns the cluster size, or
+ * LK_EINVAL. */
+int lk_cluster_info(lk_ctx* ctx, int cluster, int* smids, int cap);
+
+/* Latest from_GPU status of `cluster` (LK_ST_*), or LK_EINVAL. */
+int lk_status(lk_ctx* ctx, int cluster);
+
+/* First device-side error reason (LK_DERR_*), or LK_EINVAL. */
+int lk_device_error(lk_ctx* ctx);
+
+/* Number of SMs of the context's device and of CTAs in the context. */
+int lk_num_sms(lk_ctx* ctx);
+int lk_num_ctas(lk_ctx* ctx);
+
+/* Copy the execution log out: up to `cap` records, grouped by CTA, each CTA's
+ * records in the order it ran them (only the last exec_log_cap per CTA are
+ * kept).  *n receives the count written; *dropped (optional) the number of
+ * older records overwritten.  Safe while the context runs (the records of
+ * descriptors still running may be absent) and after lk_dispose has stopped
+ * the kernel.  Returns LK_OK, LK_EINVAL, LK_EDEVICE. */
+int lk_exec_log(lk_ctx* ctx, lk_exec_rec* buf, size_t cap, size_t* n, uint64_t* dropped);
+
+/* Human-readable name of an LK_* return code. */
+const char* lk_strerror(int code);
+
+/* ---- finite mode: one launch that runs a fixed list and returns -------- */
+/* Runs `count` descriptors through a fresh persistent kernel whose mailbox
+ * ring is pre-filled in device memory and ends with EXIT, so the kernel needs
+ * no host interaction and can be timed with CUDA events or replayed by a
+ * profiler.  cluster_of[i] names descriptor i's cluster; in0/in1/out are
+ * per-descriptor device pointers (NULL where unused).  *elapsed_ms (optional)
+ * receives the CUDA-event time of the launch.  If log_out is non-null it
+ * receives up to log_cap execution-log records and *log_n their count.
+ * Returns LK_OK or the lk_init / lk_dispose errors. */
+int lk_run_finite(const lk_init_params* p, const lk_desc* descs, const int* cluster_of,
+                  const void* const* in0, const void* const* in1, void* const* out, size_t count,
+                  float* elapsed_ms, lk_exec_rec* log_out, size_t log_cap, size_t* log_n);
+
+/* ---- trace runner: timed submission streams (native, no Python in the loop) */
+typedef struct {
+  uint64_t t_arrival_ns;  /* release time relative to the run's start               */
+  int32_t cluster;        /* target cluster (LK) or stream slot (ordinary launches) */
+  uint32_t op;            /* LK_OP_*                                                */
+  uint64_t n;             /* as lk_desc.n                                           */
+  const void* in0;        /* device pointers, as lk_submit                          */
+  const void* in1;
+  void* out;
+  const void* h_in0;      /* LK_TRACE_E2E only: pinned host copies of the inputs    */
+  const void* h_in1;      /* (copied to in0 / in1 before the item is released)      */
+  void* h_out;            /* ... and the host buffer `out` is copied back to        */
+  uint64_t in0_bytes;     /* bytes copied for each                                  */
+  uint64_t in1_bytes;
+  uint64_t out_bytes;
+} lk_trace_item;          /* 96 bytes */
+
+typedef struct {
+  uint64_t t_submit_ns;   /* host CLOCK_MONOTONIC at submit entry (E2E: at the start */
+                          /* of the input copy), relative to the run's start         */
+  uint64_t t_complete_ns; /* host time the completion was observed (E2E: the output  */
+                          /* copy finished)                                          */
+  int32_t status;         /* LK_OK or the error the item hit                        */
+  int32_t thread;         /* host thread that handled it                            */
+} lk_trace_result;
+
+#define LK_TRACE_OPEN   0  /* release on arrival; several items in flight per cluster */
+#define LK_TRACE_CLOSED 1  /* a thread releases its next item after the previous one finished */
+#define LK_TRACE_E2E    2  /* closed loop with host->device input and device->host output copies */
+
+/* Run a trace through a running context.  Items are split across n_threads
+ * host threads by cluster (cluster % n_threads); each thread releases its
+ * items in t_arrival order, no earlier than their arrival time, in the given
+ * mode (LK_TRACE_*).  Latency = t_complete - t_submit.
+ * pin_cpu_base >= 0 pins thread i to CPU pin_cpu_base + i.
+ * Returns LK_OK if every item finished, else the first error. */
+int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_threads,
+                 int mode, int pin_cpu_base, uint64_t timeout_ns, lk_trace_result* res);
+
+/* The same trace as ordinary kernel launches: per item, cudaLaunchKernel of
+ * the same body with grid = ctas_of_slot[item.cluster] CTAs of `threads`
+ * threads, then cudaStreamSynchronize; one non-blocking stream per slot.
+ * mode LK_TRACE_E2E adds the same copies as lk_run_trace; other modes are
+ * closed loop per thread (a launch returns only after its item finished).
+ * Must not run while a full-chip context is alive (its CTAs hold the SMs). */
+int lk_baseline_run_trace(int device, const lk_trace_item* items, size_t count, int n_slots,
+                          const int* ctas_of_slot, int threads, int n_threads, int mode,
+                          int pin_cpu_base, lk_trace_result* res);
+
+/* Dispose (as lk_dispose) and report the persistent kernel's lifetime from
+ * CUDA events recorded around its launch on its own stream (-1 if unknown). */
+int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms);
+
+/* Host-mapped round-trip floor: one host thread release-stores a counter, one
+ * GPU thread acquire-spins on it and release-stores an echo, the host
+ * acquire-spins on the echo.  Writes `iters` round-trip times (ns). */
+int lk_pingpong(int device, int iters, uint64_t* rtt_ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LK_H */

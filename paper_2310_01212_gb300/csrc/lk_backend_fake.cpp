@@ -1,0 +1,254 @@
+/*
+ * lk_backend_fake.cpp -- a host-thread stand-in for the GPU (test build
+ * liblk_fake.so only).
+ *
+ * It plays the device's side of the mailbox protocol over the same memory
+ * layout as the persistent kernel: per cluster, one thread acquires ring
+ * slots in FIFO order, reports WORKING / FINISHED in the from_GPU words,
+ * release-stores `done`, writes execution-log records for every rank, honours
+ * EXIT, the abort word and the idle lease.  Work bodies are not run: this
+ * backend exists to test the host runtime (tickets, ring-full refusals,
+ * handles, waits, timeouts, dispose) on a machine without a GPU.
+ *
+ * Fault knobs (read at launch):
+ *   LK_FAKE_SMS=n          SM count the fake device reports (default 16)
+ *   LK_FAKE_STALL_US=t     each descriptor takes t microseconds
+ *   LK_FAKE_DROP_AFTER=m   completions after the m-th are never published
+ *   LK_FAKE_FAIL_AFTER=m   after m descriptors the cluster stops with LK_DERR_BADDESC
+ *   LK_FAKE_NO_BOOT=1      the CTAs never report boot
+ */
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "lk_backend.h"
+
+namespace {
+
+uint64_t now_ns() {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+uint64_t env_u64(const char* k, uint64_t dflt) {
+  const char* v = getenv(k);
+  return v && *v ? strtoull(v, nullptr, 10) : dflt;
+}
+template <class T> T ld_acq(const T* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+template <class T> void st_rel(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+
+int fake_sms() { return (int)env_u64("LK_FAKE_SMS", 16); }
+
+}  // namespace
+
+struct lkb_launch {
+  std::vector<std::thread> threads;
+  std::atomic<int> alive{0};
+  uint64_t t0 = 0, t1 = 0;
+};
+
+int lkb_props_get(int device, lkb_props* out) {
+  if (device != 0) return LK_EDEVICE;
+  out->sm_count = fake_sms();
+  out->smem_per_sm = 233472;
+  out->smem_per_block_optin = 232448;
+  out->max_threads_per_sm = 2048;
+  out->can_map_host = 1;
+  out->cooperative = 1;
+  return LK_OK;
+}
+
+int lkb_alloc_mapped(int, size_t bytes, void** host, void** dev) {
+  void* p = aligned_alloc(4096, (bytes + 4095) / 4096 * 4096);
+  if (!p) return LK_ENOMEM;
+  memset(p, 0, bytes);
+  *host = *dev = p;
+  return LK_OK;
+}
+void lkb_free_mapped(void* host) { free(host); }
+int lkb_alloc_device(int, size_t bytes, void** dev) {
+  void* p = aligned_alloc(4096, (bytes + 4095) / 4096 * 4096);
+  if (!p) return LK_ENOMEM;
+  *dev = p;
+  return LK_OK;
+}
+void lkb_free_device(void* dev) { free(dev); }
+int lkb_zero_device(int, void* dev, size_t bytes) {
+  memset(dev, 0, bytes);
+  return LK_OK;
+}
+int lkb_copy_h2d(int, void* dst, const void* src, size_t bytes) {
+  memcpy(dst, src, bytes);
+  return LK_OK;
+}
+int lkb_copy_d2h(int, void* dst, const void* src, size_t bytes) {
+  memcpy(dst, src, bytes);
+  return LK_OK;
+}
+
+int lkb_stream_create(int, void** stream) {
+  *stream = (void*)1;
+  return LK_OK;
+}
+int lkb_memcpy_async(void*, void* dst, const void* src, size_t bytes, int) {
+  memcpy(dst, src, bytes);
+  return LK_OK;
+}
+int lkb_stream_sync(void*) { return LK_OK; }
+void lkb_stream_destroy(void*) {}
+
+static void set_error(const lk_kargs& a, int c, uint32_t code) {
+  uint32_t z = 0;
+  __atomic_compare_exchange_n(&a.ctrl->first_error, &z, code, false, __ATOMIC_ACQ_REL, __ATOMIC_RELAXED);
+  if (c >= 0) st_rel(&a.cword[c].error, (uint64_t)code);
+}
+
+/* One thread per cluster: the master's loop, with every rank's log record. */
+static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<int> smids, lkb_launch* l) {
+  const uint64_t stall = env_u64("LK_FAKE_STALL_US", 0) * 1000ull;
+  const uint64_t drop_after = env_u64("LK_FAKE_DROP_AFTER", ~0ull);
+  const uint64_t fail_after = env_u64("LK_FAKE_FAIL_AFTER", ~0ull);
+  const lk_slot* ring = a.ring + (size_t)c * (a.ring_mask + 1);
+  int err = 0;
+  for (uint64_t k = 0;; ++k) {
+    const lk_slot* s = ring + (k & a.ring_mask);
+    uint64_t hb = ld_acq(&a.ctrl->heartbeat);
+    uint64_t t_last = now_ns();
+    while (ld_acq(&s->seq) != k + 1) {
+      if (ld_acq(&a.ctrl->abort)) { err = LK_DERR_ABORT; break; }
+      uint64_t t = now_ns();
+      if (t - t_last > a.lease_ns) {
+        uint64_t h = ld_acq(&a.ctrl->heartbeat);
+        if (h == hb) { err = LK_DERR_LEASE; break; }
+        hb = h;
+        t_last = t;
+      }
+      std::this_thread::yield();
+    }
+    if (err) break;
+    const uint32_t cmd = s->cmd;
+    if (cmd == LK_CMD_EXIT) break;
+    if (k >= fail_after) { err = LK_DERR_BADDESC; break; }
+    const uint64_t t_pick = now_ns();
+    st_rel(&a.cword[c].status, (uint64_t)LK_ST_WORKING);
+    if (stall) std::this_thread::sleep_for(std::chrono::nanoseconds(stall));
+    const uint64_t t_end = now_ns();
+    if (a.log) {
+      for (size_t r = 0; r < ctas.size(); ++r) {
+        const int g = ctas[r];
+        lk_exec_rec* rec = a.log + (size_t)g * a.log_cap + (k % a.log_cap);
+        rec->seq = k + 1;
+        rec->cluster = (uint32_t)c;
+        rec->rank = (uint32_t)r;
+        rec->smid = (uint32_t)smids[r];
+        rec->op = cmd - LK_CMD_WORK;
+        rec->order = k;
+        rec->t_pick_ns = t_pick;
+        rec->t_start_ns = t_pick;
+        rec->t_end_ns = t_end;
+        rec->t_done_ns = r + 1 == ctas.size() ? t_end : 0;
+        a.log_count[g] = k + 1;
+      }
+    }
+    if (k < drop_after) {
+      st_rel(&a.cword[c].done, k + 1);
+      st_rel(&a.cword[c].status, (uint64_t)LK_ST_FINISHED);
+    }
+  }
+  if (err) set_error(a, c, (uint32_t)err);
+  st_rel(&a.cword[c].status, (uint64_t)(err ? LK_ST_ERROR : LK_ST_EXITED));
+  __atomic_fetch_add(&a.ctrl->exited, (uint32_t)ctas.size(), __ATOMIC_ACQ_REL);
+  l->alive.fetch_sub(1);
+}
+
+int lkb_launch_kernel(int, const lk_kargs* ap, int threads, lkb_launch** out) {
+  if (threads < 64) return LK_EDEVICE;
+  const lk_kargs a = *ap;
+  lkb_launch* l = new lkb_launch();
+  l->t0 = now_ns();
+  const int sms = fake_sms();
+  /* boot: CTA g lands on SM (5g + 3) mod sms; clusters from sorted SM ids */
+  std::vector<int> host_start(a.num_clusters + 1);
+  memcpy(host_start.data(), a.cl_start, sizeof(int) * (a.num_clusters + 1));
+  std::vector<int> sm_of(a.grid);
+  for (int g = 0; g < a.grid; ++g) sm_of[g] = (5 * g + 3) % sms;
+  std::vector<int> order(a.grid);
+  for (int g = 0; g < a.grid; ++g) order[g] = g;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return sm_of[x] < sm_of[y]; });
+  std::vector<std::vector<int>> ctas(a.num_clusters), smids(a.num_clusters);
+  for (int g = 0; g < a.grid; ++g) {
+    int pos = -1;
+    if (a.pin_smid) {
+      for (int i = 0; i < a.total; ++i)
+        if (a.pin_smid[i] == sm_of[g]) pos = i;
+    } else {
+      pos = (int)(std::find(order.begin(), order.end(), g) - order.begin());
+    }
+    int c = -1, r = -1;
+    if (pos >= 0) {
+      c = 0;
+      while (host_start[c + 1] <= pos) ++c;
+      r = pos - host_start[c];
+    }
+    a.info[g].cluster = c;
+    a.info[g].rank = r;
+    a.info[g].smid = sm_of[g];
+  }
+  for (int c = 0; c < a.num_clusters; ++c) {
+    int size = host_start[c + 1] - host_start[c];
+    ctas[c].assign(size, -1);
+    smids[c].assign(size, -1);
+  }
+  for (int g = 0; g < a.grid; ++g)
+    if (a.info[g].cluster >= 0) {
+      ctas[a.info[g].cluster][a.info[g].rank] = g;
+      smids[a.info[g].cluster][a.info[g].rank] = sm_of[g];
+    }
+  if (env_u64("LK_FAKE_NO_BOOT", 0)) {
+    /* never boots: the "kernel" just waits for the abort word */
+    l->alive.store(1);
+    l->threads.emplace_back([a, l] {
+      while (!ld_acq(&a.ctrl->abort)) std::this_thread::yield();
+      l->alive.fetch_sub(1);
+    });
+    *out = l;
+    return LK_OK;
+  }
+  for (int c = 0; c < a.num_clusters; ++c) st_rel(&a.cword[c].status, (uint64_t)LK_ST_INIT);
+  __atomic_store_n(&a.ctrl->booted, (uint32_t)a.grid, __ATOMIC_RELEASE);
+  l->alive.store(a.num_clusters);
+  for (int c = 0; c < a.num_clusters; ++c) l->threads.emplace_back(cluster_loop, a, c, ctas[c], smids[c], l);
+  *out = l;
+  return LK_OK;
+}
+
+int lkb_finished(lkb_launch* l) {
+  if (!l) return 1;
+  if (l->alive.load() == 0) {
+    if (!l->t1) l->t1 = now_ns();
+    return 1;
+  }
+  return 0;
+}
+
+float lkb_elapsed_ms(lkb_launch* l) { return l && l->t1 ? (float)((l->t1 - l->t0) / 1e6) : -1.f; }
+
+void lkb_release(lkb_launch* l) {
+  if (!l) return;
+  for (auto& t : l->threads)
+    if (t.joinable()) t.join();
+  delete l;
+}
+
+/* The ordinary-launch and ping-pong entry points need a GPU. */
+extern "C" int lk_baseline_run_trace(int, const lk_trace_item*, size_t, int, const int*, int, int, int, int,
+                                     lk_trace_result*) {
+  return LK_EDEVICE;
+}
+extern "C" int lk_pingpong(int, int, uint64_t*) { return LK_EDEVICE; }

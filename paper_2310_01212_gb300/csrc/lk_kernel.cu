@@ -1,0 +1,797 @@
+/*
+ * lk_kernel.cu -- the LightKernel persistent kernel for sm_103a, its CUDA
+ * backend, the ordinary-launch baseline and the host-mapped ping-pong.
+ *
+ * Persistent kernel (Sec. II.C): spawned once, one CTA per SM (the dynamic
+ * shared-memory request leaves no room for a second CTA, and the launch is
+ * cooperative so all CTAs are resident or the launch fails).  At boot every
+ * CTA reads %smid; the CTAs exchange their SM ids and each one joins the
+ * cluster that its SM belongs to (clusters are cut from the sorted SM ids, or
+ * given as explicit SM lists).  The paper's check that a block sits on the SM
+ * it expects becomes a table built from the SM ids actually observed.
+ *
+ * Mailboxes (Sec. II.D, Table 1): thread 0 of each cluster's rank-0 CTA is
+ * the master thread.  It acquire-polls the cluster's host-mapped ring at
+ * system scope, relays each descriptor to the other CTAs of the cluster
+ * through a device-memory ring (GPU scope), and every CTA runs its share.
+ * Each CTA then arrives on a per-descriptor counter; the last one to arrive
+ * combines partial results and release-stores the descriptor's sequence
+ * number into the host-mapped `done` word (from_GPU = THREAD_FINISHED).
+ *
+ * Every device-side wait is bounded: by an idle lease (refreshed by the
+ * host's heartbeat), by the host's abort word, and by a stall deadline.  On
+ * expiry the kernel records the reason and returns normally.
+ */
+#include <cuda_runtime.h>
+#include <pthread.h>
+#include <sched.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "lk_backend.h"
+#include "lk_bodies.cuh"
+#include "lk_layout.h"
+
+using namespace lk;
+
+#define LK_GEN_STOP 0xffffffffffffffffull
+
+/* ======================================================================= */
+/* device side                                                              */
+/* ======================================================================= */
+
+__device__ __forceinline__ void set_error(const lk_kargs& a, int c, uint32_t code) {
+  cas_relaxed_sys(&a.ctrl->first_error, 0u, code);
+  if (c >= 0) st_relaxed_sys(&a.cword[c].error, (uint64_t)code);
+  __threadfence_system();
+}
+
+/* Master thread: wait until ring slot `s` carries sequence number `want`.
+ * Returns 0 or an LK_DERR_* reason (lease ran out, abort). */
+__device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_slot* s, uint64_t want, lk_slot& out) {
+  Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
+  uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+  uint64_t t_last = gtime();
+  for (uint32_t it = 1;; ++it) {
+    if (ld_acquire_sys(&s->seq) == want) break;
+    if ((it & 63) == 0) {
+      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+      const uint64_t now = gtime();
+      if (now - t_last > a.lease_ns) {
+        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+        if (h == hb) return LK_DERR_LEASE;
+        hb = h;
+        t_last = now;
+      }
+    }
+    bo.pause();
+  }
+  /* the acquire above orders these reads after the host's slot writes */
+  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(s);
+  const ulonglong2 v0 = __ldcv(p + 0), v1 = __ldcv(p + 1), v2 = __ldcv(p + 2), v3 = __ldcv(p + 3);
+  out.seq = want;
+  out.cmd = (uint32_t)(v0.y & 0xffffffffull);
+  out.flags = (uint32_t)(v0.y >> 32);
+  out.n = v1.x;
+  out.in0 = v1.y;
+  out.in1 = v2.x;
+  out.out = v2.y;
+  out.aux = v3.x;
+  out.t_pick = 0;
+  return 0;
+}
+
+/* Wait until *word >= want (GPU scope).  Members wait on the relay
+ * generation, the master on the relay slot becoming free.  `stop_on_max`
+ * treats LK_GEN_STOP as the master's stop signal (returns -1). */
+__device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, uint64_t want, bool stop_on_max) {
+  Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
+  uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+  uint64_t t_last = gtime();
+  const uint64_t limit = a.lease_ns + 1000000000ull;
+  for (uint32_t it = 1;; ++it) {
+    const uint64_t g = ld_acquire_gpu(word);
+    if (stop_on_max && g == LK_GEN_STOP) return -1;
+    if (g >= want) return 0;
+    if ((it & 255) == 0) {
+      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+      const uint64_t now = gtime();
+      if (now - t_last > limit) {
+        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+        if (h == hb) return LK_DERR_STALL;
+        hb = h;
+        t_last = now;
+      }
+    }
+    bo.pause();
+  }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
+  constexpr int U = 2048 / MAXT;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(64) lk_slot s_desc;
+  __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_last, s_err;
+  __shared__ float s_red[32];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint64_t s_tstart;
+  const uint32_t tid = threadIdx.x;
+
+  /* ---- boot: read %smid, exchange, join a cluster --------------------- */
+  if (tid == 0) {
+    s_err = 0;
+    const uint32_t sm = smid();
+    a.boot_smid[blockIdx.x] = (int32_t)sm;
+    __threadfence();
+    atomicAdd(a.boot_count, 1u);
+    const uint64_t t0 = gtime();
+    int err = 0;
+    while (ld_acquire_gpu32(a.boot_count) < (uint32_t)a.grid) {
+      if (gtime() - t0 > a.boot_timeout_ns) {
+        err = LK_DERR_BOOT;
+        break;
+      }
+    }
+    int c = -1, rk = -1;
+    if (!err) {
+      int pos = -1;
+      if (a.pin_smid) {
+        for (int i = 0; i < a.total; ++i)
+          if (a.pin_smid[i] == (int32_t)sm) {
+            pos = i;
+            break;
+          }
+      } else {
+        pos = 0;
+        for (int j = 0; j < a.grid; ++j) {
+          const int32_t o = __ldcg(a.boot_smid + j);
+          if (o < (int32_t)sm || (o == (int32_t)sm && j < (int)blockIdx.x)) ++pos;
+        }
+      }
+      if (pos >= 0) {
+        c = 0;
+        while (a.cl_start[c + 1] <= pos) ++c;
+        rk = pos - a.cl_start[c];
+      }
+    }
+    s_cl = c;
+    s_rank = rk;
+    s_size = c >= 0 ? a.cl_start[c + 1] - a.cl_start[c] : 0;
+    lk_cta_info* inf = a.info + blockIdx.x;
+    st_relaxed_sys32(&inf->cluster, c);
+    st_relaxed_sys32(&inf->rank, rk);
+    st_relaxed_sys32(&inf->smid, (int32_t)sm);
+    if (err) {
+      set_error(a, c, (uint32_t)err);
+      s_err = err;
+    } else if (rk == 0) {
+      st_relaxed_sys(&a.cword[c].status, LK_ST_INIT);
+    }
+    mbar_init(&s_bar, 1);
+    fence_barrier_init();
+    red_release_sys_add(&a.ctrl->booted, 1u);
+  }
+  __syncthreads();
+  if (s_cl < 0 || s_err) return;
+
+  const int c = s_cl, r = s_rank, S = s_size;
+  const bool master = (r == 0);
+  lk_dcluster* dc = a.dcl + c;
+  const lk_slot* ring = a.ring + (size_t)c * (a.ring_mask + 1);
+  float* sA = reinterpret_cast<float*>(dsm);
+  float* sB = reinterpret_cast<float*>(dsm + 16384);
+  uint32_t* sh = reinterpret_cast<uint32_t*>(dsm);
+  uint32_t phase = 0;
+  int final_err = 0;
+
+  for (uint64_t k = 0;; ++k) {
+    const uint32_t slot = (uint32_t)(k % LK_BCAST_DEPTH);
+    /* ---- take (master) or receive (members) descriptor k+1 ------------- */
+    if (tid == 0) {
+      int err = 0;
+      lk_slot dsc;
+      if (master) {
+        err = take_from_ring(a, ring + (k & a.ring_mask), k + 1, dsc);
+        if (!err) {
+          dsc.t_pick = gtime();
+          /* relay slot k mod D is free once descriptor k+1-D has finished */
+          if (k + 1 > LK_BCAST_DEPTH) {
+            const int w = wait_word(a, &dc->dev_done, k + 1 - LK_BCAST_DEPTH, false);
+            err = w < 0 ? LK_DERR_STALL : w;
+          }
+        }
+        if (!err) {
+          lk_slot* b = &dc->bcast[slot];
+          *b = dsc;
+          st_release_gpu(&dc->gen, k + 1);
+          if (dsc.cmd != LK_CMD_EXIT) st_relaxed_sys(&a.cword[c].status, LK_ST_WORKING);
+        } else {
+          st_release_gpu(&dc->gen, LK_GEN_STOP);
+        }
+      } else {
+        const int w = wait_word(a, &dc->gen, k + 1, true);
+        if (w < 0) err = -1;   /* master stopped; its reason is recorded */
+        else err = w;
+        if (!err) {
+          const ulonglong2* p = reinterpret_cast<const ulonglong2*>(&dc->bcast[slot]);
+          const ulonglong2 v0 = __ldcg(p + 0), v1 = __ldcg(p + 1), v2 = __ldcg(p + 2), v3 = __ldcg(p + 3);
+          dsc.seq = v0.x;
+          dsc.cmd = (uint32_t)(v0.y & 0xffffffffull);
+          dsc.flags = (uint32_t)(v0.y >> 32);
+          dsc.n = v1.x;
+          dsc.in0 = v1.y;
+          dsc.in1 = v2.x;
+          dsc.out = v2.y;
+          dsc.aux = v3.x;
+          dsc.t_pick = v3.y;
+        }
+      }
+      if (err) {
+        if (err > 0) {
+          set_error(a, c, (uint32_t)err);
+          final_err = err;
+        } else {
+          final_err = LK_DERR_STALL;   /* for the status word only */
+        }
+        s_exit = 1;
+      } else {
+        s_desc = dsc;
+        s_exit = (dsc.cmd == LK_CMD_EXIT);
+      }
+      s_last = 0;
+      s_err = 0;
+      s_tstart = gtime();
+    }
+    __syncthreads();
+    if (s_exit) break;
+
+    /* ---- run this CTA's share ------------------------------------------ */
+    const lk_slot d = s_desc;
+    const uint32_t op = d.cmd - LK_CMD_WORK;
+    switch (op) {
+      case LK_OP_ADD_I32: body_add_copy<U, true>(d, r, S); break;
+      case LK_OP_COPY_I32: body_add_copy<U, false>(d, r, S); break;
+      case LK_OP_SUM_F32: {
+        const float p = body_sum_partial<U>(d, r, S, s_red);
+        if (tid == 0) dc->partial[slot][r] = p;
+        break;
+      }
+      case LK_OP_HIST_U8: body_hist<U>(d, r, S, sh, dc->hist[slot]); break;
+      case LK_OP_GEMM64_F32:
+        if (!body_gemm(d, r, S, sA, sB, &s_bar, phase, gtime() + 2000000000ull)) s_err = LK_DERR_STAGING;
+        break;
+      case LK_OP_NOP: break;
+      default:
+        if (tid == 0) s_err = LK_DERR_BADDESC;
+    }
+    __syncthreads();
+
+    /* ---- arrive; the last CTA completes the descriptor ------------------ */
+    uint64_t t_end = 0;
+    if (tid == 0) {
+      t_end = gtime();
+      __threadfence();
+      const uint32_t old = atom_add_acq_rel_gpu(&dc->arrive[slot], 1u);
+      s_last = (old == (uint32_t)(S - 1));
+    }
+    __syncthreads();
+    uint64_t t_done = 0;
+    if (s_last) {
+      if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
+      else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+      __syncthreads();
+      if (tid == 0) {
+        dc->arrive[slot] = 0;
+        __threadfence();
+        st_release_gpu(&dc->dev_done, k + 1);
+        st_release_sys(&a.cword[c].done, d.seq);
+        t_done = gtime();
+        st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);
+      }
+    }
+    if (tid == 0 && a.log) {
+      lk_exec_rec* rec = a.log + (size_t)blockIdx.x * a.log_cap + (k % a.log_cap);
+      rec->seq = d.seq;
+      rec->cluster = (uint32_t)c;
+      rec->rank = (uint32_t)r;
+      rec->smid = smid();
+      rec->op = op;
+      rec->order = k;
+      rec->t_pick_ns = d.t_pick;
+      rec->t_start_ns = s_tstart;
+      rec->t_end_ns = t_end;
+      rec->t_done_ns = t_done;
+      a.log_count[blockIdx.x] = k + 1;
+    }
+    if (s_err) {
+      if (tid == 0) {
+        set_error(a, c, (uint32_t)s_err);
+        final_err = s_err;
+        if (master) st_release_gpu(&dc->gen, LK_GEN_STOP);
+      }
+      break;
+    }
+  }
+  if (tid == 0) {
+    if (master) st_relaxed_sys(&a.cword[c].status, final_err ? LK_ST_ERROR : LK_ST_EXITED);
+    red_release_sys_add(&a.ctrl->exited, 1u);
+  }
+}
+
+/* ---- ordinary-launch baseline: the same bodies, one launch per item ------ */
+struct lk_scratch {
+  uint32_t counter;
+  uint32_t pad[31];
+  uint32_t hist[256];
+  float partial[LK_MAX_CTAS];
+};
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch* sc) {
+  constexpr int U = 2048 / MAXT;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ float s_red[32];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int32_t s_last;
+  const int r = blockIdx.x, S = gridDim.x;
+  const uint32_t op = d.cmd - LK_CMD_WORK;
+  switch (op) {
+    case LK_OP_ADD_I32: body_add_copy<U, true>(d, r, S); return;
+    case LK_OP_COPY_I32: body_add_copy<U, false>(d, r, S); return;
+    case LK_OP_NOP: return;
+    case LK_OP_GEMM64_F32: {
+      if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_barrier_init();
+      }
+      __syncthreads();
+      uint32_t phase = 0;
+      body_gemm(d, r, S, reinterpret_cast<float*>(dsm), reinterpret_cast<float*>(dsm + 16384), &s_bar, phase,
+                gtime() + 2000000000ull);
+      return;
+    }
+    case LK_OP_SUM_F32: {
+      const float p = body_sum_partial<U>(d, r, S, s_red);
+      if (threadIdx.x == 0) sc->partial[r] = p;
+      break;
+    }
+    case LK_OP_HIST_U8: body_hist<U>(d, r, S, reinterpret_cast<uint32_t*>(dsm), sc->hist); break;
+    default: return;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atom_add_acq_rel_gpu(&sc->counter, 1u) == (uint32_t)(S - 1);
+  }
+  __syncthreads();
+  if (s_last) {
+    if (op == LK_OP_SUM_F32) combine_sum(d, sc->partial, S);
+    else combine_hist(d, sc->hist);
+    __syncthreads();
+    if (threadIdx.x == 0) sc->counter = 0;
+  }
+}
+
+/* ---- host-mapped ping-pong (the dispatch floor) ------------------------- */
+__global__ void lk_pingpong_kernel(const uint64_t* ping, uint64_t* pong, int iters, uint64_t abort_after_ns) {
+  if (threadIdx.x != 0) return;
+  for (int i = 1; i <= iters; ++i) {
+    const uint64_t t0 = gtime();
+    while (ld_acquire_sys(ping) != (uint64_t)i) {
+      if (gtime() - t0 > abort_after_ns) {
+        st_release_sys(pong, ~0ull);
+        return;
+      }
+    }
+    st_release_sys(pong, (uint64_t)i);
+  }
+}
+
+/* ======================================================================= */
+/* host side: CUDA backend                                                  */
+/* ======================================================================= */
+namespace {
+
+std::once_flag g_preload_once;
+cudaError_t g_preload_err = cudaSuccess;
+
+/* Load every kernel of this library up front: with lazy module loading, a
+ * first launch while a persistent kernel holds the SMs could wait on it. */
+void preload_all() {
+  std::call_once(g_preload_once, [] {
+    cudaFuncAttributes fa;
+    const void* fns[] = {(const void*)lk_persistent<256>,  (const void*)lk_persistent<512>,
+                         (const void*)lk_persistent<1024>, (const void*)lk_ordinary<256>,
+                         (const void*)lk_ordinary<512>,    (const void*)lk_ordinary<1024>,
+                         (const void*)lk_pingpong_kernel};
+    for (const void* f : fns) {
+      cudaError_t e = cudaFuncGetAttributes(&fa, f);
+      if (e != cudaSuccess && g_preload_err == cudaSuccess) g_preload_err = e;
+    }
+  });
+}
+
+const void* persistent_fn(int threads) {
+  if (threads <= 256) return (const void*)lk_persistent<256>;
+  if (threads <= 512) return (const void*)lk_persistent<512>;
+  return (const void*)lk_persistent<1024>;
+}
+
+/* Allocations are recycled, never returned to the driver while the process
+ * runs: cudaFree / cudaFreeHost may wait for the whole device, which would
+ * stall behind any other persistent kernel that is still resident. */
+struct Block {
+  void* host;
+  void* dev;
+  size_t bytes;
+  int device;
+  bool mapped;
+};
+std::mutex g_pool_mu;
+std::vector<Block> g_free;
+std::vector<Block> g_used;
+
+cudaStream_t copy_stream(int device) {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> streams;
+  std::lock_guard<std::mutex> g(mu);
+  if ((int)streams.size() <= device) streams.resize(device + 1, nullptr);
+  if (!streams[device]) {
+    cudaSetDevice(device);
+    cudaStreamCreateWithFlags(&streams[device], cudaStreamNonBlocking);
+  }
+  return streams[device];
+}
+
+int take_block(int device, size_t bytes, bool mapped, Block* out) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  size_t best = (size_t)-1;
+  for (size_t i = 0; i < g_free.size(); ++i) {
+    const Block& b = g_free[i];
+    if (b.device == device && b.mapped == mapped && b.bytes >= bytes && b.bytes <= 2 * bytes + (1 << 20) &&
+        (best == (size_t)-1 || b.bytes < g_free[best].bytes))
+      best = i;
+  }
+  if (best != (size_t)-1) {
+    *out = g_free[best];
+    g_free.erase(g_free.begin() + best);
+    g_used.push_back(*out);
+    return LK_OK;
+  }
+  Block b{nullptr, nullptr, bytes, device, mapped};
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  if (mapped) {
+    if (cudaHostAlloc(&b.host, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) return LK_ENOMEM;
+    if (cudaHostGetDevicePointer(&b.dev, b.host, 0) != cudaSuccess) return LK_EDEVICE;
+  } else {
+    if (cudaMalloc(&b.dev, bytes) != cudaSuccess) return LK_ENOMEM;
+  }
+  g_used.push_back(b);
+  *out = b;
+  return LK_OK;
+}
+
+void give_back(void* key, bool mapped) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  for (size_t i = 0; i < g_used.size(); ++i) {
+    void* k = mapped ? g_used[i].host : g_used[i].dev;
+    if (k == key) {
+      g_free.push_back(g_used[i]);
+      g_used.erase(g_used.begin() + i);
+      return;
+    }
+  }
+}
+
+int zero_device(int device, void* dev, size_t bytes) {
+  /* a host->device copy of zeros runs on a copy engine, not on the SMs */
+  static std::vector<char> zeros;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  const size_t chunk = 4u << 20;
+  if (zeros.size() < chunk) zeros.assign(chunk, 0);
+  cudaStream_t s = copy_stream(device);
+  for (size_t off = 0; off < bytes; off += chunk) {
+    size_t nb = std::min(chunk, bytes - off);
+    if (cudaMemcpyAsync((char*)dev + off, zeros.data(), nb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return LK_EDEVICE;
+  }
+  return cudaStreamSynchronize(s) == cudaSuccess ? LK_OK : LK_EDEVICE;
+}
+
+}  // namespace
+
+struct lkb_launch {
+  int device;
+  cudaStream_t s;
+  cudaEvent_t e0, e1;
+};
+
+int lkb_props_get(int device, lkb_props* out) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return LK_EDEVICE;
+  out->sm_count = p.multiProcessorCount;
+  out->smem_per_sm = p.sharedMemPerMultiprocessor;
+  out->smem_per_block_optin = p.sharedMemPerBlockOptin;
+  out->max_threads_per_sm = p.maxThreadsPerMultiProcessor;
+  out->can_map_host = p.canMapHostMemory;
+  out->cooperative = p.cooperativeLaunch;
+  return LK_OK;
+}
+
+int lkb_alloc_mapped(int device, size_t bytes, void** host, void** dev) {
+  Block b;
+  int rc = take_block(device, bytes, true, &b);
+  if (rc != LK_OK) return rc;
+  memset(b.host, 0, bytes);
+  *host = b.host;
+  *dev = b.dev;
+  return LK_OK;
+}
+void lkb_free_mapped(void* host) { give_back(host, true); }
+
+int lkb_alloc_device(int device, size_t bytes, void** dev) {
+  Block b;
+  int rc = take_block(device, bytes, false, &b);
+  if (rc != LK_OK) return rc;
+  *dev = b.dev;
+  return LK_OK;
+}
+void lkb_free_device(void* dev) { give_back(dev, false); }
+
+int lkb_zero_device(int device, void* dev, size_t bytes) { return zero_device(device, dev, bytes); }
+
+int lkb_copy_h2d(int device, void* dst, const void* src, size_t bytes) {
+  cudaStream_t s = copy_stream(device);
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return LK_EDEVICE;
+  return cudaStreamSynchronize(s) == cudaSuccess ? LK_OK : LK_EDEVICE;
+}
+int lkb_copy_d2h(int device, void* dst, const void* src, size_t bytes) {
+  cudaStream_t s = copy_stream(device);
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return LK_EDEVICE;
+  return cudaStreamSynchronize(s) == cudaSuccess ? LK_OK : LK_EDEVICE;
+}
+
+int lkb_stream_create(int device, void** stream) {
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LK_EDEVICE;
+  *stream = (void*)s;
+  return LK_OK;
+}
+int lkb_memcpy_async(void* stream, void* dst, const void* src, size_t bytes, int host_to_device) {
+  return cudaMemcpyAsync(dst, src, bytes, host_to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost,
+                         (cudaStream_t)stream) == cudaSuccess
+             ? LK_OK
+             : LK_EDEVICE;
+}
+int lkb_stream_sync(void* stream) {
+  return cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? LK_OK : LK_EDEVICE;
+}
+void lkb_stream_destroy(void* stream) {
+  if (stream) cudaStreamDestroy((cudaStream_t)stream);
+}
+
+int lkb_launch_kernel(int device, const lk_kargs* a, int threads, lkb_launch** out) {
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  if (g_preload_err != cudaSuccess) return LK_EDEVICE;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return LK_EDEVICE;
+  const void* fn = persistent_fn(threads);
+  /* one CTA per SM: ask for more than half of the SM's shared memory */
+  size_t dyn = std::max<size_t>(lk::body_smem_bytes(threads), p.sharedMemPerMultiprocessor / 2);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return LK_EDEVICE;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess) return LK_EDEVICE;
+  if (per_sm != 1 || a->grid > p.multiProcessorCount) return LK_EDEVICE;
+  lkb_launch* l = new lkb_launch{device, nullptr, nullptr, nullptr};
+  if (cudaStreamCreateWithFlags(&l->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&l->e0) != cudaSuccess || cudaEventCreate(&l->e1) != cudaSuccess) {
+    lkb_release(l);
+    return LK_EDEVICE;
+  }
+  lk_kargs args = *a;
+  void* params[] = {&args};
+  cudaEventRecord(l->e0, l->s);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(a->grid), dim3(threads), params, dyn, l->s);
+  if (e != cudaSuccess) {
+    if (getenv("LK_LOG")) fprintf(stderr, "lk: cooperative launch failed: %s\n", cudaGetErrorString(e));
+    lkb_release(l);
+    return LK_EDEVICE;
+  }
+  cudaEventRecord(l->e1, l->s);
+  *out = l;
+  return LK_OK;
+}
+
+int lkb_finished(lkb_launch* l) {
+  if (!l) return 1;
+  cudaError_t e = cudaEventQuery(l->e1);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return -1;
+}
+
+float lkb_elapsed_ms(lkb_launch* l) {
+  float ms = -1.f;
+  if (!l || cudaEventElapsedTime(&ms, l->e0, l->e1) != cudaSuccess) return -1.f;
+  return ms;
+}
+
+void lkb_release(lkb_launch* l) {
+  if (!l) return;
+  if (l->e0) cudaEventDestroy(l->e0);
+  if (l->e1) cudaEventDestroy(l->e1);
+  if (l->s) cudaStreamDestroy(l->s);
+  delete l;
+}
+
+/* ======================================================================= */
+/* ordinary-launch baseline and ping-pong (C ABI)                           */
+/* ======================================================================= */
+namespace {
+inline uint64_t now_ns() {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+void pin_cpu(int cpu) {
+  if (cpu < 0) return;
+  int n = (int)std::thread::hardware_concurrency();
+  if (n <= 0) return;
+  cpu_set_t set;
+  CPU_ZERO(&set);
+  CPU_SET(cpu % n, &set);
+  pthread_setaffinity_np(pthread_self(), sizeof set, &set);
+}
+cudaError_t launch_ordinary(const lk_slot& d, int grid, int threads, lk_scratch* sc, cudaStream_t s) {
+  const uint32_t op = d.cmd - LK_CMD_WORK;
+  const size_t smem = (op == LK_OP_HIST_U8 || op == LK_OP_GEMM64_F32) ? lk::body_smem_bytes(threads) : 0;
+  if (threads <= 256) lk_ordinary<256><<<grid, threads, smem, s>>>(d, sc);
+  else if (threads <= 512) lk_ordinary<512><<<grid, threads, smem, s>>>(d, sc);
+  else lk_ordinary<1024><<<grid, threads, smem, s>>>(d, sc);
+  return cudaGetLastError();
+}
+}  // namespace
+
+extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, size_t count, int n_slots,
+                                     const int* ctas_of_slot, int threads, int n_threads, int mode,
+                                     int pin_cpu_base, lk_trace_result* res) {
+  if ((count > 0 && (!items || !res)) || n_slots < 1 || !ctas_of_slot || n_threads < 1 || threads < 64 ||
+      threads > 1024 || threads % 32)
+    return LK_EINVAL;
+  for (int s = 0; s < n_slots; ++s)
+    if (ctas_of_slot[s] < 1 || ctas_of_slot[s] > LK_MAX_CTAS) return LK_EINVAL;
+  for (size_t i = 0; i < count; ++i) {
+    if (items[i].cluster < 0 || items[i].cluster >= n_slots || items[i].op >= LK_OP_COUNT) return LK_EINVAL;
+    res[i] = lk_trace_result{0, 0, LK_PENDING, -1};
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  std::vector<cudaStream_t> st(n_slots, nullptr);
+  std::vector<lk_scratch*> sc(n_slots, nullptr);
+  int rc = LK_OK;
+  for (int s = 0; s < n_slots && rc == LK_OK; ++s) {
+    if (cudaStreamCreateWithFlags(&st[s], cudaStreamNonBlocking) != cudaSuccess) rc = LK_EDEVICE;
+    else if (cudaMalloc(&sc[s], sizeof(lk_scratch)) != cudaSuccess) rc = LK_ENOMEM;
+    else if (cudaMemsetAsync(sc[s], 0, sizeof(lk_scratch), st[s]) != cudaSuccess) rc = LK_EDEVICE;
+    else if (cudaStreamSynchronize(st[s]) != cudaSuccess) rc = LK_EDEVICE;
+  }
+  if (rc == LK_OK) {
+    std::vector<std::vector<size_t>> mine(n_threads);
+    for (size_t i = 0; i < count; ++i) mine[items[i].cluster % n_threads].push_back(i);
+    for (auto& v : mine)
+      std::stable_sort(v.begin(), v.end(),
+                       [&](size_t a, size_t b) { return items[a].t_arrival_ns < items[b].t_arrival_ns; });
+    std::atomic<int> ready{0};
+    std::atomic<uint64_t> start{0};
+    std::atomic<int> err{0};
+    auto worker = [&](int w) {
+      pin_cpu(pin_cpu_base >= 0 ? pin_cpu_base + w : -1);
+      cudaSetDevice(device);
+      ready.fetch_add(1);
+      uint64_t t0;
+      while ((t0 = start.load(std::memory_order_acquire)) == 0) {
+      }
+      for (size_t i : mine[w]) {
+        const lk_trace_item& it = items[i];
+        while (now_ns() < t0 + it.t_arrival_ns) {
+        }
+        lk_slot d;
+        memset(&d, 0, sizeof d);
+        d.cmd = LK_CMD_WORK + it.op;
+        d.n = it.n;
+        d.in0 = (uint64_t)(uintptr_t)it.in0;
+        d.in1 = (uint64_t)(uintptr_t)it.in1;
+        d.out = (uint64_t)(uintptr_t)it.out;
+        const int s = it.cluster;
+        const bool e2e = mode == LK_TRACE_E2E;
+        const uint64_t ts = now_ns();
+        cudaError_t e = cudaSuccess;
+        if (e2e) {
+          if (it.in0_bytes && it.h_in0)
+            e = cudaMemcpyAsync((void*)it.in0, it.h_in0, it.in0_bytes, cudaMemcpyHostToDevice, st[s]);
+          if (e == cudaSuccess && it.in1_bytes && it.h_in1)
+            e = cudaMemcpyAsync((void*)it.in1, it.h_in1, it.in1_bytes, cudaMemcpyHostToDevice, st[s]);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
+        }
+        if (e == cudaSuccess) e = launch_ordinary(d, ctas_of_slot[s], threads, sc[s], st[s]);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
+        if (e == cudaSuccess && e2e && it.out_bytes && it.h_out) {
+          e = cudaMemcpyAsync(it.h_out, it.out, it.out_bytes, cudaMemcpyDeviceToHost, st[s]);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
+        }
+        const uint64_t tc = now_ns();
+        res[i].t_submit_ns = ts - t0;
+        res[i].t_complete_ns = tc - t0;
+        res[i].thread = w;
+        res[i].status = e == cudaSuccess ? LK_OK : LK_EDEVICE;
+        if (e != cudaSuccess) {
+          int z = 0;
+          err.compare_exchange_strong(z, LK_EDEVICE);
+          return;
+        }
+      }
+    };
+    std::vector<std::thread> th;
+    for (int w = 0; w < n_threads; ++w) th.emplace_back(worker, w);
+    while (ready.load() < n_threads) std::this_thread::yield();
+    start.store(now_ns(), std::memory_order_release);
+    for (auto& x : th) x.join();
+    rc = err.load();
+  }
+  for (int s = 0; s < n_slots; ++s) {
+    if (st[s]) cudaStreamSynchronize(st[s]);
+    if (sc[s]) cudaFree(sc[s]);
+    if (st[s]) cudaStreamDestroy(st[s]);
+  }
+  return rc;
+}
+
+extern "C" int lk_pingpong(int device, int iters, uint64_t* rtt_ns) {
+  if (iters < 1 || !rtt_ns) return LK_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  void *h = nullptr, *dptr = nullptr;
+  int rc = lkb_alloc_mapped(device, 4096, &h, &dptr);
+  if (rc != LK_OK) return rc;
+  uint64_t* ping = (uint64_t*)h;
+  uint64_t* pong = (uint64_t*)h + 16;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    lkb_free_mapped(h);
+    return LK_EDEVICE;
+  }
+  lk_pingpong_kernel<<<1, 32, 0, s>>>((const uint64_t*)dptr, (uint64_t*)dptr + 16, iters, 2000000000ull);
+  if (cudaGetLastError() != cudaSuccess) rc = LK_EDEVICE;
+  for (int i = 1; i <= iters && rc == LK_OK; ++i) {
+    const uint64_t t0 = now_ns();
+    __atomic_store_n(ping, (uint64_t)i, __ATOMIC_RELEASE);
+    for (;;) {
+      const uint64_t x = __atomic_load_n(pong, __ATOMIC_ACQUIRE);
+      if (x == (uint64_t)i) break;
+      if (x == ~0ull || now_ns() - t0 > 3000000000ull) {
+        rc = LK_ETIMEDOUT;
+        break;
+      }
+    }
+    rtt_ns[i - 1] = now_ns() - t0;
+  }
+  if (rc != LK_OK) __atomic_store_n(ping, ~0ull, __ATOMIC_RELEASE);
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == LK_OK) rc = LK_EDEVICE;
+  cudaStreamDestroy(s);
+  lkb_free_mapped(h);
+  return rc;
+}

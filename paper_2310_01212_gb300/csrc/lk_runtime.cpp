@@ -1,0 +1,734 @@
+/*
+ * lk_runtime.cpp -- host side of LightKernel-GB300 (the C ABI of lk.h).
+ *
+ * The host is the producer side of every cluster's mailbox (Sec. II.D).  A
+ * mailbox is a ring of 64-byte slots in pinned host-mapped memory.  Posting
+ * (Trigger, Sec. III) is: take a ticket t on the cluster's tail (a CAS that
+ * also refuses when the ring is full), fill slot t mod R, then publish it by
+ * release-storing seq = t + 1.  No CUDA call is on this path.  Waiting is an
+ * acquire load of the cluster's `done` word, which the device release-stores
+ * when the last CTA of the cluster finishes a descriptor.
+ */
+#include <errno.h>
+#include <pthread.h>
+#include <sched.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "lk_backend.h"
+#include "lk_layout.h"
+
+namespace {
+
+inline uint64_t now_ns() {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+template <class T> inline T ld_acq(const T* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+template <class T> inline T ld_rlx(const T* p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+template <class T> inline void st_rel(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+template <class T> inline void st_rlx(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
+
+struct alignas(LK_LINE) Tail {
+  std::atomic<uint64_t> t{0};
+};
+
+constexpr uint64_t kSeqMask = (1ull << 48) - 1;
+
+}  // namespace
+
+struct lk_ctx {
+  int device = 0;
+  int C = 0;          /* clusters */
+  int G = 0;          /* CTAs launched */
+  int total = 0;      /* CTAs that join clusters */
+  int T = 256;        /* threads per CTA */
+  uint32_t R = 1024;  /* ring depth */
+  int sm_count = 0;
+  bool finite = false;
+  std::vector<int> sizes;
+  std::vector<int> cl_start;
+
+  void* mapped_h = nullptr;
+  void* mapped_d = nullptr;
+  lk_slot* ring_h = nullptr;     /* host view of the ring (live mode) */
+  lk_cword* cword_h = nullptr;
+  lk_ctrl* ctrl_h = nullptr;
+  lk_cta_info* info_h = nullptr;
+
+  void* dev_base = nullptr;
+  lk_kargs args{};
+  uint32_t log_cap = 0;
+
+  Tail* tail = nullptr;          /* [C], host-only tickets */
+  lkb_launch* launch = nullptr;
+  std::atomic<int> running{0};
+};
+
+/* ---------------------------------------------------------------------- */
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static void beat(lk_ctx* ctx) { st_rlx(&ctx->ctrl_h->heartbeat, now_ns()); }
+
+static int device_err_to_rc(uint32_t e) {
+  if (e == LK_DERR_NONE) return LK_OK;
+  if (e == LK_DERR_LEASE || e == LK_DERR_ABORT) return LK_ESTATE;
+  return LK_EDEVICE;
+}
+
+/* Inputs each op takes and whether it writes `out`. */
+static int op_inputs(uint32_t op) {
+  switch (op) {
+    case LK_OP_NOP: return 0;
+    case LK_OP_ADD_I32: return 2;
+    case LK_OP_HIST_U8: return 1;
+    case LK_OP_SUM_F32: return 1;
+    case LK_OP_GEMM64_F32: return 2;
+    case LK_OP_COPY_I32: return 1;
+    default: return -1;
+  }
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+/* Argument checks shared by lk_submit and the finite / trace paths. */
+static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in, void* out) {
+  if (!d) return LK_EINVAL;
+  int need = op_inputs(d->op);
+  if (need < 0 || n_in != need) return LK_EINVAL;
+  if (d->flags != 0) return LK_EINVAL;
+  if (d->n > (1ull << 40)) return LK_EINVAL;
+  const void* ins[2] = {in0, in1};
+  for (int i = 0; i < need; ++i) {
+    if (!aligned16(ins[i])) return LK_EINVAL;
+    if (d->n > 0 && !ins[i]) return LK_EINVAL;
+  }
+  if (!aligned16(out)) return LK_EINVAL;
+  switch (d->op) {
+    case LK_OP_NOP: break;
+    case LK_OP_SUM_F32:
+      if (!out) return LK_EINVAL;
+      break;
+    case LK_OP_HIST_U8:
+      if (!out) return LK_EINVAL;
+      if (d->n > 0x7fffffffull) return LK_EINVAL;   /* bins are int32 */
+      break;
+    case LK_OP_GEMM64_F32:
+      if (d->n > (1ull << 28)) return LK_EINVAL;
+      if (d->n > 0 && !out) return LK_EINVAL;
+      break;
+    default:
+      if (d->n > 0 && !out) return LK_EINVAL;
+  }
+  return LK_OK;
+}
+
+static void fill_slot(lk_slot* s, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
+                      void* out) {
+  s->cmd = cmd;
+  s->flags = d ? d->flags : 0;
+  s->n = d ? d->n : 0;
+  s->in0 = (uint64_t)(uintptr_t)in0;
+  s->in1 = (uint64_t)(uintptr_t)in1;
+  s->out = (uint64_t)(uintptr_t)out;
+  s->aux = d ? d->aux : 0;
+  s->t_pick = 0;
+}
+
+/* Returns the first device-side error, or 0. */
+static uint32_t dev_error(lk_ctx* ctx) { return ld_acq(&ctx->ctrl_h->first_error); }
+
+static bool ctx_alive(lk_ctx* ctx) {
+  if (!ctx->running.load(std::memory_order_acquire)) return false;
+  if (dev_error(ctx) != 0) return false;
+  if (ld_acq(&ctx->ctrl_h->exited) != 0) return false;
+  return true;
+}
+
+/* Ticket + publish.  Returns LK_OK / LK_EAGAIN. */
+static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
+                void* out, uint64_t* seq_out) {
+  Tail& tl = ctx->tail[c];
+  uint64_t t = tl.t.load(std::memory_order_relaxed);
+  for (;;) {
+    uint64_t done = ld_acq(&ctx->cword_h[c].done);
+    if (t - done >= ctx->R) return LK_EAGAIN;   /* slot t mod R still holds descriptor t-R+1 */
+    if (tl.t.compare_exchange_weak(t, t + 1, std::memory_order_acq_rel, std::memory_order_relaxed)) break;
+  }
+  lk_slot* s = &ctx->ring_h[(size_t)c * ctx->R + (t & (ctx->R - 1))];
+  fill_slot(s, cmd, d, in0, in1, out);
+  st_rel(&s->seq, t + 1);   /* publish: the device acquires seq, then reads the slot */
+  *seq_out = t + 1;
+  return LK_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Build the memory layout.  live: ring in host-mapped memory, else device. */
+static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_depth_override) {
+  if (!p || p->num_clusters < 1 || p->num_clusters > LK_MAX_CLUSTERS || !p->sms_per_cluster)
+    return LK_EINVAL;
+  lkb_props props;
+  int rc = lkb_props_get(p->device, &props);
+  if (rc != LK_OK) return rc;
+  if (!props.can_map_host || !props.cooperative) return LK_EDEVICE;
+  ctx->device = p->device;
+  ctx->sm_count = props.sm_count;
+  ctx->C = p->num_clusters;
+  ctx->sizes.assign(p->sms_per_cluster, p->sms_per_cluster + p->num_clusters);
+  ctx->cl_start.assign(ctx->C + 1, 0);
+  for (int c = 0; c < ctx->C; ++c) {
+    if (ctx->sizes[c] < 1) return LK_EINVAL;
+    ctx->cl_start[c + 1] = ctx->cl_start[c] + ctx->sizes[c];
+  }
+  ctx->total = ctx->cl_start[ctx->C];
+  if (ctx->total > props.sm_count || ctx->total > LK_MAX_CTAS) return LK_EINVAL;
+  if (p->smids) {
+    std::vector<int> seen(props.sm_count, 0);
+    for (int i = 0; i < ctx->total; ++i) {
+      if (p->smids[i] < 0 || p->smids[i] >= props.sm_count || seen[p->smids[i]]) return LK_EINVAL;
+      seen[p->smids[i]] = 1;
+    }
+    ctx->G = props.sm_count;   /* one CTA on every SM; those not listed return at boot */
+  } else {
+    ctx->G = ctx->total;
+  }
+  ctx->T = p->threads_per_cta ? p->threads_per_cta : 256;
+  if (ctx->T < 64 || ctx->T > 1024 || ctx->T % 32) return LK_EINVAL;
+  uint32_t R = ring_depth_override ? ring_depth_override : (p->ring_depth ? (uint32_t)p->ring_depth : 1024u);
+  if (R < 2 || (R & (R - 1)) || R > (1u << 24)) return LK_EINVAL;
+  ctx->R = R;
+  ctx->log_cap = p->exec_log_cap;
+  if (p->flags != 0) return LK_EINVAL;
+
+  /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] */
+  size_t off_ring = 0;
+  size_t ring_bytes = (size_t)ctx->C * R * sizeof(lk_slot);
+  size_t off_cw = live ? align_up(ring_bytes, LK_LINE) : 0;
+  size_t off_ctrl = align_up(off_cw + ctx->C * sizeof(lk_cword), LK_LINE);
+  size_t off_info = align_up(off_ctrl + sizeof(lk_ctrl), LK_LINE);
+  size_t mapped_bytes = align_up(off_info + ctx->G * sizeof(lk_cta_info), 4096);
+  rc = lkb_alloc_mapped(ctx->device, mapped_bytes, &ctx->mapped_h, &ctx->mapped_d);
+  if (rc != LK_OK) return rc;
+  char* mh = (char*)ctx->mapped_h;
+  char* md = (char*)ctx->mapped_d;
+  ctx->cword_h = (lk_cword*)(mh + off_cw);
+  ctx->ctrl_h = (lk_ctrl*)(mh + off_ctrl);
+  ctx->info_h = (lk_cta_info*)(mh + off_info);
+
+  /* device block: [ring (finite only)] dcl[C] cl_start pin_smid boot_smid boot_count log_count log */
+  size_t d_ring = 0;
+  size_t d_dcl = live ? 0 : align_up(ring_bytes, LK_LINE);
+  size_t d_start = align_up(d_dcl + ctx->C * sizeof(lk_dcluster), LK_LINE);
+  size_t d_pin = align_up(d_start + (ctx->C + 1) * sizeof(int32_t), LK_LINE);
+  size_t d_bsm = align_up(d_pin + (p->smids ? ctx->total : 0) * sizeof(int32_t), LK_LINE);
+  size_t d_bcnt = align_up(d_bsm + ctx->G * sizeof(int32_t), LK_LINE);
+  size_t d_lcnt = align_up(d_bcnt + sizeof(uint32_t), LK_LINE);
+  size_t d_log = align_up(d_lcnt + ctx->G * sizeof(uint64_t), LK_LINE);
+  size_t dev_bytes = align_up(d_log + (size_t)ctx->G * ctx->log_cap * sizeof(lk_exec_rec), 4096);
+  rc = lkb_alloc_device(ctx->device, dev_bytes, &ctx->dev_base);
+  if (rc != LK_OK) return rc;
+  char* db = (char*)ctx->dev_base;
+  /* control state starts at zero; the log records need no clearing */
+  rc = lkb_zero_device(ctx->device, db, d_log);
+  if (rc != LK_OK) return rc;
+  rc = lkb_copy_h2d(ctx->device, db + d_start, ctx->cl_start.data(), (ctx->C + 1) * sizeof(int32_t));
+  if (rc == LK_OK && p->smids)
+    rc = lkb_copy_h2d(ctx->device, db + d_pin, p->smids, ctx->total * sizeof(int32_t));
+  if (rc != LK_OK) return rc;
+
+  lk_kargs& a = ctx->args;
+  memset(&a, 0, sizeof a);
+  a.ring = (lk_slot*)(live ? (void*)(md + off_ring) : (void*)(db + d_ring));
+  a.cword = (lk_cword*)(md + off_cw);
+  a.ctrl = (lk_ctrl*)(md + off_ctrl);
+  a.info = (lk_cta_info*)(md + off_info);
+  a.dcl = (lk_dcluster*)(db + d_dcl);
+  a.cl_start = (int32_t*)(db + d_start);
+  a.pin_smid = p->smids ? (int32_t*)(db + d_pin) : nullptr;
+  a.boot_smid = (int32_t*)(db + d_bsm);
+  a.boot_count = (uint32_t*)(db + d_bcnt);
+  a.log_count = (uint64_t*)(db + d_lcnt);
+  a.log = ctx->log_cap ? (lk_exec_rec*)(db + d_log) : nullptr;
+  a.num_clusters = ctx->C;
+  a.grid = ctx->G;
+  a.total = ctx->total;
+  a.ring_mask = R - 1;
+  a.log_cap = ctx->log_cap;
+  a.flags = 0;
+  a.backoff_base_ns = p->backoff_base_ns;
+  a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;
+  a.lease_ns = p->idle_lease_ns ? p->idle_lease_ns : 10000000000ull;
+  a.boot_timeout_ns = p->boot_timeout_ns ? p->boot_timeout_ns : 10000000000ull;
+  if (live) ctx->ring_h = (lk_slot*)(mh + off_ring);
+
+  ctx->tail = new (std::nothrow) Tail[ctx->C];
+  if (!ctx->tail) return LK_ENOMEM;
+  return LK_OK;
+}
+
+static void teardown(lk_ctx* ctx) {
+  if (ctx->launch) lkb_release(ctx->launch);
+  if (ctx->dev_base) lkb_free_device(ctx->dev_base);
+  if (ctx->mapped_h) lkb_free_mapped(ctx->mapped_h);
+  delete[] ctx->tail;
+  delete ctx;
+}
+
+/* Wait for the kernel to return; on timeout set abort and wait again. */
+static int join_kernel(lk_ctx* ctx, uint64_t timeout_ns) {
+  uint64_t t0 = now_ns();
+  for (;;) {
+    int f = lkb_finished(ctx->launch);
+    if (f < 0) return LK_EDEVICE;
+    if (f == 1) return LK_OK;
+    if (now_ns() - t0 > timeout_ns) break;
+    std::this_thread::yield();
+  }
+  st_rel(&ctx->ctrl_h->abort, (uint64_t)1);
+  t0 = now_ns();
+  for (;;) {
+    int f = lkb_finished(ctx->launch);
+    if (f < 0) return LK_EDEVICE;
+    if (f == 1) return LK_ETIMEDOUT;   /* returned, but only after the abort */
+    if (now_ns() - t0 > timeout_ns + 2000000000ull) return LK_EBUSY;   /* still running */
+    std::this_thread::yield();
+  }
+}
+
+extern "C" {
+
+int lk_init(lk_ctx** out, const lk_init_params* p) {
+  if (!out || !p) return LK_EINVAL;
+  *out = nullptr;
+  lk_ctx* ctx = new (std::nothrow) lk_ctx();
+  if (!ctx) return LK_ENOMEM;
+  int rc = setup(ctx, p, true, 0);
+  if (rc != LK_OK) { teardown(ctx); return rc; }
+  beat(ctx);
+  rc = lkb_launch_kernel(ctx->device, &ctx->args, ctx->T, &ctx->launch);
+  if (rc != LK_OK) { ctx->launch = nullptr; teardown(ctx); return rc; }
+  /* boot: every CTA read %smid, joined its cluster and counted itself */
+  uint64_t t0 = now_ns();
+  uint64_t limit = ctx->args.boot_timeout_ns + 1000000000ull;
+  for (;;) {
+    uint32_t b = ld_acq(&ctx->ctrl_h->booted);
+    if (b >= (uint32_t)ctx->G) break;
+    uint32_t e = dev_error(ctx);
+    int f = lkb_finished(ctx->launch);
+    if (e != 0 || f != 0 || now_ns() - t0 > limit) {
+      int j = join_kernel(ctx, 0);
+      if (j == LK_EBUSY) { *out = nullptr; return LK_ETIMEDOUT; }   /* leaked: kernel still up */
+      teardown(ctx);
+      return (f < 0) ? LK_EDEVICE : (e == LK_DERR_BOOT || e == 0 ? LK_ETIMEDOUT : LK_EDEVICE);
+    }
+    std::this_thread::yield();
+  }
+  ctx->running.store(1, std::memory_order_release);
+  *out = ctx;
+  return LK_OK;
+}
+
+int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in, int n_in,
+              void* out, lk_handle* h) {
+  if (!ctx || !h || !d) return LK_EINVAL;
+  if (cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
+  if (n_in < 0 || n_in > 2 || (n_in > 0 && !in)) return LK_EINVAL;
+  const void* in0 = n_in > 0 ? in[0] : nullptr;
+  const void* in1 = n_in > 1 ? in[1] : nullptr;
+  int rc = validate(d, in0, in1, n_in, out);
+  if (rc != LK_OK) return rc;
+  if (!ctx_alive(ctx)) return LK_ESTATE;
+  beat(ctx);
+  uint64_t seq = 0;
+  rc = post(ctx, cluster, LK_CMD_WORK + d->op, d, in0, in1, out, &seq);
+  if (rc != LK_OK) return rc;
+  *h = ((uint64_t)cluster << 48) | seq;
+  return LK_OK;
+}
+
+static int poll_seq(lk_ctx* ctx, int c, uint64_t seq) {
+  if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+  uint32_t e = dev_error(ctx);
+  if (e != 0) {
+    /* the cluster may still have finished it before stopping */
+    if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+    return device_err_to_rc(e);
+  }
+  if (ld_acq(&ctx->ctrl_h->exited) != 0 || !ctx->running.load(std::memory_order_relaxed)) {
+    if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+    return LK_ESTATE;
+  }
+  return LK_PENDING;
+}
+
+static int decode(lk_ctx* ctx, lk_handle h, int* c, uint64_t* seq) {
+  uint64_t cl = h >> 48;
+  uint64_t s = h & kSeqMask;
+  if (cl >= (uint64_t)ctx->C || s == 0) return LK_EINVAL;
+  if (s > ctx->tail[cl].t.load(std::memory_order_acquire)) return LK_EINVAL;
+  *c = (int)cl;
+  *seq = s;
+  return LK_OK;
+}
+
+int lk_poll(lk_ctx* ctx, lk_handle h) {
+  if (!ctx) return LK_EINVAL;
+  int c;
+  uint64_t s;
+  if (decode(ctx, h, &c, &s) != LK_OK) return LK_EINVAL;
+  beat(ctx);
+  return poll_seq(ctx, c, s);
+}
+
+int lk_heartbeat(lk_ctx* ctx) {
+  if (!ctx) return LK_EINVAL;
+  beat(ctx);
+  return LK_OK;
+}
+
+int lk_wait(lk_ctx* ctx, lk_handle h, uint64_t timeout_ns) {
+  if (!ctx) return LK_EINVAL;
+  int c;
+  uint64_t s;
+  if (decode(ctx, h, &c, &s) != LK_OK) return LK_EINVAL;
+  if (ld_acq(&ctx->cword_h[c].done) >= s) return LK_OK;
+  beat(ctx);
+  uint64_t t0 = now_ns();
+  uint64_t last_beat = t0;
+  for (uint32_t i = 0;; ++i) {
+    if (ld_acq(&ctx->cword_h[c].done) >= s) return LK_OK;
+    if ((i & 255) == 255) {
+      int rc = poll_seq(ctx, c, s);
+      if (rc != LK_PENDING) return rc;
+      uint64_t t = now_ns();
+      if (t - t0 > timeout_ns) return LK_ETIMEDOUT;
+      if (t - last_beat > 1000000ull) { beat(ctx); last_beat = t; }
+    }
+  }
+}
+
+int lk_sync(lk_ctx* ctx, uint64_t timeout_ns) {
+  if (!ctx) return LK_EINVAL;
+  uint64_t t0 = now_ns();
+  for (int c = 0; c < ctx->C; ++c) {
+    uint64_t s = ctx->tail[c].t.load(std::memory_order_acquire);
+    if (s == 0) continue;
+    uint64_t spent = now_ns() - t0;
+    int rc = lk_wait(ctx, ((uint64_t)c << 48) | s, spent >= timeout_ns ? 0 : timeout_ns - spent);
+    if (rc != LK_OK) return rc;
+  }
+  return LK_OK;
+}
+
+int lk_dispose(lk_ctx* ctx, uint64_t timeout_ns) { return lk_dispose_timed(ctx, timeout_ns, nullptr); }
+
+int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms) {
+  if (kernel_ms) *kernel_ms = -1.f;
+  if (!ctx) return LK_EINVAL;
+  uint64_t t0 = now_ns();
+  if (ctx->launch && ctx_alive(ctx)) {
+    beat(ctx);
+    for (int c = 0; c < ctx->C; ++c) {
+      uint64_t seq;
+      for (;;) {
+        int rc = post(ctx, c, LK_CMD_EXIT, nullptr, nullptr, nullptr, nullptr, &seq);
+        if (rc == LK_OK) break;
+        if (!ctx_alive(ctx) || now_ns() - t0 > timeout_ns) break;
+        std::this_thread::yield();
+      }
+    }
+  }
+  ctx->running.store(0, std::memory_order_release);
+  int rc = LK_OK;
+  if (ctx->launch) {
+    uint64_t spent = now_ns() - t0;
+    rc = join_kernel(ctx, spent >= timeout_ns ? 0 : timeout_ns - spent);
+    if (rc == LK_EBUSY) return LK_EBUSY;   /* kernel still running: keep everything */
+    if (kernel_ms) *kernel_ms = lkb_elapsed_ms(ctx->launch);
+  }
+  uint32_t e = dev_error(ctx);
+  teardown(ctx);
+  if (rc != LK_OK) return rc;
+  if (e != 0 && e != LK_DERR_LEASE) return LK_EDEVICE;
+  return LK_OK;
+}
+
+int lk_cluster_info(lk_ctx* ctx, int cluster, int* smids, int cap) {
+  if (!ctx || cluster < 0 || cluster >= ctx->C || cap < 0 || (cap > 0 && !smids)) return LK_EINVAL;
+  int size = ctx->sizes[cluster];
+  for (int g = 0; g < ctx->G; ++g) {
+    lk_cta_info inf = ctx->info_h[g];
+    if (inf.cluster == cluster && inf.rank >= 0 && inf.rank < size && inf.rank < cap) smids[inf.rank] = inf.smid;
+  }
+  return size;
+}
+
+int lk_status(lk_ctx* ctx, int cluster) {
+  if (!ctx || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
+  return (int)ld_acq(&ctx->cword_h[cluster].status);
+}
+
+int lk_device_error(lk_ctx* ctx) {
+  if (!ctx) return LK_EINVAL;
+  return (int)dev_error(ctx);
+}
+
+int lk_num_sms(lk_ctx* ctx) { return ctx ? ctx->sm_count : LK_EINVAL; }
+int lk_num_ctas(lk_ctx* ctx) { return ctx ? ctx->total : LK_EINVAL; }
+
+/* Gather the per-CTA logs (device memory) into caller order. */
+static int read_log(lk_ctx* ctx, lk_exec_rec* buf, size_t cap, size_t* n, uint64_t* dropped) {
+  *n = 0;
+  if (dropped) *dropped = 0;
+  if (!ctx->log_cap || !ctx->args.log) return LK_OK;
+  std::vector<uint64_t> counts(ctx->G);
+  int rc = lkb_copy_d2h(ctx->device, counts.data(), ctx->args.log_count, ctx->G * sizeof(uint64_t));
+  if (rc != LK_OK) return rc;
+  std::vector<lk_exec_rec> tmp((size_t)ctx->log_cap);
+  uint64_t drop = 0;
+  size_t w = 0;
+  for (int g = 0; g < ctx->G; ++g) {
+    uint64_t cnt = counts[g];
+    if (cnt == 0) continue;
+    uint64_t keep = cnt < ctx->log_cap ? cnt : ctx->log_cap;
+    drop += cnt - keep;
+    rc = lkb_copy_d2h(ctx->device, tmp.data(), ctx->args.log + (size_t)g * ctx->log_cap,
+                      (size_t)ctx->log_cap * sizeof(lk_exec_rec));
+    if (rc != LK_OK) return rc;
+    uint64_t first = cnt - keep;
+    for (uint64_t k = first; k < cnt && w < cap; ++k) buf[w++] = tmp[k % ctx->log_cap];
+  }
+  *n = w;
+  if (dropped) *dropped = drop;
+  return LK_OK;
+}
+
+int lk_exec_log(lk_ctx* ctx, lk_exec_rec* buf, size_t cap, size_t* n, uint64_t* dropped) {
+  if (!ctx || !n || (cap > 0 && !buf)) return LK_EINVAL;
+  return read_log(ctx, buf, cap, n, dropped);
+}
+
+const char* lk_strerror(int code) {
+  switch (code) {
+    case LK_OK: return "LK_OK";
+    case LK_PENDING: return "LK_PENDING";
+    case LK_EINVAL: return "LK_EINVAL: invalid argument";
+    case LK_EAGAIN: return "LK_EAGAIN: cluster mailbox ring full";
+    case LK_ETIMEDOUT: return "LK_ETIMEDOUT: deadline passed";
+    case LK_EDEVICE: return "LK_EDEVICE: device-side or CUDA error";
+    case LK_ESTATE: return "LK_ESTATE: context not running";
+    case LK_ENOMEM: return "LK_ENOMEM: allocation failed";
+    case LK_EBUSY: return "LK_EBUSY: kernel still running; context kept";
+    default: return "LK_?: unknown code";
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+int lk_run_finite(const lk_init_params* p, const lk_desc* descs, const int* cluster_of,
+                  const void* const* in0, const void* const* in1, void* const* out, size_t count,
+                  float* elapsed_ms, lk_exec_rec* log_out, size_t log_cap, size_t* log_n) {
+  if (!p || (count > 0 && (!descs || !cluster_of))) return LK_EINVAL;
+  if (log_n) *log_n = 0;
+  std::vector<uint64_t> per(p->num_clusters > 0 ? p->num_clusters : 1, 0);
+  for (size_t i = 0; i < count; ++i) {
+    if (cluster_of[i] < 0 || cluster_of[i] >= p->num_clusters) return LK_EINVAL;
+    const lk_desc* d = &descs[i];
+    int rc = validate(d, in0 ? in0[i] : nullptr, in1 ? in1[i] : nullptr, op_inputs(d->op),
+                      out ? out[i] : nullptr);
+    if (rc != LK_OK) return rc;
+    per[cluster_of[i]]++;
+  }
+  uint64_t mx = 0;
+  for (uint64_t v : per) mx = std::max(mx, v);
+  uint32_t R = 2;
+  while (R < mx + 1) R <<= 1;
+  lk_ctx* ctx = new (std::nothrow) lk_ctx();
+  if (!ctx) return LK_ENOMEM;
+  ctx->finite = true;
+  int rc = setup(ctx, p, false, R);
+  if (rc != LK_OK) { teardown(ctx); return rc; }
+  /* fill the ring on the host, then copy it into device memory */
+  std::vector<lk_slot> ring((size_t)ctx->C * R);
+  memset(ring.data(), 0, ring.size() * sizeof(lk_slot));
+  std::vector<uint64_t> t(ctx->C, 0);
+  for (size_t i = 0; i < count; ++i) {
+    int c = cluster_of[i];
+    lk_slot* s = &ring[(size_t)c * R + t[c]];
+    fill_slot(s, LK_CMD_WORK + descs[i].op, &descs[i], in0 ? in0[i] : nullptr,
+              in1 ? in1[i] : nullptr, out ? out[i] : nullptr);
+    s->seq = ++t[c];
+  }
+  for (int c = 0; c < ctx->C; ++c) {
+    lk_slot* s = &ring[(size_t)c * R + t[c]];
+    fill_slot(s, LK_CMD_EXIT, nullptr, nullptr, nullptr, nullptr);
+    s->seq = ++t[c];
+  }
+  rc = lkb_copy_h2d(ctx->device, ctx->args.ring, ring.data(), ring.size() * sizeof(lk_slot));
+  if (rc != LK_OK) { teardown(ctx); return rc; }
+  beat(ctx);
+  rc = lkb_launch_kernel(ctx->device, &ctx->args, ctx->T, &ctx->launch);
+  if (rc != LK_OK) { ctx->launch = nullptr; teardown(ctx); return rc; }
+  /* bounded: the lease ends an idle kernel; the abort ends a stuck one */
+  uint64_t limit = ctx->args.lease_ns + ctx->args.boot_timeout_ns;
+  rc = join_kernel(ctx, limit);
+  if (rc == LK_EBUSY) return LK_ETIMEDOUT;   /* leaked: kernel still up */
+  if (rc == LK_OK && elapsed_ms) *elapsed_ms = lkb_elapsed_ms(ctx->launch);
+  if (rc == LK_OK && log_out && log_n) rc = read_log(ctx, log_out, log_cap, log_n, nullptr);
+  uint32_t e = dev_error(ctx);
+  teardown(ctx);
+  if (rc != LK_OK) return rc;
+  return e ? LK_EDEVICE : LK_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+static void pin_to(int cpu) {
+#ifdef __linux__
+  if (cpu < 0) return;
+  int n = (int)std::thread::hardware_concurrency();
+  if (n <= 0) return;
+  cpu_set_t set;
+  CPU_ZERO(&set);
+  CPU_SET(cpu % n, &set);
+  pthread_setaffinity_np(pthread_self(), sizeof set, &set);
+#else
+  (void)cpu;
+#endif
+}
+
+int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_threads,
+                 int mode, int pin_cpu_base, uint64_t timeout_ns, lk_trace_result* res) {
+  if (!ctx || (count > 0 && (!items || !res)) || n_threads < 1 || n_threads > 256) return LK_EINVAL;
+  if (mode < LK_TRACE_OPEN || mode > LK_TRACE_E2E) return LK_EINVAL;
+  const bool closed_loop = mode != LK_TRACE_OPEN;
+  const bool e2e = mode == LK_TRACE_E2E;
+  for (size_t i = 0; i < count; ++i) {
+    const lk_trace_item& it = items[i];
+    if (it.cluster < 0 || it.cluster >= ctx->C) return LK_EINVAL;
+    lk_desc d{it.op, 0, it.n, 0};
+    int rc = validate(&d, it.in0, it.in1, op_inputs(it.op), it.out);
+    if (rc != LK_OK) return rc;
+    res[i] = lk_trace_result{0, 0, LK_PENDING, -1};
+  }
+  if (!ctx_alive(ctx)) return LK_ESTATE;
+  /* per thread: its items in arrival order */
+  std::vector<std::vector<size_t>> mine(n_threads);
+  for (size_t i = 0; i < count; ++i) mine[items[i].cluster % n_threads].push_back(i);
+  for (auto& v : mine)
+    std::stable_sort(v.begin(), v.end(), [&](size_t a, size_t b) { return items[a].t_arrival_ns < items[b].t_arrival_ns; });
+  std::atomic<int> ready{0};
+  std::atomic<uint64_t> start{0};
+  std::atomic<int> first_err{0};
+
+  auto worker = [&](int w) {
+    pin_to(pin_cpu_base >= 0 ? pin_cpu_base + w : -1);
+    const std::vector<size_t>& v = mine[w];
+    void* stream = nullptr;
+    if (e2e && lkb_stream_create(ctx->device, &stream) != LK_OK) stream = nullptr;
+    ready.fetch_add(1);
+    uint64_t t0;
+    while ((t0 = start.load(std::memory_order_acquire)) == 0) {}
+    uint64_t deadline = t0 + timeout_ns;
+    /* pending handles in submission order per cluster (completion is FIFO per cluster) */
+    std::vector<std::vector<std::pair<uint64_t, size_t>>> pend(ctx->C);
+    std::vector<size_t> head(ctx->C, 0);
+    size_t next = 0, finished = 0;
+    while (finished < v.size()) {
+      uint64_t now = now_ns();
+      if (now > deadline) {
+        for (size_t k = 0; k < v.size(); ++k)
+          if (res[v[k]].status == LK_PENDING) res[v[k]].status = LK_ETIMEDOUT;
+        int z = 0;
+        first_err.compare_exchange_strong(z, LK_ETIMEDOUT);
+        if (stream) lkb_stream_destroy(stream);
+        return;
+      }
+      bool can_release = next < v.size() && now >= t0 + items[v[next]].t_arrival_ns &&
+                         (!closed_loop || finished == next);
+      if (can_release) {
+        const lk_trace_item& it = items[v[next]];
+        lk_desc d{it.op, 0, it.n, 0};
+        uint64_t ts = now_ns();
+        uint64_t seq = 0;
+        int rc = LK_OK;
+        if (e2e) {
+          /* Copyin (Sec. III): inputs from pinned host memory, on this thread's stream */
+          if (!stream) rc = LK_EDEVICE;
+          if (rc == LK_OK && it.in0_bytes && it.h_in0)
+            rc = lkb_memcpy_async(stream, (void*)it.in0, it.h_in0, it.in0_bytes, 1);
+          if (rc == LK_OK && it.in1_bytes && it.h_in1)
+            rc = lkb_memcpy_async(stream, (void*)it.in1, it.h_in1, it.in1_bytes, 1);
+          if (rc == LK_OK) rc = lkb_stream_sync(stream);
+        }
+        if (rc == LK_OK) rc = post(ctx, it.cluster, LK_CMD_WORK + it.op, &d, it.in0, it.in1, it.out, &seq);
+        while (rc == LK_EAGAIN && e2e) rc = post(ctx, it.cluster, LK_CMD_WORK + it.op, &d, it.in0, it.in1, it.out, &seq);
+        if (rc == LK_OK) {
+          res[v[next]].t_submit_ns = ts - t0;
+          res[v[next]].thread = w;
+          pend[it.cluster].push_back({seq, v[next]});
+          ++next;
+        } else if (rc != LK_EAGAIN) {
+          res[v[next]].status = rc;
+          ++next;
+          ++finished;
+        }
+      }
+      /* completions */
+      for (int c = w; c < ctx->C; c += n_threads) {
+        auto& pq = pend[c];
+        if (head[c] == pq.size()) continue;
+        uint64_t done = ld_acq(&ctx->cword_h[c].done);
+        if (done < pq[head[c]].first) {
+          if (dev_error(ctx) != 0 || ld_acq(&ctx->ctrl_h->exited) != 0) {
+            int rc = device_err_to_rc(dev_error(ctx));
+            if (rc == LK_OK) rc = LK_ESTATE;
+            for (size_t k = head[c]; k < pq.size(); ++k) res[pq[k].second].status = rc;
+            finished += pq.size() - head[c];
+            head[c] = pq.size();
+            int z = 0;
+            first_err.compare_exchange_strong(z, rc);
+          }
+          continue;
+        }
+        uint64_t tc = now_ns() - t0;
+        while (head[c] < pq.size() && pq[head[c]].first <= done) {
+          const size_t idx = pq[head[c]].second;
+          int st = LK_OK;
+          if (e2e && items[idx].out_bytes && items[idx].h_out) {
+            /* Copyout (Sec. III) */
+            st = lkb_memcpy_async(stream, items[idx].h_out, items[idx].out, items[idx].out_bytes, 0);
+            if (st == LK_OK) st = lkb_stream_sync(stream);
+            tc = now_ns() - t0;
+          }
+          res[idx].t_complete_ns = tc;
+          res[idx].status = st;
+          ++head[c];
+          ++finished;
+        }
+      }
+      if ((next & 1023) == 0) beat(ctx);
+    }
+    if (stream) lkb_stream_destroy(stream);
+  };
+  std::vector<std::thread> th;
+  for (int w = 0; w < n_threads; ++w) th.emplace_back(worker, w);
+  while (ready.load() < n_threads) std::this_thread::yield();
+  start.store(now_ns(), std::memory_order_release);
+  for (auto& x : th) x.join();
+  beat(ctx);
+  int e = first_err.load();
+  for (size_t i = 0; i < count && e == 0; ++i)
+    if (res[i].status != LK_OK) e = res[i].status;
+  return e;
+}
+
+}  // extern "C"

@@ -1,0 +1,329 @@
+"""Python binding of the LightKernel C ABI (include/lk.h).
+
+Argument marshalling only: every step of the dispatch path and every work body
+runs in liblk.so (host runtime + persistent CUDA kernel).  There is no Python
+or CPU fallback: if the library is missing, loading fails with an error.
+
+Functions keep the C names (lk_init, lk_submit, lk_poll, lk_wait, lk_sync,
+lk_dispose, ...).  Device pointers may be given as ints or as objects with a
+``data_ptr()`` method (torch tensors).  Failures raise ``LkError`` carrying the
+C return code, except where a code is an expected answer (lk_poll's
+LK_PENDING, lk_wait's LK_ETIMEDOUT, lk_submit's LK_EAGAIN), which are returned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# ---- constants (include/lk.h) ------------------------------------------------
+LK_OK, LK_PENDING = 0, 1
+LK_EINVAL, LK_EAGAIN, LK_ETIMEDOUT, LK_EDEVICE, LK_ESTATE, LK_ENOMEM, LK_EBUSY = -1, -2, -3, -4, -5, -6, -7
+LK_ST_INIT, LK_ST_FINISHED, LK_ST_WORKING, LK_ST_NOP, LK_ST_EXITED, LK_ST_ERROR = 0, 1, 2, 4, 8, 32
+LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
+LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
+LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING = range(7)
+OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
+             LK_OP_COPY_I32: 1}
+OP_NAMES = {LK_OP_NOP: "nop", LK_OP_ADD_I32: "add_i32", LK_OP_HIST_U8: "hist_u8", LK_OP_SUM_F32: "sum_f32",
+            LK_OP_GEMM64_F32: "gemm64_f32", LK_OP_COPY_I32: "copy_i32"}
+
+
+class LkError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+# ---- structures ----------------------------------------------------------------
+class lk_init_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("num_clusters", ctypes.c_int),
+                ("sms_per_cluster", ctypes.POINTER(ctypes.c_int)), ("smids", ctypes.POINTER(ctypes.c_int)),
+                ("threads_per_cta", ctypes.c_int), ("ring_depth", ctypes.c_int),
+                ("backoff_base_ns", ctypes.c_uint64), ("backoff_cap_ns", ctypes.c_uint64),
+                ("idle_lease_ns", ctypes.c_uint64), ("boot_timeout_ns", ctypes.c_uint64),
+                ("exec_log_cap", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class lk_desc(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("aux", ctypes.c_uint64)]
+
+
+EXEC_REC_DTYPE = np.dtype([("seq", "<u8"), ("cluster", "<u4"), ("rank", "<u4"), ("smid", "<u4"), ("op", "<u4"),
+                           ("order", "<u8"), ("t_pick_ns", "<u8"), ("t_start_ns", "<u8"), ("t_end_ns", "<u8"),
+                           ("t_done_ns", "<u8")])
+assert EXEC_REC_DTYPE.itemsize == 64
+
+TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op", "<u4"), ("n", "<u8"),
+                             ("in0", "<u8"), ("in1", "<u8"), ("out", "<u8"), ("h_in0", "<u8"), ("h_in1", "<u8"),
+                             ("h_out", "<u8"), ("in0_bytes", "<u8"), ("in1_bytes", "<u8"), ("out_bytes", "<u8")])
+LK_TRACE_OPEN, LK_TRACE_CLOSED, LK_TRACE_E2E = 0, 1, 2
+TRACE_RES_DTYPE = np.dtype([("t_submit_ns", "<u8"), ("t_complete_ns", "<u8"), ("status", "<i4"),
+                            ("thread", "<i4")])
+assert TRACE_ITEM_DTYPE.itemsize == 96 and TRACE_RES_DTYPE.itemsize == 24
+
+# ---- library loading -------------------------------------------------------------
+_libs: dict = {}
+_lock = threading.Lock()
+
+
+def library_path(fake: bool = False) -> str:
+    return _build.FAKE if fake else _build.LIB
+
+
+def load(fake: bool = False) -> ctypes.CDLL:
+    """Load liblk.so (or the fake-device test build).  Raises if it is missing."""
+    with _lock:
+        if fake in _libs:
+            return _libs[fake]
+        path = library_path(fake)
+        if not os.path.exists(path):
+            raise OSError(f"{path} is missing: run paper_2310_01212_gb300.build.build() "
+                          "(no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        P, I, U64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+        sig = {
+            "lk_init": (I, [ctypes.POINTER(P), ctypes.POINTER(lk_init_params)]),
+            "lk_submit": (I, [P, I, ctypes.POINTER(lk_desc), ctypes.POINTER(P), I, P, ctypes.POINTER(U64)]),
+            "lk_poll": (I, [P, U64]),
+            "lk_wait": (I, [P, U64, U64]),
+            "lk_sync": (I, [P, U64]),
+            "lk_heartbeat": (I, [P]),
+            "lk_dispose": (I, [P, U64]),
+            "lk_dispose_timed": (I, [P, U64, ctypes.POINTER(ctypes.c_float)]),
+            "lk_cluster_info": (I, [P, I, ctypes.POINTER(I), I]),
+            "lk_status": (I, [P, I]),
+            "lk_device_error": (I, [P]),
+            "lk_num_sms": (I, [P]),
+            "lk_num_ctas": (I, [P]),
+            "lk_exec_log": (I, [P, P, SZ, ctypes.POINTER(SZ), ctypes.POINTER(U64)]),
+            "lk_strerror": (ctypes.c_char_p, [I]),
+            "lk_run_finite": (I, [ctypes.POINTER(lk_init_params), ctypes.POINTER(lk_desc), ctypes.POINTER(I),
+                                  ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), SZ,
+                                  ctypes.POINTER(ctypes.c_float), P, SZ, ctypes.POINTER(SZ)]),
+            "lk_run_trace": (I, [P, P, SZ, I, I, I, U64, P]),
+            "lk_baseline_run_trace": (I, [I, P, SZ, I, ctypes.POINTER(I), I, I, I, I, P]),
+            "lk_pingpong": (I, [I, I, ctypes.POINTER(U64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _libs[fake] = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().lk_strerror(code).decode()
+    except OSError:
+        return load(True).lk_strerror(code).decode()
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
+                backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
+                boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0):
+    """lk_init_params plus the arrays it points to (kept alive by the tuple)."""
+    sz = (ctypes.c_int * len(sizes))(*sizes)
+    sm = None if smids is None else (ctypes.c_int * len(smids))(*smids)
+    p = lk_init_params(device, len(sizes), sz, sm, threads_per_cta, ring_depth, backoff_base_ns, backoff_cap_ns,
+                       idle_lease_ns, boot_timeout_ns, exec_log_cap, 0)
+    return p, (sz, sm)
+
+
+# ---- the C ABI, one function each ---------------------------------------------------
+class Context:
+    """A running LightKernel context (owns an lk_ctx*)."""
+
+    def __init__(self, sizes, fake: bool = False, **kw):
+        self.kernel_ms = -1.0
+        self.lib = load(fake)
+        self.sizes = list(sizes)
+        self._params, self._keep = make_params(self.sizes, **kw)
+        self.ptr = ctypes.c_void_p()
+        rc = self.lib.lk_init(ctypes.byref(self.ptr), ctypes.byref(self._params))
+        if rc != LK_OK:
+            self.ptr = None
+            raise LkError(rc, "lk_init")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.dispose()
+
+    def __del__(self):
+        try:
+            self.dispose()
+        except Exception:
+            pass
+
+    def dispose(self, timeout_ns: int = 20_000_000_000) -> int:
+        if not self.ptr:
+            return LK_OK
+        ms = ctypes.c_float(-1.0)
+        rc = self.lib.lk_dispose_timed(self.ptr, timeout_ns, ctypes.byref(ms))
+        if rc != LK_EBUSY:
+            self.ptr = None
+            self.kernel_ms = ms.value
+        return rc
+
+
+def lk_init(sizes, fake: bool = False, **kw) -> Context:
+    return Context(sizes, fake=fake, **kw)
+
+
+def lk_submit(ctx: Context, cluster: int, op: int, n: int, ins=(), out=None, aux: int = 0) -> int | None:
+    """Returns the handle, or None if the cluster's ring is full (LK_EAGAIN)."""
+    d = lk_desc(op, 0, n, aux)
+    arr = (ctypes.c_void_p * max(1, len(ins)))(*[_ptr(i) for i in ins]) if ins else None
+    h = ctypes.c_uint64()
+    rc = ctx.lib.lk_submit(ctx.ptr, cluster, ctypes.byref(d), arr, len(ins), _ptr(out), ctypes.byref(h))
+    if rc == LK_EAGAIN:
+        return None
+    if rc != LK_OK:
+        raise LkError(rc, "lk_submit")
+    return h.value
+
+
+def lk_poll(ctx: Context, h: int) -> int:
+    rc = ctx.lib.lk_poll(ctx.ptr, h)
+    if rc < 0:
+        raise LkError(rc, "lk_poll")
+    return rc
+
+
+def lk_wait(ctx: Context, h: int, timeout_ns: int = 10_000_000_000) -> int:
+    rc = ctx.lib.lk_wait(ctx.ptr, h, timeout_ns)
+    if rc not in (LK_OK, LK_ETIMEDOUT):
+        raise LkError(rc, "lk_wait")
+    return rc
+
+
+def lk_sync(ctx: Context, timeout_ns: int = 10_000_000_000) -> int:
+    rc = ctx.lib.lk_sync(ctx.ptr, timeout_ns)
+    if rc not in (LK_OK, LK_ETIMEDOUT):
+        raise LkError(rc, "lk_sync")
+    return rc
+
+
+def lk_heartbeat(ctx: Context) -> int:
+    return ctx.lib.lk_heartbeat(ctx.ptr)
+
+
+def lk_dispose(ctx: Context, timeout_ns: int = 20_000_000_000) -> int:
+    return ctx.dispose(timeout_ns)
+
+
+def lk_cluster_info(ctx: Context, cluster: int) -> list:
+    cap = 1024
+    buf = (ctypes.c_int * cap)()
+    n = ctx.lib.lk_cluster_info(ctx.ptr, cluster, buf, cap)
+    if n < 0:
+        raise LkError(n, "lk_cluster_info")
+    return list(buf[:n])
+
+
+def lk_status(ctx: Context, cluster: int) -> int:
+    rc = ctx.lib.lk_status(ctx.ptr, cluster)
+    if rc < 0:
+        raise LkError(rc, "lk_status")
+    return rc
+
+
+def lk_device_error(ctx: Context) -> int:
+    return ctx.lib.lk_device_error(ctx.ptr)
+
+
+def lk_num_sms(ctx: Context) -> int:
+    return ctx.lib.lk_num_sms(ctx.ptr)
+
+
+def lk_num_ctas(ctx: Context) -> int:
+    return ctx.lib.lk_num_ctas(ctx.ptr)
+
+
+def lk_exec_log(ctx: Context, cap: int | None = None):
+    """Execution log as a numpy structured array (EXEC_REC_DTYPE) and the dropped count."""
+    if cap is None:
+        cap = max(1, sum(ctx.sizes) * max(1, ctx._params.exec_log_cap))
+    buf = np.zeros(cap, dtype=EXEC_REC_DTYPE)
+    n = ctypes.c_size_t()
+    dropped = ctypes.c_uint64()
+    rc = ctx.lib.lk_exec_log(ctx.ptr, buf.ctypes.data, cap, ctypes.byref(n), ctypes.byref(dropped))
+    if rc != LK_OK:
+        raise LkError(rc, "lk_exec_log")
+    return buf[: n.value], dropped.value
+
+
+def lk_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def lk_run_finite(sizes, descs, cluster_of, in0=None, in1=None, out=None, log_cap: int = 0, fake: bool = False,
+                  **kw):
+    """Finite mode: one launch runs the listed descriptors and returns.
+    descs: list of (op, n).  Returns (elapsed_ms, exec log array)."""
+    lib = load(fake)
+    p, keep = make_params(sizes, exec_log_cap=kw.pop("exec_log_cap", max(1, len(descs))), **kw)
+    cnt = len(descs)
+    D = (lk_desc * max(1, cnt))(*[lk_desc(op, 0, n, 0) for op, n in descs])
+    C = (ctypes.c_int * max(1, cnt))(*cluster_of)
+
+    def arr(xs):
+        if xs is None:
+            return None
+        return (ctypes.c_void_p * max(1, cnt))(*[_ptr(x) for x in xs])
+
+    ms = ctypes.c_float(-1.0)
+    logbuf = np.zeros(max(1, log_cap), dtype=EXEC_REC_DTYPE)
+    ln = ctypes.c_size_t()
+    rc = lib.lk_run_finite(ctypes.byref(p), D, C, arr(in0), arr(in1), arr(out), cnt, ctypes.byref(ms),
+                           logbuf.ctypes.data if log_cap else None, log_cap, ctypes.byref(ln))
+    if rc != LK_OK:
+        raise LkError(rc, "lk_run_finite")
+    return ms.value, logbuf[: ln.value]
+
+
+def lk_run_trace(ctx: Context, items: np.ndarray, n_threads: int, closed_loop: bool = False, pin_cpu_base: int = -1,
+                 timeout_ns: int = 120_000_000_000, mode: int | None = None):
+    items = np.ascontiguousarray(items, dtype=TRACE_ITEM_DTYPE)
+    res = np.zeros(items.size, dtype=TRACE_RES_DTYPE)
+    if mode is None:
+        mode = LK_TRACE_CLOSED if closed_loop else LK_TRACE_OPEN
+    rc = ctx.lib.lk_run_trace(ctx.ptr, items.ctypes.data, items.size, n_threads, mode, pin_cpu_base,
+                              timeout_ns, res.ctypes.data)
+    return rc, res
+
+
+def lk_baseline_run_trace(items: np.ndarray, ctas_of_slot, threads: int, n_threads: int, device: int = 0,
+                          pin_cpu_base: int = -1, mode: int = LK_TRACE_CLOSED):
+    lib = load()
+    items = np.ascontiguousarray(items, dtype=TRACE_ITEM_DTYPE)
+    res = np.zeros(items.size, dtype=TRACE_RES_DTYPE)
+    cs = (ctypes.c_int * len(ctas_of_slot))(*ctas_of_slot)
+    rc = lib.lk_baseline_run_trace(device, items.ctypes.data, items.size, len(ctas_of_slot), cs, threads,
+                                   n_threads, mode, pin_cpu_base, res.ctypes.data)
+    return rc, res
+
+
+def lk_pingpong(iters: int, device: int = 0) -> np.ndarray:
+    lib = load()
+    buf = (ctypes.c_uint64 * iters)()
+    rc = lib.lk_pingpong(device, iters, buf)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_pingpong")
+    return np.frombuffer(buf, dtype=np.uint64).copy()

@@ -1,0 +1,158 @@
+"""GPU parity of every work body against the oracle, through the C ABI:
+bit-exact for integer work, within 1e-4 * sum|x| of binary64 for float32.
+Sizes span several CTAs' shares, ragged tails and the empty case."""
+import numpy as np
+import pytest
+
+from gpu_util import gemm_ok, host, need_gpu, sum_ok, to_dev
+from paper_2310_01212_gb300 import lk, synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 3, 4, 5, 17, 1023, 4096, 65536 + 7, (1 << 20) + 13]
+
+
+@pytest.fixture(scope="module")
+def torch_ready(native_built):
+    return need_gpu()
+
+
+@pytest.mark.parametrize("S", [1, 2, 37])
+def test_add_copy_bit_exact(torch_ready, oracle_lib, S):
+    torch = torch_ready
+    cases = []
+    for i, n in enumerate(SIZES):
+        a = synth.int32_uniform(11, 2 * i, n, -(2**31), 2**31 - 1)
+        b = synth.int32_uniform(11, 2 * i + 1, n, -(2**31), 2**31 - 1)
+        cases.append((n, a, b, to_dev(a), to_dev(b), torch.zeros(max(n, 1), dtype=torch.int32, device="cuda"),
+                      torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")))
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+        hs = []
+        for n, a, b, da, db, oa, oc in cases:
+            hs.append(lk.lk_submit(c, 0, lk.LK_OP_ADD_I32, n, (da, db), oa))
+            hs.append(lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, n, (da,), oc))
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    for n, a, b, da, db, oa, oc in cases:
+        assert np.array_equal(host(oa)[:n], oracle_lib.add_i32(a, b)), n
+        assert np.array_equal(host(oc)[:n], oracle_lib.copy_i32(a)), n
+
+
+@pytest.mark.parametrize("S", [1, 2, 37])
+def test_hist_bit_exact(torch_ready, oracle_lib, S):
+    torch = torch_ready
+    cases = []
+    for i, n in enumerate(SIZES):
+        x = synth.bytes_uniform(12, i, n)
+        cases.append((x, to_dev(x) if n else torch.zeros(16, dtype=torch.uint8, device="cuda"),
+                      torch.full((256,), -1, dtype=torch.int32, device="cuda")))
+    # value v appears v+1 times (shuffled): every bin distinct
+    x = np.concatenate([np.full(v + 1, v, np.uint8) for v in range(256)])
+    x = x[synth.permutation(12, 99, x.size)]
+    cases.append((x, to_dev(x), torch.full((256,), -1, dtype=torch.int32, device="cuda")))
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+        hs = [lk.lk_submit(c, 0, lk.LK_OP_HIST_U8, x.size, (dx,), out) for x, dx, out in cases]
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    for x, dx, out in cases:
+        assert np.array_equal(host(out).astype(np.int64), oracle_lib.hist_u8(x)), x.size
+
+
+@pytest.mark.parametrize("S", [1, 2, 37])
+def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S):
+    torch = torch_ready
+    cases = []
+    for i, n in enumerate(SIZES):
+        x = synth.normal_f32(13, i, n)
+        cases.append((x, to_dev(x) if n else torch.zeros(4, device="cuda"), torch.full((4,), 7.0, device="cuda"), False))
+    # integer-valued floats whose partial sums stay below 2^24: every order is exact
+    for n in (100003, 65536):
+        x = ((np.arange(n) % 7) - 3).astype(np.float32)
+        cases.append((x, to_dev(x), torch.full((4,), 7.0, device="cuda"), True))
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+        hs = [lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, x.size, (dx,), out) for x, dx, out, _ in cases]
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    for x, dx, out, exact in cases:
+        got = float(host(out)[0])
+        if exact:
+            assert got == oracle_lib.sum_f32(x)
+        else:
+            assert sum_ok(got, x, oracle_lib), (x.size, got, oracle_lib.sum_f32(x))
+
+
+@pytest.mark.parametrize("S", [1, 2, 37])
+def test_gemm_tiles(torch_ready, oracle_lib, S):
+    torch = torch_ready
+    cases = []
+    for i, t in enumerate([1, 2, 3, 5, 37, 100]):
+        A = synth.normal_f32(14, 2 * i, t * 4096).reshape(t, 64, 64)
+        B = synth.normal_f32(14, 2 * i + 1, t * 4096).reshape(t, 64, 64)
+        cases.append((A, B, to_dev(A), to_dev(B), torch.zeros((t, 64, 64), device="cuda")))
+    I = np.broadcast_to(np.eye(64, dtype=np.float32), (3, 64, 64)).copy()
+    B = synth.normal_f32(14, 77, 3 * 4096).reshape(3, 64, 64)
+    cases.append((I, B, to_dev(I), to_dev(B), torch.zeros((3, 64, 64), device="cuda")))
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+        hs = [lk.lk_submit(c, 0, lk.LK_OP_GEMM64_F32, A.shape[0], (dA, dB), dC) for A, B, dA, dB, dC in cases]
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    for A, B, dA, dB, dC in cases:
+        assert gemm_ok(host(dC), A, B, oracle_lib), A.shape
+    # identity tile: exact
+    assert np.array_equal(host(cases[-1][4]), B)
+
+
+def test_misaligned_pointers_rejected_on_host(torch_ready):
+    torch = torch_ready
+    x = torch.zeros(1024, dtype=torch.int32, device="cuda")
+    with lk.lk_init([1], idle_lease_ns=5_000_000_000) as c:
+        with pytest.raises(lk.LkError) as e:
+            lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 16, (x.data_ptr() + 4,), x)
+        assert e.value.code == lk.LK_EINVAL
+        h = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert lk.lk_wait(c, h) == lk.LK_OK
+
+
+def test_sum_is_identical_alone_and_in_the_mix(torch_ready, oracle_lib):
+    """The split depends only on (n, cluster size): a result does not depend on
+    what else ran before or beside it."""
+    torch = torch_ready
+    x = synth.normal_f32(15, 1, 262144)
+    dx = to_dev(x)
+    outs = [torch.zeros(4, device="cuda") for _ in range(3)]
+    noise = to_dev(synth.int32_uniform(15, 2, 1 << 22, -100, 100))
+    nout = torch.zeros(1 << 22, dtype=torch.int32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([16, 16], idle_lease_ns=5_000_000_000) as c:
+        lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, x.size, (dx,), outs[0]))
+        hs = [lk.lk_submit(c, 1, lk.LK_OP_ADD_I32, 1 << 22, (noise, noise), nout) for _ in range(4)]
+        h1 = lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, x.size, (dx,), outs[1])
+        hs += [lk.lk_submit(c, 1, lk.LK_OP_COPY_I32, 1 << 22, (noise,), nout) for _ in range(4)]
+        h2 = lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, x.size, (dx,), outs[2])
+        for h in hs + [h1, h2]:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    v = [host(o)[0] for o in outs]
+    assert v[0] == v[1] == v[2]
+    assert sum_ok(v[0], x, oracle_lib)
+
+
+def test_finite_mode_bodies(torch_ready, oracle_lib):
+    torch = torch_ready
+    n = 300007
+    a = synth.int32_uniform(16, 1, n, -(2**20), 2**20)
+    b = synth.int32_uniform(16, 2, n, -(2**20), 2**20)
+    x = synth.normal_f32(16, 3, n)
+    da, db, dx = to_dev(a), to_dev(b), to_dev(x)
+    oa = torch.zeros(n, dtype=torch.int32, device="cuda")
+    os_ = torch.zeros(4, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    ms, log = lk.lk_run_finite([3, 2], [(lk.LK_OP_ADD_I32, n), (lk.LK_OP_SUM_F32, n)], [0, 1],
+                               in0=[da, dx], in1=[db, None], out=[oa, os_], log_cap=64)
+    assert ms > 0
+    assert np.array_equal(host(oa), oracle_lib.add_i32(a, b))
+    assert sum_ok(host(os_)[0], x, oracle_lib)
+    assert sorted(log["cluster"].tolist()) == [0, 0, 0, 1, 1]

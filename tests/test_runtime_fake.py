@@ -1,0 +1,265 @@
+"""Host runtime (liblk_fake.so: the real lk_runtime.cpp over a host-thread
+stand-in for the GPU).  Tickets, FIFO handles, ring-full refusals, argument
+checks, waits and timeouts, device-side errors, the idle lease, dispose and
+the execution log, all without a GPU.  Faults are injected on the host."""
+import os
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2310_01212_gb300 import lk
+
+
+@pytest.fixture
+def fake_env(native_built):
+    saved = {k: os.environ.get(k) for k in ("LK_FAKE_SMS", "LK_FAKE_STALL_US", "LK_FAKE_DROP_AFTER",
+                                            "LK_FAKE_FAIL_AFTER", "LK_FAKE_NO_BOOT")}
+    for k in saved:
+        os.environ.pop(k, None)
+    yield os.environ
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+
+
+def ctx_(sizes=(2, 3), **kw):
+    kw.setdefault("exec_log_cap", 256)
+    return lk.lk_init(list(sizes), fake=True, **kw)
+
+
+A = 0x10000   # any 16-byte-aligned "device" address: the fake runs no bodies
+
+
+def test_boot_clusters_cut_from_sorted_smids(fake_env):
+    with ctx_() as c:
+        # fake SMs: CTA g on (5g+3) mod 16 -> 3, 8, 13, 2, 7 ; sorted 2,3 | 7,8,13
+        assert lk.lk_cluster_info(c, 0) == [2, 3]
+        assert lk.lk_cluster_info(c, 1) == [7, 8, 13]
+        assert lk.lk_status(c, 0) == lk.LK_ST_INIT
+        assert lk.lk_num_ctas(c) == 5 and lk.lk_num_sms(c) == 16
+
+
+def test_explicit_smid_lists(fake_env):
+    with ctx_(sizes=(2, 1), smids=[8, 3, 13]) as c:
+        assert lk.lk_cluster_info(c, 0) == [8, 3]
+        assert lk.lk_cluster_info(c, 1) == [13]
+        h = lk.lk_submit(c, 1, lk.LK_OP_NOP, 0)
+        assert lk.lk_wait(c, h) == lk.LK_OK
+
+
+def test_submit_wait_handles_fifo(fake_env):
+    with ctx_() as c:
+        hs = [lk.lk_submit(c, i % 2, lk.LK_OP_NOP, 0) for i in range(10)]
+        for i, h in enumerate(hs):
+            assert h >> 48 == i % 2 and h & ((1 << 48) - 1) == i // 2 + 1
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+            assert lk.lk_poll(c, h) == lk.LK_OK
+        assert lk.lk_status(c, 0) == lk.LK_ST_FINISHED
+        assert lk.lk_sync(c) == lk.LK_OK
+
+
+@pytest.mark.parametrize("op,ins,out,n", [
+    (lk.LK_OP_ADD_I32, (A, A + 8), A, 16),       # misaligned input
+    (lk.LK_OP_ADD_I32, (A,), A, 16),             # wrong input count
+    (lk.LK_OP_SUM_F32, (A,), None, 16),          # sum needs an output
+    (lk.LK_OP_HIST_U8, (A,), A, 1 << 31),        # int32 bins cannot count 2^31
+    (lk.LK_OP_COPY_I32, (A,), A + 4, 16),        # misaligned output
+    (lk.LK_OP_ADD_I32, (0, A), A, 16),           # null input with n > 0
+    (99, (), None, 0),                           # unknown op
+])
+def test_argument_checks(fake_env, op, ins, out, n):
+    with ctx_() as c:
+        with pytest.raises(lk.LkError) as e:
+            lk.lk_submit(c, 0, op, n, ins, out)
+        assert e.value.code == lk.LK_EINVAL
+
+
+def test_bad_cluster_and_handle(fake_env):
+    with ctx_() as c:
+        with pytest.raises(lk.LkError):
+            lk.lk_submit(c, 2, lk.LK_OP_NOP, 0)
+        with pytest.raises(lk.LkError):
+            lk.lk_poll(c, 0)
+        with pytest.raises(lk.LkError):
+            lk.lk_poll(c, (0 << 48) | 5)    # never issued
+
+
+def test_zero_length_items_allowed(fake_env):
+    with ctx_() as c:
+        h1 = lk.lk_submit(c, 0, lk.LK_OP_ADD_I32, 0, (0, 0), None)
+        h2 = lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, 0, (0,), A)
+        assert lk.lk_wait(c, h1) == lk.LK_OK and lk.lk_wait(c, h2) == lk.LK_OK
+
+
+def test_ring_full_is_refused(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "300000"
+    with ctx_(ring_depth=2) as c:
+        h0 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        h1 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert lk.lk_submit(c, 0, lk.LK_OP_NOP, 0) is None    # LK_EAGAIN: nothing posted
+        assert lk.lk_submit(c, 1, lk.LK_OP_NOP, 0) is not None   # other cluster unaffected
+        assert lk.lk_wait(c, h0) == lk.LK_OK
+        h2 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert h2 is not None and h2 & 0xffff == 3
+        assert lk.lk_wait(c, h1) == lk.LK_OK and lk.lk_wait(c, h2) == lk.LK_OK
+
+
+def test_lost_completion_times_out(fake_env):
+    fake_env["LK_FAKE_DROP_AFTER"] = "1"
+    with ctx_() as c:
+        h1 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        h2 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert lk.lk_wait(c, h1) == lk.LK_OK
+        t0 = time.monotonic()
+        assert lk.lk_wait(c, h2, timeout_ns=50_000_000) == lk.LK_ETIMEDOUT
+        assert 0.04 < time.monotonic() - t0 < 2.0
+        assert lk.lk_poll(c, h2) == lk.LK_PENDING
+
+
+def test_device_error_surfaces(fake_env):
+    fake_env["LK_FAKE_FAIL_AFTER"] = "1"
+    c = ctx_()
+    h1 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    h2 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    assert lk.lk_wait(c, h1) == lk.LK_OK
+    with pytest.raises(lk.LkError) as e:
+        lk.lk_wait(c, h2)
+    assert e.value.code == lk.LK_EDEVICE
+    assert lk.lk_device_error(c) == lk.LK_DERR_BADDESC
+    assert lk.lk_status(c, 0) == lk.LK_ST_ERROR
+    with pytest.raises(lk.LkError) as e:
+        lk.lk_submit(c, 1, lk.LK_OP_NOP, 0)
+    assert e.value.code == lk.LK_ESTATE
+    assert c.dispose() == lk.LK_EDEVICE
+
+
+def test_idle_lease_expires_and_heartbeat_extends(fake_env):
+    c = ctx_(idle_lease_ns=300_000_000)
+    for _ in range(6):              # 0.6 s of beats: stays up
+        time.sleep(0.1)
+        assert lk.lk_heartbeat(c) == lk.LK_OK
+    h = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    assert lk.lk_wait(c, h) == lk.LK_OK
+    time.sleep(1.0)                 # silence: the lease runs out
+    assert lk.lk_device_error(c) == lk.LK_DERR_LEASE
+    with pytest.raises(lk.LkError) as e:
+        lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    assert e.value.code == lk.LK_ESTATE
+    assert lk.lk_poll(c, h) == lk.LK_OK      # finished work stays finished
+    assert c.dispose() == lk.LK_OK
+
+
+def test_boot_timeout(fake_env):
+    fake_env["LK_FAKE_NO_BOOT"] = "1"
+    with pytest.raises(lk.LkError) as e:
+        ctx_(boot_timeout_ns=100_000_000)
+    assert e.value.code == lk.LK_ETIMEDOUT
+
+
+def test_dispose_aborts_a_stuck_device(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "1500000"
+    c = ctx_()
+    lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    time.sleep(0.05)
+    t0 = time.monotonic()
+    rc = c.dispose(timeout_ns=100_000_000)
+    assert rc in (lk.LK_ETIMEDOUT, lk.LK_OK)
+    assert time.monotonic() - t0 < 5
+
+
+@pytest.mark.parametrize("sizes,bad", [((20,), "too many CTAs"), ((0, 2), "empty cluster")])
+def test_init_rejects_bad_partitions(fake_env, sizes, bad):
+    with pytest.raises(lk.LkError) as e:
+        ctx_(sizes=sizes)
+    assert e.value.code == lk.LK_EINVAL, bad
+
+
+@pytest.mark.parametrize("kw", [dict(threads_per_cta=48), dict(ring_depth=3), dict(smids=[1, 1, 2, 3, 4]),
+                                dict(smids=[1, 2, 3, 4, 99])])
+def test_init_rejects_bad_params(fake_env, kw):
+    with pytest.raises(lk.LkError) as e:
+        ctx_(**kw)
+    assert e.value.code == lk.LK_EINVAL
+
+
+def test_multi_producer_exec_log_passes_checker(fake_env, oracle_lib):
+    import oracle
+
+    sizes = (2, 3, 1)
+    c = ctx_(sizes=sizes, exec_log_cap=1024)
+    posted = {}
+    lock = threading.Lock()
+
+    def producer(p):
+        for j in range(150):
+            cl = (p + j) % 3
+            op = (lk.LK_OP_NOP, lk.LK_OP_ADD_I32, lk.LK_OP_COPY_I32)[j % 3]
+            ins = {lk.LK_OP_NOP: (), lk.LK_OP_ADD_I32: (A, A), lk.LK_OP_COPY_I32: (A,)}[op]
+            while True:
+                h = lk.lk_submit(c, cl, op, 64 if op else 0, ins, A if op else None)
+                if h is not None:
+                    break
+            with lock:
+                posted[(h >> 48, h & 0xffffffffffff)] = op
+
+    th = [threading.Thread(target=producer, args=(p,)) for p in range(4)]
+    [t.start() for t in th]
+    [t.join() for t in th]
+    assert lk.lk_sync(c) == lk.LK_OK
+    log, dropped = lk.lk_exec_log(c)
+    assert dropped == 0
+    n_posted = [sum(1 for (cl, _) in posted if cl == k) for k in range(3)]
+    posted_op = [posted[(k, s)] for k in range(3) for s in range(1, n_posted[k] + 1)]
+    pinned = sum((lk.lk_cluster_info(c, k) for k in range(3)), [])
+    res = oracle.check_exec_log(log["seq"], log["cluster"], log["rank"], log["smid"], log["op"], log["order"],
+                                sizes, n_posted, pinned_smid=pinned, posted_op=posted_op)
+    assert res["violations"] == 0, res
+    assert len(log) == sum(n_posted[k] * sizes[k] for k in range(3))
+    assert c.dispose() == lk.LK_OK
+
+
+def test_exec_log_ring_keeps_latest(fake_env):
+    with ctx_(sizes=(1,), exec_log_cap=4) as c:
+        for _ in range(10):
+            lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0))
+        log, dropped = lk.lk_exec_log(c, cap=100)
+        assert dropped == 6 and log["seq"].tolist() == [7, 8, 9, 10] and log["order"].tolist() == [6, 7, 8, 9]
+
+
+def test_trace_runner_open_and_closed_loop(fake_env):
+    with ctx_(sizes=(1, 1, 1, 1)) as c:
+        n = 400
+        items = np.zeros(n, dtype=lk.TRACE_ITEM_DTYPE)
+        items["t_arrival_ns"] = np.arange(n) * 20_000
+        items["cluster"] = np.arange(n) % 4
+        items["op"] = lk.LK_OP_NOP
+        for closed in (False, True):
+            rc, res = lk.lk_run_trace(c, items, n_threads=2, closed_loop=closed)
+            assert rc == lk.LK_OK
+            assert np.all(res["status"] == lk.LK_OK)
+            assert np.all(res["t_complete_ns"] >= res["t_submit_ns"])
+            assert np.all(res["t_submit_ns"] >= items["t_arrival_ns"])
+
+
+def test_trace_runner_reports_device_error(fake_env):
+    fake_env["LK_FAKE_FAIL_AFTER"] = "3"
+    c = ctx_(sizes=(1,))
+    items = np.zeros(10, dtype=lk.TRACE_ITEM_DTYPE)
+    items["op"] = lk.LK_OP_NOP
+    rc, res = lk.lk_run_trace(c, items, n_threads=1, timeout_ns=5_000_000_000)
+    assert rc == lk.LK_EDEVICE
+    assert np.sum(res["status"] == lk.LK_OK) == 3
+    c.dispose()
+
+
+def test_finite_mode_runs_the_list(fake_env):
+    descs = [(lk.LK_OP_NOP, 0)] * 7
+    ms, log = lk.lk_run_finite([2, 1], descs, [0, 1, 0, 0, 1, 0, 1], fake=True, log_cap=64)
+    assert ms >= 0
+    assert sorted(log[log["cluster"] == 0]["seq"].tolist()) == [1, 1, 2, 2, 3, 3, 4, 4]
+    assert sorted(log[log["cluster"] == 1]["seq"].tolist()) == [1, 2, 3]
