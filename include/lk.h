@@ -277,6 +277,30 @@ int lk_baseline_run_trace(int device, const lk_trace_item* items, size_t count, 
  * CUDA events recorded around its launch on its own stream (-1 if unknown). */
 int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms);
 
+/* ---- one ordinary launch that allocates nothing ------------------------ */
+/* The paper has no counterpart: this is a convenience of this library.
+ * It runs one descriptor as an ordinary kernel launch (the same bodies and
+ * split as lk_baseline_run_trace: `ctas` CTAs of `threads` threads) on the
+ * caller's `stream` (a cudaStream_t; NULL = the legacy default stream) and
+ * returns without waiting.  Unlike every other entry point it calls no
+ * cudaMalloc, cudaFree or other allocating routine: the scratch that the sum
+ * and histogram bodies use to combine per-CTA results is one file-scope
+ * device array of 5,248 bytes, so it suits callers that cannot allocate --
+ * a real-time loop that must not take the allocator's unbounded latency
+ * after start-up, or a host thread sharing the GPU with a running persistent
+ * context, where an allocation or free can block until that kernel returns.
+ *   device: CUDA ordinal; in[0..n_in-1], out: device pointers, 16-byte
+ *   aligned, as lk_submit.  ctas: 1..1024 (the array holds one partial sum per
+ *   CTA: more is rejected with LK_EINVAL, nothing launched).
+ * The first call on a device looks up the array's device address and clears
+ * it (an asynchronous memset on `stream`); make that first call before any
+ * stream capture.  All calls on a device share the one array and each
+ * launch's last CTA leaves it zeroed for the next, so calls whose launches
+ * overlap on the GPU race on it: serialise them (one stream, or events).
+ * Returns LK_OK (launched), LK_EINVAL, LK_EDEVICE (CUDA error). */
+int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
+                      int ctas, int threads, void* stream);
+
 /* Host-mapped round-trip floor: one host thread release-stores a counter, one
  * GPU thread acquire-spins on it and release-stores an echo, the host
  * acquire-spins on the echo.  Writes `iters` round-trip times (ns). */

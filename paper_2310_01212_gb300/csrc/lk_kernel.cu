@@ -760,6 +760,67 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
   return rc;
 }
 
+/* ---- one ordinary launch that allocates nothing --------------------------
+ * The sum and histogram bodies combine per-CTA results through a small
+ * scratch block (arrival counter, 256 histogram bins, one partial per CTA).
+ * lk_baseline_run_trace takes that block from cudaMalloc; this entry point
+ * takes it from the file-scope array below instead, so it never allocates.
+ * Capacity: one lk_scratch (5,248 bytes), i.e. at most LK_MAX_CTAS CTAs per
+ * launch.  Every GPU that loads this library keeps the array until exit. */
+static __device__ __align__(256) lk_scratch g_noalloc_scratch;
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256];   /* device address of g_noalloc_scratch, per device */
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+extern "C" int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
+                                 int ctas, int threads, void* stream) {
+  if (!d || d->flags != 0 || device < 0 || device >= 256) return LK_EINVAL;
+  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1};
+  if (d->op >= LK_OP_COUNT || n_in != need[d->op] || (n_in > 0 && !in)) return LK_EINVAL;
+  if (ctas < 1 || ctas > LK_MAX_CTAS) return LK_EINVAL;   /* beyond the static scratch */
+  if (threads < 64 || threads > 1024 || threads % 32) return LK_EINVAL;
+  if (d->n > (1ull << 40) || (d->op == LK_OP_HIST_U8 && d->n > 0x7fffffffull) ||
+      (d->op == LK_OP_GEMM64_F32 && d->n > (1ull << 28)))
+    return LK_EINVAL;
+  for (int i = 0; i < n_in; ++i)
+    if (!aligned16(in[i]) || (d->n > 0 && !in[i])) return LK_EINVAL;
+  if (!aligned16(out)) return LK_EINVAL;
+  if ((d->op == LK_OP_SUM_F32 || d->op == LK_OP_HIST_U8) && !out) return LK_EINVAL;
+  if (d->op != LK_OP_NOP && d->op != LK_OP_SUM_F32 && d->op != LK_OP_HIST_U8 && d->n > 0 && !out) return LK_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  if (g_preload_err != cudaSuccess) return LK_EDEVICE;
+  void* scratch;
+  {
+    /* set-up, once per device, with that device current: the array's name is
+     * only a host-side stand-in, so look up its device address */
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LK_EDEVICE;
+      /* the array starts zeroed at module load and every launch's last CTA
+       * returns the counter and bins to zero; clear once more here anyway */
+      if (cudaMemsetAsync(p, 0, sizeof(lk_scratch), (cudaStream_t)stream) != cudaSuccess) return LK_EDEVICE;
+      g_noalloc_ptr[device] = p;
+    }
+    scratch = g_noalloc_ptr[device];
+  }
+  lk_slot sl;
+  memset(&sl, 0, sizeof sl);
+  sl.cmd = LK_CMD_WORK + d->op;
+  sl.n = d->n;
+  sl.in0 = n_in > 0 ? (uint64_t)(uintptr_t)in[0] : 0;
+  sl.in1 = n_in > 1 ? (uint64_t)(uintptr_t)in[1] : 0;
+  sl.out = (uint64_t)(uintptr_t)out;
+  return launch_ordinary(sl, ctas, threads, (lk_scratch*)scratch, (cudaStream_t)stream) == cudaSuccess
+             ? LK_OK
+             : LK_EDEVICE;
+}
+
 extern "C" int lk_pingpong(int device, int iters, uint64_t* rtt_ns) {
   if (iters < 1 || !rtt_ns) return LK_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;

@@ -109,6 +109,7 @@ def load(fake: bool = False) -> ctypes.CDLL:
             "lk_run_trace": (I, [P, P, SZ, I, I, I, U64, P]),
             "lk_baseline_run_trace": (I, [I, P, SZ, I, ctypes.POINTER(I), I, I, I, I, P]),
             "lk_pingpong": (I, [I, I, ctypes.POINTER(U64)]),
+            "lk_launch_noalloc": (I, [I, ctypes.POINTER(lk_desc), ctypes.POINTER(P), I, P, I, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -327,3 +328,14 @@ def lk_pingpong(iters: int, device: int = 0) -> np.ndarray:
     if rc != LK_OK:
         raise LkError(rc, "lk_pingpong")
     return np.frombuffer(buf, dtype=np.uint64).copy()
+
+
+def lk_launch_noalloc(op: int, n: int, ins=(), out=None, ctas: int = 37, threads: int = 256, stream=None,
+                      device: int = 0) -> int:
+    """One ordinary launch that allocates nothing (see include/lk.h).  Returns
+    without waiting; `stream` is a cudaStream_t as an int (torch:
+    ``torch.cuda.current_stream().cuda_stream``) or None."""
+    lib = load()
+    d = lk_desc(op, 0, n, 0)
+    arr = (ctypes.c_void_p * max(1, len(ins)))(*[_ptr(i) for i in ins]) if ins else None
+    return lib.lk_launch_noalloc(device, ctypes.byref(d), arr, len(ins), _ptr(out), ctas, threads, stream or 0)
