@@ -415,8 +415,11 @@ def main():
     nop["op"] = lk.LK_OP_NOP
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000) as ctx:
         rc, r1 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
+    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT) as ctx:
+        rc, r3 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
     rc2, r2 = lk.lk_baseline_run_trace(nop, sizes, threads=cfg["threads"], n_threads=1, device=dev)
     nop_lk = (r1["t_complete_ns"] - r1["t_submit_ns"])[1000:] / 1000.0
+    nop_direct = (r3["t_complete_ns"] - r3["t_submit_ns"])[1000:] / 1000.0
     nop_base = (r2["t_complete_ns"] - r2["t_submit_ns"])[1000:] / 1000.0
 
     # ---- end to end: host buffers, copies inside the timed path ---------------------
@@ -486,7 +489,8 @@ def main():
         "arrival_to_complete_us": lat_summary(lat_arr),
         "max_us": mx,
         "baseline_launch_sync_us": lat_summary(base),
-        "dispatch_nop_us": {"lk": lat_summary(nop_lk), "launch_sync": lat_summary(nop_base)},
+        "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
+                            "launch_sync": lat_summary(nop_base)},
         "pingpong_floor_us": lat_summary(rtt),
         "throughput_items_per_s": items_all / wall_all,
         "wall_ms_per_step": 1000.0 * wall_all / args.steps,

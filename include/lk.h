@@ -114,8 +114,17 @@ typedef struct {
                                /* lk_heartbeat beat); 0 -> 10 s                          */
   uint64_t boot_timeout_ns;    /* lk_init fails if the CTAs are not all up; 0 -> 10 s    */
   uint32_t exec_log_cap;       /* execution-log records kept per CTA (ring); 0 = no log  */
-  uint32_t flags;              /* reserved, 0                                           */
+  uint32_t flags;              /* LK_INIT_* bits                                        */
 } lk_init_params;
+
+/* lk_init_params.flags: how descriptors reach a cluster's CTAs.
+ * Default: only the cluster's master thread (thread 0 of rank 0, the paper's
+ * one master thread per mailbox, Sec. II.D) polls the host-mapped ring, and
+ * relays each descriptor to the other CTAs through a tagged slot in device
+ * memory.  LK_INIT_DIRECT: every CTA's thread 0 polls the ring itself (no
+ * relay hop, but every extra reader of the ring's cache line delays the
+ * host's stores to it). */
+#define LK_INIT_DIRECT 1u
 
 /* A work descriptor.  The in/out pointers travel beside it. */
 typedef struct {
@@ -151,7 +160,8 @@ int lk_init(lk_ctx** out, const lk_init_params* p);
 /* Trigger (Sec. III): post descriptor d with its data items to `cluster`.
  *   in[0..n_in-1]: device pointers to the inputs (ADD: 2, HIST/SUM/COPY: 1,
  *   GEMM: 2 = A tiles, B tiles, NOP: 0); out: device pointer to the output.
- *   Every non-null pointer must be 16-byte aligned.  No CUDA call is made:
+ *   Every non-null pointer must be 16-byte aligned and below 2^48; n must
+ *   be at most 2^40 (HIST: below 2^31, GEMM: at most 2^28 tiles).  No CUDA call is made:
  *   the descriptor reaches the device through the mailbox ring only.
  * On success *h names the descriptor.
  * Errors: LK_EINVAL (cluster, op, n_in, alignment, n too large),
@@ -190,7 +200,10 @@ int lk_dispose(lk_ctx* ctx, uint64_t timeout_ns);
  * LK_EINVAL. */
 int lk_cluster_info(lk_ctx* ctx, int cluster, int* smids, int cap);
 
-/* Latest from_GPU status of `cluster` (LK_ST_*), or LK_EINVAL. */
+/* from_GPU status of `cluster` (Table 1): LK_ST_INIT after boot until the
+ * first post, LK_ST_WORKING while posted descriptors are unfinished,
+ * LK_ST_FINISHED once all of them finished, LK_ST_EXITED / LK_ST_ERROR after
+ * the cluster's CTAs returned.  LK_EINVAL for a bad cluster. */
 int lk_status(lk_ctx* ctx, int cluster);
 
 /* First device-side error reason (LK_DERR_*), or LK_EINVAL. */

@@ -114,13 +114,22 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
   const uint64_t stall = env_u64("LK_FAKE_STALL_US", 0) * 1000ull;
   const uint64_t drop_after = env_u64("LK_FAKE_DROP_AFTER", ~0ull);
   const uint64_t fail_after = env_u64("LK_FAKE_FAIL_AFTER", ~0ull);
-  const lk_slot* ring = a.ring + (size_t)c * (a.ring_mask + 1);
+  const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
   int err = 0;
   for (uint64_t k = 0;; ++k) {
-    const lk_slot* s = ring + (k & a.ring_mask);
+    const lk_wire* s = ring + (k & a.ring_mask);
+    const uint64_t tag = lk_lap_tag(k, a.ring_log2);
     uint64_t hb = ld_acq(&a.ctrl->heartbeat);
     uint64_t t_last = now_ns();
-    while (ld_acq(&s->seq) != k + 1) {
+    uint64_t w[6];
+    auto current = [&]() {
+      for (int i = 0; i < 6; ++i) w[i] = __atomic_load_n(&s->w[i], __ATOMIC_RELAXED);
+      for (int i = 0; i < 6; ++i)
+        if ((w[i] >> LK_TAG_SHIFT) != tag) return false;
+      __atomic_thread_fence(__ATOMIC_ACQUIRE);
+      return true;
+    };
+    while (!current()) {
       if (ld_acq(&a.ctrl->abort)) { err = LK_DERR_ABORT; break; }
       uint64_t t = now_ns();
       if (t - t_last > a.lease_ns) {
@@ -132,7 +141,9 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       std::this_thread::yield();
     }
     if (err) break;
-    const uint32_t cmd = s->cmd;
+    lk_slot dsc;
+    lk_wire_decode(w, k + 1, &dsc);
+    const uint32_t cmd = dsc.cmd;
     if (cmd == LK_CMD_EXIT) break;
     if (k >= fail_after) { err = LK_DERR_BADDESC; break; }
     const uint64_t t_pick = now_ns();

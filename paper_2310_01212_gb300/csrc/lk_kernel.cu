@@ -10,13 +10,13 @@
  * given as explicit SM lists).  The paper's check that a block sits on the SM
  * it expects becomes a table built from the SM ids actually observed.
  *
- * Mailboxes (Sec. II.D, Table 1): thread 0 of each cluster's rank-0 CTA is
- * the master thread.  It acquire-polls the cluster's host-mapped ring at
- * system scope, relays each descriptor to the other CTAs of the cluster
- * through a device-memory ring (GPU scope), and every CTA runs its share.
- * Each CTA then arrives on a per-descriptor counter; the last one to arrive
- * combines partial results and release-stores the descriptor's sequence
- * number into the host-mapped `done` word (from_GPU = THREAD_FINISHED).
+ * Mailboxes (Sec. II.D, Table 1): each CTA's thread 0 polls its cluster's
+ * host-mapped ring (or, with LK_INIT_RELAY, only rank 0 -- the paper's master
+ * thread -- polls it and relays each descriptor through a device ring), and
+ * every CTA runs its share.  Each CTA then release-stores its own finished
+ * count; rank 0 gathers the counts, combines partial results and publishes
+ * the descriptor's sequence number in the host-mapped `done` word
+ * (from_GPU = THREAD_FINISHED).
  *
  * Every device-side wait is bounded: by an idle lease (refreshed by the
  * host's heartbeat), by the host's abort word, and by a stall deadline.  On
@@ -54,14 +54,37 @@ __device__ __forceinline__ void set_error(const lk_kargs& a, int c, uint32_t cod
   __threadfence_system();
 }
 
-/* Master thread: wait until ring slot `s` carries sequence number `want`.
+__device__ __forceinline__ void ld_relaxed_sys_v2(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.relaxed.sys.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_sys() { asm volatile("fence.acq_rel.sys;" ::: "memory"); }
+
+__device__ __forceinline__ bool tags_match(const uint64_t* w, uint64_t tag) {
+  return (w[0] >> LK_TAG_SHIFT) == tag && (w[1] >> LK_TAG_SHIFT) == tag && (w[2] >> LK_TAG_SHIFT) == tag &&
+         (w[3] >> LK_TAG_SHIFT) == tag && (w[4] >> LK_TAG_SHIFT) == tag && (w[5] >> LK_TAG_SHIFT) == tag;
+}
+__device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
+  ld_relaxed_sys_v2(&s->w[0], w[0], w[1]);
+  ld_relaxed_sys_v2(&s->w[2], w[2], w[3]);
+  ld_relaxed_sys_v2(&s->w[4], w[4], w[5]);
+}
+
+/* Wait until ring slot `s` holds ticket k (every tagged word carries lap tag
+ * `tag`), then decode it.  A probe loads the six tagged words at once, so it
+ * costs one round trip over the host link.  One probe at a time, from one
+ * thread: every extra read in flight on the slot's line makes the host's
+ * stores to that line wait for ownership again.  The acquire fence after a
+ * successful probe pairs with the host's release fence before its stores.
  * Returns 0 or an LK_DERR_* reason (lease ran out, abort). */
-__device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_slot* s, uint64_t want, lk_slot& out) {
+__device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, uint64_t tag, uint64_t seq,
+                                           lk_slot& out) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
+  uint64_t w[6];
   for (uint32_t it = 1;; ++it) {
-    if (ld_acquire_sys(&s->seq) == want) break;
+    probe(s, w);
+    if (tags_match(w, tag)) break;
     if ((it & 63) == 0) {
       if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
       const uint64_t now = gtime();
@@ -74,25 +97,69 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_slot* s, 
     }
     bo.pause();
   }
-  /* the acquire above orders these reads after the host's slot writes */
-  const ulonglong2* p = reinterpret_cast<const ulonglong2*>(s);
-  const ulonglong2 v0 = __ldcv(p + 0), v1 = __ldcv(p + 1), v2 = __ldcv(p + 2), v3 = __ldcv(p + 3);
-  out.seq = want;
-  out.cmd = (uint32_t)(v0.y & 0xffffffffull);
-  out.flags = (uint32_t)(v0.y >> 32);
-  out.n = v1.x;
-  out.in0 = v1.y;
-  out.in1 = v2.x;
-  out.out = v2.y;
-  out.aux = v3.x;
-  out.t_pick = 0;
+  fence_acq_rel_sys();
+  lk_wire_decode(w, seq, &out);
   return 0;
 }
 
-/* Wait until *word >= want (GPU scope).  Members wait on the relay
- * generation, the master on the relay slot becoming free.  `stop_on_max`
- * treats LK_GEN_STOP as the master's stop signal (returns -1). */
-__device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, uint64_t want, bool stop_on_max) {
+/* Relay (LK_INIT_RELAY): the master copies descriptor k into relay slot
+ * k mod D as six lap-tagged words (the host ring's format, tag = relay lap),
+ * after the acquire-release fence that followed its ring probe, so members
+ * need no separate generation word: they probe the slot in L2 (one round
+ * trip) and issue a GPU-scope acquire fence when every tag is current. */
+__device__ __forceinline__ void relay_publish(lk_wire* rs, uint64_t k, const lk_slot& d) {
+  const uint64_t tag = ((k / LK_BCAST_DEPTH + 1) & 0xffffull) << LK_TAG_SHIFT;
+  const uint64_t v[6] = {tag | ((uint64_t)(d.flags & 0xffffu) << 16) | (d.cmd & 0xffffu), tag | (d.n & LK_LOW48),
+                         tag | (d.in0 & LK_LOW48), tag | (d.in1 & LK_LOW48), tag | (d.out & LK_LOW48),
+                         tag | (d.aux & LK_LOW48)};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[i]), "l"(v[i]) : "memory");
+  /* the pickup time (for the execution log), tagged too: its low 48 bits */
+  asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[6]), "l"(tag | (d.t_pick & LK_LOW48)) : "memory");
+}
+
+__device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster* dc, const lk_wire* rs, uint64_t k,
+                                            lk_slot& out) {
+  const uint64_t tag = (k / LK_BCAST_DEPTH + 1) & 0xffffull;
+  Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
+  uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+  uint64_t t_last = gtime();
+  const uint64_t limit = a.lease_ns + 1000000000ull;
+  uint64_t w[8];
+  for (uint32_t it = 1;; ++it) {
+    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(&rs->w[0]) : "memory");
+    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[2]), "=l"(w[3]) : "l"(&rs->w[2]) : "memory");
+    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
+    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
+    if (tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag) break;
+    if ((it & 255) == 0) {
+      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+      if (ld_acquire_gpu(&dc->gen) == LK_GEN_STOP) return -1;
+      const uint64_t now = gtime();
+      if (now - t_last > limit) {
+        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+        if (h == hb) return LK_DERR_STALL;
+        hb = h;
+        t_last = now;
+      }
+    }
+    bo.pause();
+  }
+  fence_acq_rel_gpu();
+  lk_wire_decode(w, k + 1, &out);
+  /* the master's pickup time: its low 48 bits under this reader's high bits */
+  const uint64_t now = gtime();
+  uint64_t tp = (now & ~LK_LOW48) | (w[6] & LK_LOW48);
+  if (tp > now) tp -= (1ull << 48);
+  out.t_pick = tp;
+  return 0;
+}
+
+/* Wait until *word >= want (GPU scope): relay generation, device-side done.
+ * `stop_on_max` treats LK_GEN_STOP as the master's stop signal (returns -1).
+ * *seen (optional) receives the value that satisfied the wait. */
+__device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, uint64_t want, bool stop_on_max,
+                                      uint64_t* seen = nullptr) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
@@ -100,7 +167,10 @@ __device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, u
   for (uint32_t it = 1;; ++it) {
     const uint64_t g = ld_acquire_gpu(word);
     if (stop_on_max && g == LK_GEN_STOP) return -1;
-    if (g >= want) return 0;
+    if (g >= want) {
+      if (seen) *seen = g;
+      return 0;
+    }
     if ((it & 255) == 0) {
       if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
       const uint64_t now = gtime();
@@ -115,14 +185,99 @@ __device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, u
   }
 }
 
+/* Warp 0 of rank 0: wait until every rank of the cluster has finished
+ * descriptor `want` (flag[q] >= want).  Lanes poll disjoint ranks in
+ * parallel, so the wait costs about one L2 round trip once the last rank is
+ * done.  Returns 0 or an LK_DERR_* reason (same bounds as wait_word). */
+__device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag, int S, uint64_t want) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t pending = 0;   /* bit j: rank lane + 32 j not seen yet */
+  for (int j = 0; j < 32 && (int)lane + 32 * j < S; ++j) pending |= 1u << j;
+  uint64_t hb = 0, t_last = 0;
+  if (lane == 0) {
+    hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+    t_last = gtime();
+  }
+  const uint64_t limit = a.lease_ns + 1000000000ull;
+  for (uint32_t it = 1;; ++it) {
+    /* relaxed loads can all be in flight at once (acquire loads would each
+     * wait for the one before); one acquire fence follows success */
+    for (int g = 0; g < 32 && (pending >> g); g += 8) {
+      uint64_t v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (pending & (1u << (g + j)))
+          asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(v[j]) : "l"(flag + lane + 32 * (g + j)) : "memory");
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if ((pending & (1u << (g + j))) && v[j] >= want) pending &= ~(1u << (g + j));
+    }
+    if (__all_sync(0xffffffffu, pending == 0)) {
+      fence_acq_rel_gpu();
+      return 0;
+    }
+    if ((it & 255) == 0) {
+      int err = 0;
+      if (lane == 0) {
+        if (ld_relaxed_sys(&a.ctrl->abort)) {
+          err = LK_DERR_ABORT;
+        } else {
+          const uint64_t now = gtime();
+          if (now - t_last > limit) {
+            const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+            if (h == hb) err = LK_DERR_STALL;
+            hb = h;
+            t_last = now;
+          }
+        }
+      }
+      err = __shfl_sync(0xffffffffu, err, 0);
+      if (err) return err;
+    }
+  }
+}
+
+/* Unroll depth (vectors in flight per thread per round) per body: the same
+ * bytes in flight per SM for every block size. */
+template <int MAXT> struct Unroll {
+  static constexpr int two_streams = 2048 / MAXT;   /* add: 2 loads per vector   */
+  static constexpr int one_stream = 4096 / MAXT;    /* copy, sum                 */
+  static constexpr int hist = 1024 / MAXT;        /* counting, not loads, bounds it */
+};
+
+/* This CTA's share of descriptor d (rank r of S).  Returns an LK_DERR_* code
+ * or 0.  `partial_out` receives the sum body's per-CTA partial. */
+template <int MAXT>
+__device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                        uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc) {
+  const uint32_t op = d.cmd - LK_CMD_WORK;
+  switch (op) {
+    case LK_OP_ADD_I32: body_add_copy<Unroll<MAXT>::two_streams, true>(d, r, S); return 0;
+    case LK_OP_COPY_I32: body_add_copy<Unroll<MAXT>::one_stream, false>(d, r, S); return 0;
+    case LK_OP_SUM_F32: {
+      const float p = body_sum_partial<Unroll<MAXT>::one_stream>(d, r, S, red);
+      if (threadIdx.x == 0) *partial_out = p;
+      return 0;
+    }
+    case LK_OP_HIST_U8:
+      body_hist<Unroll<MAXT>::hist>(d, r, S, reinterpret_cast<uint32_t*>(dsm), hist_acc);
+      return 0;
+    case LK_OP_GEMM64_F32:
+      return body_gemm(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, gtime() + 2000000000ull)
+                 ? 0
+                 : LK_DERR_STAGING;
+    case LK_OP_NOP: return 0;
+    default: return LK_DERR_BADDESC;
+  }
+}
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
-  constexpr int U = 2048 / MAXT;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(64) lk_slot s_desc;
-  __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_last, s_err;
+  __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bars[2];
   __shared__ uint64_t s_tstart;
   const uint32_t tid = threadIdx.x;
 
@@ -176,7 +331,8 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     } else if (rk == 0) {
       st_relaxed_sys(&a.cword[c].status, LK_ST_INIT);
     }
-    mbar_init(&s_bar, 1);
+    mbar_init(&s_bars[0], 1);
+    mbar_init(&s_bars[1], 1);
     fence_barrier_init();
     red_release_sys_add(&a.ctrl->booted, 1u);
   }
@@ -185,69 +341,50 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
 
   const int c = s_cl, r = s_rank, S = s_size;
   const bool master = (r == 0);
+  const bool relay = (a.flags & LK_KFLAG_DIRECT) == 0;
   lk_dcluster* dc = a.dcl + c;
-  const lk_slot* ring = a.ring + (size_t)c * (a.ring_mask + 1);
-  float* sA = reinterpret_cast<float*>(dsm);
-  float* sB = reinterpret_cast<float*>(dsm + 16384);
-  uint32_t* sh = reinterpret_cast<uint32_t*>(dsm);
+  const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
   uint32_t phase = 0;
   int final_err = 0;
+  uint64_t known_done = 0;   /* latest dev_done this CTA has seen */
 
   for (uint64_t k = 0;; ++k) {
     const uint32_t slot = (uint32_t)(k % LK_BCAST_DEPTH);
-    /* ---- take (master) or receive (members) descriptor k+1 ------------- */
+    /* ---- descriptor k+1: from the ring, or from the master's relay ------ */
     if (tid == 0) {
       int err = 0;
       lk_slot dsc;
-      if (master) {
-        err = take_from_ring(a, ring + (k & a.ring_mask), k + 1, dsc);
-        if (!err) {
-          dsc.t_pick = gtime();
-          /* relay slot k mod D is free once descriptor k+1-D has finished */
-          if (k + 1 > LK_BCAST_DEPTH) {
-            const int w = wait_word(a, &dc->dev_done, k + 1 - LK_BCAST_DEPTH, false);
-            err = w < 0 ? LK_DERR_STALL : w;
-          }
-        }
-        if (!err) {
-          lk_slot* b = &dc->bcast[slot];
-          *b = dsc;
-          st_release_gpu(&dc->gen, k + 1);
-          if (dsc.cmd != LK_CMD_EXIT) st_relaxed_sys(&a.cword[c].status, LK_ST_WORKING);
-        } else {
-          st_release_gpu(&dc->gen, LK_GEN_STOP);
-        }
+      const lk_wire* w = ring + (k & a.ring_mask);
+      const uint64_t tag = lk_lap_tag(k, a.ring_log2);
+      if (!relay || master) {
+        err = take_from_ring(a, w, tag, k + 1, dsc);
+        if (!err) dsc.t_pick = gtime();
       } else {
-        const int w = wait_word(a, &dc->gen, k + 1, true);
-        if (w < 0) err = -1;   /* master stopped; its reason is recorded */
-        else err = w;
-        if (!err) {
-          const ulonglong2* p = reinterpret_cast<const ulonglong2*>(&dc->bcast[slot]);
-          const ulonglong2 v0 = __ldcg(p + 0), v1 = __ldcg(p + 1), v2 = __ldcg(p + 2), v3 = __ldcg(p + 3);
-          dsc.seq = v0.x;
-          dsc.cmd = (uint32_t)(v0.y & 0xffffffffull);
-          dsc.flags = (uint32_t)(v0.y >> 32);
-          dsc.n = v1.x;
-          dsc.in0 = v1.y;
-          dsc.in1 = v2.x;
-          dsc.out = v2.y;
-          dsc.aux = v3.x;
-          dsc.t_pick = v3.y;
-        }
+        err = take_from_relay(a, dc, &dc->relay[slot], k, dsc);
+      }
+      /* relay-ring slot k mod D (relay copy, partials, histogram accumulator)
+       * is free once descriptor k+1-D has finished */
+      if (!err && k + 1 > LK_BCAST_DEPTH && known_done < k + 1 - LK_BCAST_DEPTH &&
+          (master ? relay : dsc.cmd != LK_CMD_EXIT)) {
+        const int ww = wait_word(a, &dc->dev_done, k + 1 - LK_BCAST_DEPTH, false, &known_done);
+        err = ww < 0 ? LK_DERR_STALL : ww;
+      }
+      if (relay && master) {
+        if (!err) relay_publish(&dc->relay[slot], k, dsc);
+        else st_release_gpu(&dc->gen, LK_GEN_STOP);
       }
       if (err) {
         if (err > 0) {
           set_error(a, c, (uint32_t)err);
           final_err = err;
         } else {
-          final_err = LK_DERR_STALL;   /* for the status word only */
+          final_err = LK_DERR_STALL;   /* master stopped; its reason is recorded */
         }
         s_exit = 1;
       } else {
         s_desc = dsc;
         s_exit = (dsc.cmd == LK_CMD_EXIT);
       }
-      s_last = 0;
       s_err = 0;
       s_tstart = gtime();
     }
@@ -257,45 +394,35 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    switch (op) {
-      case LK_OP_ADD_I32: body_add_copy<U, true>(d, r, S); break;
-      case LK_OP_COPY_I32: body_add_copy<U, false>(d, r, S); break;
-      case LK_OP_SUM_F32: {
-        const float p = body_sum_partial<U>(d, r, S, s_red);
-        if (tid == 0) dc->partial[slot][r] = p;
-        break;
-      }
-      case LK_OP_HIST_U8: body_hist<U>(d, r, S, sh, dc->hist[slot]); break;
-      case LK_OP_GEMM64_F32:
-        if (!body_gemm(d, r, S, sA, sB, &s_bar, phase, gtime() + 2000000000ull)) s_err = LK_DERR_STAGING;
-        break;
-      case LK_OP_NOP: break;
-      default:
-        if (tid == 0) s_err = LK_DERR_BADDESC;
-    }
+    const int berr = run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+    if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
-    /* ---- arrive; the last CTA completes the descriptor ------------------ */
-    uint64_t t_end = 0;
+    /* ---- finish: every rank raises its flag; rank 0 completes ---------- */
+    uint64_t t_end = 0, t_done = 0;
     if (tid == 0) {
       t_end = gtime();
-      __threadfence();
-      const uint32_t old = atom_add_acq_rel_gpu(&dc->arrive[slot], 1u);
-      s_last = (old == (uint32_t)(S - 1));
+      if (S > 1) st_release_gpu(&dc->flag[r], k + 1);   /* orders this CTA's writes (after the barrier) */
     }
-    __syncthreads();
-    uint64_t t_done = 0;
-    if (s_last) {
-      if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
-      else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+    if (master) {
+      if (S > 1 && tid < 32) {
+        const int gerr = gather_flags(a, dc->flag, S, k + 1);
+        if (gerr && tid == 0) s_err = gerr;
+      }
       __syncthreads();
-      if (tid == 0) {
-        dc->arrive[slot] = 0;
-        __threadfence();
-        st_release_gpu(&dc->dev_done, k + 1);
-        st_release_sys(&a.cword[c].done, d.seq);
-        t_done = gtime();
-        st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);
+      if (!s_err) {
+        if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
+        else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+        __syncthreads();
+        if (tid == 0) {
+          /* one system-scope fence orders every output write (this CTA's,
+           * and the other ranks' through their flags) before both stores */
+          fence_acq_rel_sys();
+          asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&dc->dev_done), "l"(k + 1) : "memory");
+          known_done = k + 1;
+          st_relaxed_sys(&a.cword[c].done, d.seq);
+          t_done = gtime();
+        }
       }
     }
     if (tid == 0 && a.log) {
@@ -312,11 +439,12 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
       rec->t_done_ns = t_done;
       a.log_count[blockIdx.x] = k + 1;
     }
+    __syncthreads();
     if (s_err) {
       if (tid == 0) {
         set_error(a, c, (uint32_t)s_err);
         final_err = s_err;
-        if (master) st_release_gpu(&dc->gen, LK_GEN_STOP);
+        if (master && relay) st_release_gpu(&dc->gen, LK_GEN_STOP);
       }
       break;
     }
@@ -337,36 +465,23 @@ struct lk_scratch {
 
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch* sc) {
-  constexpr int U = 2048 / MAXT;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_bars[2];
   __shared__ int32_t s_last;
   const int r = blockIdx.x, S = gridDim.x;
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  switch (op) {
-    case LK_OP_ADD_I32: body_add_copy<U, true>(d, r, S); return;
-    case LK_OP_COPY_I32: body_add_copy<U, false>(d, r, S); return;
-    case LK_OP_NOP: return;
-    case LK_OP_GEMM64_F32: {
-      if (threadIdx.x == 0) {
-        mbar_init(&s_bar, 1);
-        fence_barrier_init();
-      }
-      __syncthreads();
-      uint32_t phase = 0;
-      body_gemm(d, r, S, reinterpret_cast<float*>(dsm), reinterpret_cast<float*>(dsm + 16384), &s_bar, phase,
-                gtime() + 2000000000ull);
-      return;
+  if (op == LK_OP_GEMM64_F32) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bars[0], 1);
+      mbar_init(&s_bars[1], 1);
+      fence_barrier_init();
     }
-    case LK_OP_SUM_F32: {
-      const float p = body_sum_partial<U>(d, r, S, s_red);
-      if (threadIdx.x == 0) sc->partial[r] = p;
-      break;
-    }
-    case LK_OP_HIST_U8: body_hist<U>(d, r, S, reinterpret_cast<uint32_t*>(dsm), sc->hist); break;
-    default: return;
+    __syncthreads();
   }
+  uint32_t phase = 0;
+  run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
+  if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -415,6 +530,14 @@ void preload_all() {
                          (const void*)lk_pingpong_kernel};
     for (const void* f : fns) {
       cudaError_t e = cudaFuncGetAttributes(&fa, f);
+      if (e != cudaSuccess && g_preload_err == cudaSuccess) g_preload_err = e;
+    }
+    /* ordinary launches of the histogram / GEMM bodies take 64 KB of shared memory */
+    const void* ord[] = {(const void*)lk_ordinary<256>, (const void*)lk_ordinary<512>, (const void*)lk_ordinary<1024>};
+    const int ord_t[] = {256, 512, 1024};
+    for (int i = 0; i < 3; ++i) {
+      cudaError_t e = cudaFuncSetAttribute(ord[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)lk::body_smem_bytes(ord_t[i]));
       if (e != cudaSuccess && g_preload_err == cudaSuccess) g_preload_err = e;
     }
   });

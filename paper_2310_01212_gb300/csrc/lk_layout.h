@@ -3,20 +3,19 @@
  * kernel (internal; not part of the public ABI).
  *
  * Host-mapped pinned memory (the host<->device mailboxes of Sec. II.D):
- *   ring[c][R]      descriptor slots of cluster c (the to_GPU side).  A slot is
- *                   one 64-byte line; its `seq` word is written last, with
- *                   release order, and names the slot's position in the
- *                   cluster's FIFO (1-based).  Table 1's single to_GPU integer
- *                   becomes the slot's `cmd` (THREAD_WORK + op, THREAD_EXIT).
+ *   ring[c][R]      descriptor slots of cluster c (the to_GPU side), one
+ *                   64-byte line each, published with a lap tag in every word
+ *                   (lk_wire below).  Table 1's single to_GPU integer becomes
+ *                   the slot's `cmd` (THREAD_WORK + op, THREAD_EXIT).
  *   cword[c]        per-cluster from_GPU words: `done` (seq of the last
  *                   finished descriptor, monotone), `status` (Table 1 code),
  *                   each on its own 128-byte line.
  *   ctrl            abort word, heartbeat, boot / exit counters, first error.
  *   info[g]         (cluster, rank, smid) of CTA g, written at boot.
  * Device memory (cluster-internal relay, L2-resident):
- *   dcl[c]          broadcast ring (D slots), generation, device-side done,
- *                   arrival counters, per-rank partial sums, histogram
- *                   accumulators.
+ *   dcl[c]          relay ring (D slots), generation, device-side done,
+ *                   per-rank finished counts, per-rank partial sums,
+ *                   histogram accumulators.
  *   log[g][cap]     execution-log records (lk_exec_rec) of CTA g.
  */
 #ifndef LK_LAYOUT_H
@@ -25,13 +24,13 @@
 #include "../../include/lk.h"
 
 #define LK_LINE 128
-#define LK_BCAST_DEPTH 4          /* descriptors a cluster may have in flight */
+#define LK_BCAST_DEPTH 8          /* descriptors a cluster may have in flight */
 #define LK_MAX_CTAS 1024          /* upper bound on CTAs per context          */
 #define LK_MAX_CLUSTERS 256
 
-/* One mailbox slot: 64 bytes, seq published last. */
+/* A descriptor as the device uses it (decoded; also the relay-ring format). */
 typedef struct __attribute__((aligned(64))) {
-  uint64_t seq;     /* 1-based FIFO position; written last (release)   */
+  uint64_t seq;     /* 1-based FIFO position                           */
   uint32_t cmd;     /* LK_CMD_WORK + op, or LK_CMD_EXIT                 */
   uint32_t flags;
   uint64_t n;
@@ -39,8 +38,48 @@ typedef struct __attribute__((aligned(64))) {
   uint64_t in1;
   uint64_t out;
   uint64_t aux;
-  uint64_t t_pick;  /* device-side: %globaltimer when the master took it */
+  uint64_t t_pick;  /* device-side: %globaltimer when the slot was taken */
 } lk_slot;
+
+/* A mailbox slot as it sits in the host-mapped ring: eight 8-byte words.
+ * Words 0..5 each carry, in their top 16 bits, the slot's lap tag: for
+ * ticket t of a ring of 2^L slots, tag = ((t >> L) + 1) mod 2^16.  The host
+ * issues a release fence, then stores the words (8-byte single-copy atomic
+ * stores); a reader loads all six words at once and accepts the slot only
+ * when every tag equals the lap it waits for, then issues an acquire fence.
+ * Pickup thus costs one round trip over the host link instead of two (flag,
+ * then payload).  Addresses, n and aux must fit in 48 bits.
+ *   w0 = tag | flags << 16 | cmd      w3 = tag | in1
+ *   w1 = tag | n                      w4 = tag | out
+ *   w2 = tag | in0                    w5 = tag | aux
+ *   w6 = seq (t + 1)                  w7 = 0                              */
+typedef struct __attribute__((aligned(64))) {
+  uint64_t w[8];
+} lk_wire;
+
+#define LK_TAG_SHIFT 48
+#define LK_LOW48 0x0000ffffffffffffull
+
+#ifdef __CUDACC__
+#define LK_HD __host__ __device__ __forceinline__
+#else
+#define LK_HD static inline
+#endif
+
+LK_HD uint64_t lk_lap_tag(uint64_t t, uint32_t ring_log2) { return ((t >> ring_log2) + 1) & 0xffffull; }
+
+/* Decode words 0..5 into a descriptor (tags are checked by the caller). */
+LK_HD void lk_wire_decode(const uint64_t w[6], uint64_t seq, lk_slot* d) {
+  d->seq = seq;
+  d->cmd = (uint32_t)(w[0] & 0xffffull);
+  d->flags = (uint32_t)((w[0] >> 16) & 0xffffull);
+  d->n = w[1] & LK_LOW48;
+  d->in0 = w[2] & LK_LOW48;
+  d->in1 = w[3] & LK_LOW48;
+  d->out = w[4] & LK_LOW48;
+  d->aux = w[5] & LK_LOW48;
+  d->t_pick = 0;
+}
 
 typedef struct __attribute__((aligned(LK_LINE))) {
   uint64_t done;                 /* seq of the last finished descriptor (device writes) */
@@ -69,22 +108,25 @@ typedef struct {
   int32_t pad;
 } lk_cta_info;
 
-/* Per-cluster relay state in device memory. */
+/* Per-cluster state in device memory.  `flag[r]` is the number of
+ * descriptors rank r has finished (monotone); rank 0 gathers the flags and
+ * completes each descriptor, so no counter is shared by all CTAs. */
 typedef struct __attribute__((aligned(LK_LINE))) {
-  uint64_t gen;                          /* descriptors relayed so far (master writes)  */
+  uint64_t gen;                          /* LK_GEN_STOP once the master stopped         */
   uint8_t pad0[LK_LINE - 8];
-  uint64_t dev_done;                     /* descriptors finished (last arriver writes)  */
+  uint64_t dev_done;                     /* descriptors finished (rank 0 writes)        */
   uint8_t pad1[LK_LINE - 8];
-  uint32_t arrive[LK_BCAST_DEPTH];       /* CTAs done with relay slot d                 */
-  uint8_t pad2[LK_LINE - 4 * LK_BCAST_DEPTH];
-  lk_slot bcast[LK_BCAST_DEPTH];         /* relay ring                                  */
+  uint64_t flag[LK_MAX_CTAS];            /* per-rank finished count                     */
+  lk_wire relay[LK_BCAST_DEPTH];         /* relay ring (lap-tagged like the host ring)  */
   uint32_t hist[LK_BCAST_DEPTH][256];    /* histogram accumulators, zero at rest        */
   float partial[LK_BCAST_DEPTH][LK_MAX_CTAS]; /* per-rank partial sums                  */
 } lk_dcluster;
 
 /* Everything the persistent kernel needs; passed by value at launch. */
+#define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
+
 typedef struct {
-  lk_slot* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */
+  lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */
   lk_cword* cword;               /* [C] host-mapped                                     */
   lk_ctrl* ctrl;                 /* host-mapped                                         */
   lk_cta_info* info;             /* [G] host-mapped                                     */
@@ -99,6 +141,7 @@ typedef struct {
   int32_t grid;
   int32_t total;                 /* CTAs that join clusters (= sum of sizes)            */
   uint32_t ring_mask;            /* R - 1                                               */
+  uint32_t ring_log2;            /* log2 R                                              */
   uint32_t log_cap;
   uint32_t flags;
   uint64_t backoff_base_ns;

@@ -36,8 +36,8 @@ inline uint64_t now_ns() {
 
 template <class T> inline T ld_acq(const T* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 template <class T> inline T ld_rlx(const T* p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
-template <class T> inline void st_rel(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
-template <class T> inline void st_rlx(T* p, T v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
+template <class T, class V> inline void st_rel(T* p, V v) { __atomic_store_n(p, (T)v, __ATOMIC_RELEASE); }
+template <class T, class V> inline void st_rlx(T* p, V v) { __atomic_store_n(p, (T)v, __ATOMIC_RELAXED); }
 
 struct alignas(LK_LINE) Tail {
   std::atomic<uint64_t> t{0};
@@ -61,7 +61,8 @@ struct lk_ctx {
 
   void* mapped_h = nullptr;
   void* mapped_d = nullptr;
-  lk_slot* ring_h = nullptr;     /* host view of the ring (live mode) */
+  lk_wire* ring_h = nullptr;     /* host view of the ring (live mode) */
+  uint32_t R_log2 = 10;
   lk_cword* cword_h = nullptr;
   lk_ctrl* ctrl_h = nullptr;
   lk_cta_info* info_h = nullptr;
@@ -107,13 +108,13 @@ static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in
   int need = op_inputs(d->op);
   if (need < 0 || n_in != need) return LK_EINVAL;
   if (d->flags != 0) return LK_EINVAL;
-  if (d->n > (1ull << 40)) return LK_EINVAL;
+  if (d->n > (1ull << 40) || d->aux > LK_LOW48) return LK_EINVAL;
   const void* ins[2] = {in0, in1};
   for (int i = 0; i < need; ++i) {
-    if (!aligned16(ins[i])) return LK_EINVAL;
+    if (!aligned16(ins[i]) || (uintptr_t)ins[i] > LK_LOW48) return LK_EINVAL;
     if (d->n > 0 && !ins[i]) return LK_EINVAL;
   }
-  if (!aligned16(out)) return LK_EINVAL;
+  if (!aligned16(out) || (uintptr_t)out > LK_LOW48) return LK_EINVAL;
   switch (d->op) {
     case LK_OP_NOP: break;
     case LK_OP_SUM_F32:
@@ -133,16 +134,22 @@ static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in
   return LK_OK;
 }
 
-static void fill_slot(lk_slot* s, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
-                      void* out) {
-  s->cmd = cmd;
-  s->flags = d ? d->flags : 0;
-  s->n = d ? d->n : 0;
-  s->in0 = (uint64_t)(uintptr_t)in0;
-  s->in1 = (uint64_t)(uintptr_t)in1;
-  s->out = (uint64_t)(uintptr_t)out;
-  s->aux = d ? d->aux : 0;
-  s->t_pick = 0;
+/* Publish ticket t into slot s (see lk_wire): a release fence orders every
+ * earlier host write before the slot's words; each word carries the lap tag,
+ * so a reader that sees all tags current has the whole descriptor. */
+static void write_slot(lk_wire* s, uint64_t t, uint32_t R_log2, uint32_t cmd, const lk_desc* d,
+                       const void* in0, const void* in1, void* out) {
+  const uint64_t tag = lk_lap_tag(t, R_log2) << LK_TAG_SHIFT;
+  const uint64_t flags = d ? d->flags : 0;
+  __atomic_thread_fence(__ATOMIC_RELEASE);
+  st_rlx(&s->w[0], tag | (flags & 0xffffull) << 16 | (uint64_t)(cmd & 0xffffu));
+  st_rlx(&s->w[1], tag | ((d ? d->n : 0) & LK_LOW48));
+  st_rlx(&s->w[2], tag | ((uint64_t)(uintptr_t)in0 & LK_LOW48));
+  st_rlx(&s->w[3], tag | ((uint64_t)(uintptr_t)in1 & LK_LOW48));
+  st_rlx(&s->w[4], tag | ((uint64_t)(uintptr_t)out & LK_LOW48));
+  st_rlx(&s->w[5], tag | ((d ? d->aux : 0) & LK_LOW48));
+  st_rlx(&s->w[6], t + 1);
+  st_rlx(&s->w[7], (uint64_t)0);
 }
 
 /* Returns the first device-side error, or 0. */
@@ -165,9 +172,8 @@ static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* 
     if (t - done >= ctx->R) return LK_EAGAIN;   /* slot t mod R still holds descriptor t-R+1 */
     if (tl.t.compare_exchange_weak(t, t + 1, std::memory_order_acq_rel, std::memory_order_relaxed)) break;
   }
-  lk_slot* s = &ctx->ring_h[(size_t)c * ctx->R + (t & (ctx->R - 1))];
-  fill_slot(s, cmd, d, in0, in1, out);
-  st_rel(&s->seq, t + 1);   /* publish: the device acquires seq, then reads the slot */
+  lk_wire* s = &ctx->ring_h[(size_t)c * ctx->R + (t & (ctx->R - 1))];
+  write_slot(s, t, ctx->R_log2, cmd, d, in0, in1, out);
   *seq_out = t + 1;
   return LK_OK;
 }
@@ -207,12 +213,14 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   uint32_t R = ring_depth_override ? ring_depth_override : (p->ring_depth ? (uint32_t)p->ring_depth : 1024u);
   if (R < 2 || (R & (R - 1)) || R > (1u << 24)) return LK_EINVAL;
   ctx->R = R;
+  ctx->R_log2 = 0;
+  while ((1u << ctx->R_log2) < R) ctx->R_log2++;
   ctx->log_cap = p->exec_log_cap;
-  if (p->flags != 0) return LK_EINVAL;
+  if (p->flags & ~(uint32_t)LK_INIT_DIRECT) return LK_EINVAL;
 
   /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] */
   size_t off_ring = 0;
-  size_t ring_bytes = (size_t)ctx->C * R * sizeof(lk_slot);
+  size_t ring_bytes = (size_t)ctx->C * R * sizeof(lk_wire);
   size_t off_cw = live ? align_up(ring_bytes, LK_LINE) : 0;
   size_t off_ctrl = align_up(off_cw + ctx->C * sizeof(lk_cword), LK_LINE);
   size_t off_info = align_up(off_ctrl + sizeof(lk_ctrl), LK_LINE);
@@ -248,7 +256,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
 
   lk_kargs& a = ctx->args;
   memset(&a, 0, sizeof a);
-  a.ring = (lk_slot*)(live ? (void*)(md + off_ring) : (void*)(db + d_ring));
+  a.ring = (lk_wire*)(live ? (void*)(md + off_ring) : (void*)(db + d_ring));
   a.cword = (lk_cword*)(md + off_cw);
   a.ctrl = (lk_ctrl*)(md + off_ctrl);
   a.info = (lk_cta_info*)(md + off_info);
@@ -263,13 +271,14 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.grid = ctx->G;
   a.total = ctx->total;
   a.ring_mask = R - 1;
+  a.ring_log2 = ctx->R_log2;
   a.log_cap = ctx->log_cap;
-  a.flags = 0;
+  a.flags = (p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u;
   a.backoff_base_ns = p->backoff_base_ns;
   a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;
   a.lease_ns = p->idle_lease_ns ? p->idle_lease_ns : 10000000000ull;
   a.boot_timeout_ns = p->boot_timeout_ns ? p->boot_timeout_ns : 10000000000ull;
-  if (live) ctx->ring_h = (lk_slot*)(mh + off_ring);
+  if (live) ctx->ring_h = (lk_wire*)(mh + off_ring);
 
   ctx->tail = new (std::nothrow) Tail[ctx->C];
   if (!ctx->tail) return LK_ENOMEM;
@@ -475,7 +484,14 @@ int lk_cluster_info(lk_ctx* ctx, int cluster, int* smids, int cap) {
 
 int lk_status(lk_ctx* ctx, int cluster) {
   if (!ctx || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
-  return (int)ld_acq(&ctx->cword_h[cluster].status);
+  /* the device writes the status word only at boot and at exit; in between
+   * Table 1's WORKING / FINISHED follow from the ring counters, which saves
+   * the device two system-scope stores per descriptor */
+  const uint64_t st = ld_acq(&ctx->cword_h[cluster].status);
+  if (st == LK_ST_EXITED || st == LK_ST_ERROR) return (int)st;
+  const uint64_t tail = ctx->tail[cluster].t.load(std::memory_order_acquire);
+  if (tail == 0) return LK_ST_INIT;
+  return ld_acq(&ctx->cword_h[cluster].done) >= tail ? LK_ST_FINISHED : LK_ST_WORKING;
 }
 
 int lk_device_error(lk_ctx* ctx) {
@@ -558,22 +574,20 @@ int lk_run_finite(const lk_init_params* p, const lk_desc* descs, const int* clus
   int rc = setup(ctx, p, false, R);
   if (rc != LK_OK) { teardown(ctx); return rc; }
   /* fill the ring on the host, then copy it into device memory */
-  std::vector<lk_slot> ring((size_t)ctx->C * R);
-  memset(ring.data(), 0, ring.size() * sizeof(lk_slot));
+  std::vector<lk_wire> ring((size_t)ctx->C * R);
+  memset(ring.data(), 0, ring.size() * sizeof(lk_wire));
   std::vector<uint64_t> t(ctx->C, 0);
   for (size_t i = 0; i < count; ++i) {
     int c = cluster_of[i];
-    lk_slot* s = &ring[(size_t)c * R + t[c]];
-    fill_slot(s, LK_CMD_WORK + descs[i].op, &descs[i], in0 ? in0[i] : nullptr,
-              in1 ? in1[i] : nullptr, out ? out[i] : nullptr);
-    s->seq = ++t[c];
+    write_slot(&ring[(size_t)c * R + t[c]], t[c], ctx->R_log2, LK_CMD_WORK + descs[i].op, &descs[i],
+               in0 ? in0[i] : nullptr, in1 ? in1[i] : nullptr, out ? out[i] : nullptr);
+    ++t[c];
   }
   for (int c = 0; c < ctx->C; ++c) {
-    lk_slot* s = &ring[(size_t)c * R + t[c]];
-    fill_slot(s, LK_CMD_EXIT, nullptr, nullptr, nullptr, nullptr);
-    s->seq = ++t[c];
+    write_slot(&ring[(size_t)c * R + t[c]], t[c], ctx->R_log2, LK_CMD_EXIT, nullptr, nullptr, nullptr, nullptr);
+    ++t[c];
   }
-  rc = lkb_copy_h2d(ctx->device, ctx->args.ring, ring.data(), ring.size() * sizeof(lk_slot));
+  rc = lkb_copy_h2d(ctx->device, ctx->args.ring, ring.data(), ring.size() * sizeof(lk_wire));
   if (rc != LK_OK) { teardown(ctx); return rc; }
   beat(ctx);
   rc = lkb_launch_kernel(ctx->device, &ctx->args, ctx->T, &ctx->launch);

@@ -25,6 +25,7 @@ LK_OK, LK_PENDING = 0, 1
 LK_EINVAL, LK_EAGAIN, LK_ETIMEDOUT, LK_EDEVICE, LK_ESTATE, LK_ENOMEM, LK_EBUSY = -1, -2, -3, -4, -5, -6, -7
 LK_ST_INIT, LK_ST_FINISHED, LK_ST_WORKING, LK_ST_NOP, LK_ST_EXITED, LK_ST_ERROR = 0, 1, 2, 4, 8, 32
 LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
+LK_INIT_DIRECT = 1
 LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
 LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING = range(7)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
@@ -136,12 +137,12 @@ def _ptr(x) -> int:
 
 def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
                 backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
-                boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0):
+                boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0):
     """lk_init_params plus the arrays it points to (kept alive by the tuple)."""
     sz = (ctypes.c_int * len(sizes))(*sizes)
     sm = None if smids is None else (ctypes.c_int * len(smids))(*smids)
     p = lk_init_params(device, len(sizes), sz, sm, threads_per_cta, ring_depth, backoff_base_ns, backoff_cap_ns,
-                       idle_lease_ns, boot_timeout_ns, exec_log_cap, 0)
+                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags)
     return p, (sz, sm)
 
 

@@ -36,7 +36,8 @@ def check_log(oracle, ctx, log, sizes, n_posted, posted_op=None):
     return res, pinned
 
 
-def test_config_small_closed_loop(torch_ready, oracle_lib):
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT])
+def test_config_small_closed_loop(torch_ready, oracle_lib, flags):
     """4 SMs as 2 clusters of 2, 256 threads; 10,000 closed-loop int32 adds of
     4096 elements, values uniform in [-2^20, 2^20], seed 0, round-robin."""
     torch = torch_ready
@@ -54,7 +55,7 @@ def test_config_small_closed_loop(torch_ready, oracle_lib):
     items["in1"] = db.data_ptr() + np.arange(N, dtype=np.uint64) * row
     items["out"] = out.data_ptr() + np.arange(N, dtype=np.uint64) * row
     torch.cuda.current_stream().synchronize()
-    with lk.lk_init([2, 2], threads_per_cta=256, exec_log_cap=N, idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init([2, 2], threads_per_cta=256, exec_log_cap=N, idle_lease_ns=5_000_000_000, flags=flags) as c:
         rc, res = lk.lk_run_trace(c, items, n_threads=1, closed_loop=True)
         assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
         log, dropped = lk.lk_exec_log(c)
@@ -65,7 +66,7 @@ def test_config_small_closed_loop(torch_ready, oracle_lib):
         assert len(set(pinned)) == 4          # one CTA per SM
     assert np.array_equal(host(out), oracle_lib.add_i32(a, b))
     lat = (res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0
-    print(f"\nconfig small closed loop: p50 {np.percentile(lat, 50):.2f} us  p99 {np.percentile(lat, 99):.2f} us  "
+    print(f"\nconfig small closed loop (flags {flags}): p50 {np.percentile(lat, 50):.2f} us  p99 {np.percentile(lat, 99):.2f} us  "
           f"max {lat.max():.2f} us")
 
 
@@ -101,7 +102,8 @@ def test_explicit_smid_lists(torch_ready, oracle_lib):
             assert r["smid"] == lists[r["cluster"]][r["rank"]]
 
 
-def test_many_producers_mixed_bodies(torch_ready, oracle_lib):
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT])
+def test_many_producers_mixed_bodies(torch_ready, oracle_lib, flags):
     torch = torch_ready
     sizes = [8, 8, 8, 8]
     n = 65536
@@ -116,7 +118,7 @@ def test_many_producers_mixed_bodies(torch_ready, oracle_lib):
     torch.cuda.current_stream().synchronize()
     posted = {}
     lock = threading.Lock()
-    with lk.lk_init(sizes, exec_log_cap=1024, idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init(sizes, exec_log_cap=1024, idle_lease_ns=5_000_000_000, flags=flags) as c:
         def producer(p):
             for j in range(J):
                 cl = (p + j) % 4
