@@ -410,7 +410,7 @@ def main():
     base = np.concatenate(base)
 
     # ---- dispatch alone: closed-loop NOPs, persistent kernel vs launch+sync ---------
-    nop = np.zeros(20_000, dtype=lk.TRACE_ITEM_DTYPE)
+    nop = np.zeros(2 * items_per_step, dtype=lk.TRACE_ITEM_DTYPE)
     nop["cluster"] = np.arange(nop.size) % 4
     nop["op"] = lk.LK_OP_NOP
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000) as ctx:
@@ -418,9 +418,10 @@ def main():
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT) as ctx:
         rc, r3 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
     rc2, r2 = lk.lk_baseline_run_trace(nop, sizes, threads=cfg["threads"], n_threads=1, device=dev)
-    nop_lk = (r1["t_complete_ns"] - r1["t_submit_ns"])[1000:] / 1000.0
-    nop_direct = (r3["t_complete_ns"] - r3["t_submit_ns"])[1000:] / 1000.0
-    nop_base = (r2["t_complete_ns"] - r2["t_submit_ns"])[1000:] / 1000.0
+    skip = nop.size // 20   # first items warm the path
+    nop_lk = (r1["t_complete_ns"] - r1["t_submit_ns"])[skip:] / 1000.0
+    nop_direct = (r3["t_complete_ns"] - r3["t_submit_ns"])[skip:] / 1000.0
+    nop_base = (r2["t_complete_ns"] - r2["t_submit_ns"])[skip:] / 1000.0
 
     # ---- end to end: host buffers, copies inside the timed path ---------------------
     lim = 256 << 20

@@ -5,23 +5,29 @@
  * the data; the split depends only on (n, S), so a result does not depend on
  * which descriptors ran before or beside it.
  *
+ * Streaming bodies (add, copy, sum, histogram) move a CTA's share through
+ * shared memory: thread 0 issues TMA bulk copies (cp.async.bulk, 16-byte
+ * granules, completion counted on an mbarrier per stage) into a ring of
+ * LK_STAGES stages, so up to three stages (96 KB) per SM are in flight while
+ * every warp consumes the fourth; registers no longer bound the bytes in
+ * flight.  One CTA barrier per chunk both releases the consumed stage for
+ * refill and makes every thread agree on whether the stage arrived in time.
+ *
  * Bodies:
- *   add_i32   out[i] = a[i] + b[i] mod 2^32          (128-bit streaming loads)
- *   copy_i32  out[i] = in[i]
+ *   add_i32   out[i] = a[i] + b[i] mod 2^32: both inputs staged, 128-bit
+ *             streaming stores of the sums
+ *   copy_i32  out[i] = in[i]: staged in, then a bulk store straight from the
+ *             stage (no registers touched)
  *   hist_u8   per-CTA counts -> cluster accumulator (global atomics) -> copied
- *             out by the last CTA.  Small shares count into per-warp bins with
+ *             out by rank 0.  Small shares count into per-warp bins with
  *             shared atomics; large shares count into lane-private packed
  *             16-bit counters, which no two lanes of a warp ever share, so
  *             random bytes cause no shared-memory bank conflicts.
  *   sum_f32   per-thread float accumulators, warp shuffles, per-CTA partial;
- *             the last CTA adds the partials in rank order in binary64
+ *             rank 0 adds the partials in rank order in binary64
  *   gemm64    64x64x64 float32 tiles staged into shared memory by TMA bulk
- *             copies (cp.async.bulk + mbarrier, two stages so the next tile
- *             loads while this one computes), 4x4 register micro-tiles, FFMA
- *             in k order
- * Every streaming loop issues all of a thread's loads for one round (U per
- * thread, predicated on the share's end) before using any of them, so a
- * share of any size costs one memory round trip per round.
+ *             copies (two stages so the next tile loads while this one
+ *             computes), 4x4 register micro-tiles, FFMA in k order
  * Used by the persistent kernel and by the ordinary-launch baseline kernels.
  */
 #ifndef LK_BODIES_CUH
@@ -42,83 +48,164 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
                    (int)((unsigned)x.z + (unsigned)y.z), (int)((unsigned)x.w + (unsigned)y.w));
 }
 
+/* ---- shared-memory layout of a CTA ------------------------------------- */
+#define LK_SMEM_WORK (64u * 1024u)     /* histogram counters or GEMM stages   */
+#define LK_SMEM_STREAM (128u * 1024u)  /* streaming stages                    */
+#define LK_SMEM_DYN (LK_SMEM_WORK + LK_SMEM_STREAM)
+#define LK_STAGES 4u
+#define LK_NUM_BARS 4u                 /* mbarriers: one per stage (GEMM uses two) */
+
+/* Stream the 16-byte vectors [beg, end) of NIN inputs through the stages.
+ * consume(v0, nv, s0, s1) runs on every thread for each chunk: vectors
+ * v0 .. v0+nv-1 of the share sit at s0[0..nv) (and s1[0..nv) for a second
+ * input).  With STORE, consume issues bulk stores from the stage (thread 0)
+ * and a stage is refilled only after those stores have read it.  `phase`
+ * holds one parity bit per mbarrier and persists across descriptors.
+ * Returns false, on every thread alike, if a stage did not arrive before
+ * `deadline`; this CTA's copies in flight are allowed to land first. */
+template <int NIN, bool STORE, class F>
+__device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint64_t beg, uint64_t end,
+                                       unsigned char* stage_mem, uint64_t* bars, uint32_t& phase, uint64_t deadline,
+                                       F&& consume) {
+  constexpr uint32_t stage_vec = LK_SMEM_STREAM / LK_STAGES / NIN / 16u;   /* vectors per input per chunk */
+  const uint64_t total = end > beg ? end - beg : 0;
+  const uint64_t nch = (total + stage_vec - 1) / stage_vec;
+  if (nch == 0) return true;
+  auto sbuf = [&](uint32_t st, int which) {
+    return reinterpret_cast<uint4*>(stage_mem + ((size_t)st * NIN + which) * stage_vec * 16u);
+  };
+  auto issue = [&](uint64_t ch) {   /* thread 0 only */
+    const uint32_t st = (uint32_t)(ch % LK_STAGES);
+    const uint64_t v0 = beg + ch * stage_vec;
+    const uint32_t nv = (uint32_t)((end - v0) < stage_vec ? (end - v0) : stage_vec);
+    mbar_expect_tx(&bars[st], nv * 16u * NIN);
+    bulk_g2s(sbuf(st, 0), in0 + v0, nv * 16u, &bars[st]);
+    if (NIN > 1) bulk_g2s(sbuf(st, 1), in1 + v0, nv * 16u, &bars[st]);
+  };
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();   /* earlier generic writes before these async reads */
+    fence_proxy_async_smem();     /* earlier generic shared accesses before async writes */
+    for (uint64_t ch = 0; ch < nch && ch < LK_STAGES; ++ch) issue(ch);
+  }
+  for (uint64_t ch = 0; ch < nch; ++ch) {
+    const uint32_t st = (uint32_t)(ch % LK_STAGES);
+    const bool ok = mbar_wait(&bars[st], (phase >> st) & 1u, deadline);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        for (uint64_t c2 = ch; c2 < nch && c2 < ch + LK_STAGES; ++c2) {
+          const uint32_t s2 = (uint32_t)(c2 % LK_STAGES);
+          mbar_wait(&bars[s2], (phase >> s2) & 1u, deadline + 1000000000ull);
+        }
+        if (STORE) bulk_wait_all();
+      }
+      __syncthreads();
+      return false;
+    }
+    phase ^= 1u << st;
+    /* every thread has finished chunk ch-1: refill its stage */
+    if (threadIdx.x == 0 && ch >= 1 && ch - 1 + LK_STAGES < nch) {
+      if (STORE) bulk_wait_read_all();
+      fence_proxy_async_smem();
+      issue(ch - 1 + LK_STAGES);
+    }
+    const uint64_t v0 = beg + ch * stage_vec;
+    const uint32_t nv = (uint32_t)((end - v0) < stage_vec ? (end - v0) : stage_vec);
+    consume(v0, nv, sbuf(st, 0), NIN > 1 ? sbuf(st, 1) : nullptr);
+  }
+  __syncthreads();   /* every consumer is done before a later body reuses the stages */
+  if (STORE && threadIdx.x == 0) {
+    bulk_wait_all();
+    fence_proxy_async_global();   /* the stores' writes before this thread's later release */
+  }
+  return true;
+}
+
 /* ---- int32 add / copy -------------------------------------------------- */
-template <int U, bool ADD>
-__device__ __forceinline__ void body_add_copy(const lk_slot& d, int r, int S) {
-  const uint64_t n = d.n;
-  const int4* a = reinterpret_cast<const int4*>(d.in0);
-  const int4* b = reinterpret_cast<const int4*>(d.in1);
-  int4* o = reinterpret_cast<int4*>(d.out);
-  const uint64_t nv = n >> 2;
+__device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                         uint32_t& phase, uint64_t deadline) {
+  const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
+  int4* o = reinterpret_cast<int4*>(d.out);
   const uint32_t T = blockDim.x;
-  for (uint64_t base = beg + threadIdx.x; base < end; base += (uint64_t)U * T) {
-    int4 x[U], y[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + (uint64_t)u * T;
-      if (i < end) {
-        x[u] = ld_stream(a + i);
-        if (ADD) y[u] = ld_stream(b + i);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + (uint64_t)u * T;
-      if (i < end) st_stream(o + i, ADD ? add4(x[u], y[u]) : x[u]);
-    }
-  }
+  const bool ok = stream<2, false>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
+                                   beg, end, dsm + LK_SMEM_WORK, bars, phase, deadline,
+                                   [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
+                                     const int4* a = reinterpret_cast<const int4*>(s0);
+                                     const int4* b = reinterpret_cast<const int4*>(s1);
+                                     for (uint32_t v = threadIdx.x; v < cnt; v += T) st_stream(o + v0 + v, add4(a[v], b[v]));
+                                   });
   if (r == S - 1) {
     const int32_t* as = reinterpret_cast<const int32_t*>(d.in0);
     const int32_t* bs = reinterpret_cast<const int32_t*>(d.in1);
     int32_t* os = reinterpret_cast<int32_t*>(d.out);
-    for (uint64_t j = nv * 4 + threadIdx.x; j < n; j += T)
-      os[j] = ADD ? (int32_t)((uint32_t)as[j] + (uint32_t)bs[j]) : as[j];
+    for (uint64_t j = nv * 4 + threadIdx.x; j < n; j += T) os[j] = (int32_t)((uint32_t)as[j] + (uint32_t)bs[j]);
   }
+  return ok;
+}
+
+__device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                          uint32_t& phase, uint64_t deadline) {
+  const uint64_t n = d.n, nv = n >> 2;
+  uint64_t beg, end;
+  share(nv, r, S, beg, end);
+  uint4* o = reinterpret_cast<uint4*>(d.out);
+  const bool ok = stream<1, true>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars,
+                                  phase, deadline, [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4*) {
+                                    if (threadIdx.x == 0) {
+                                      bulk_s2g(o + v0, s0, cnt * 16u);
+                                      bulk_commit();
+                                    }
+                                  });
+  if (r == S - 1) {
+    const int32_t* as = reinterpret_cast<const int32_t*>(d.in0);
+    int32_t* os = reinterpret_cast<int32_t*>(d.out);
+    for (uint64_t j = nv * 4 + threadIdx.x; j < n; j += blockDim.x) os[j] = as[j];
+  }
+  return ok;
 }
 
 /* ---- float32 sum: this CTA's partial (valid in thread 0) ---------------- */
-template <int U>
-__device__ __forceinline__ float body_sum_partial(const lk_slot& d, int r, int S, float* red) {
-  const uint64_t n = d.n;
-  const float4* x = reinterpret_cast<const float4*>(d.in0);
-  const uint64_t nv = n >> 2;
+__device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                         uint32_t& phase, uint64_t deadline, float* red, float* partial_out) {
+  const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   const uint32_t T = blockDim.x;
-  float acc[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) acc[u] = 0.f;
-  for (uint64_t base = beg + threadIdx.x; base < end; base += (uint64_t)U * T) {
-    float4 v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + (uint64_t)u * T;
-      v[u] = i < end ? ld_stream(x + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] += (v[u].x + v[u].y) + (v[u].z + v[u].w);
-  }
+  float acc0 = 0.f, acc1 = 0.f;
+  const bool ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK,
+                                   bars, phase, deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                                     const float4* x = reinterpret_cast<const float4*>(s0);
+                                     uint32_t v = threadIdx.x;
+                                     for (; v + T < cnt; v += 2 * T) {
+                                       const float4 p = x[v], q = x[v + T];
+                                       acc0 += (p.x + p.y) + (p.z + p.w);
+                                       acc1 += (q.x + q.y) + (q.z + q.w);
+                                     }
+                                     if (v < cnt) {
+                                       const float4 p = x[v];
+                                       acc0 += (p.x + p.y) + (p.z + p.w);
+                                     }
+                                   });
   if (r == S - 1) {
     const float* xs = reinterpret_cast<const float*>(d.in0);
-    for (uint64_t j = nv * 4 + threadIdx.x; j < n; j += T) acc[0] += xs[j];
+    for (uint64_t j = nv * 4 + threadIdx.x; j < n; j += T) acc0 += xs[j];
   }
-  float s = acc[0];
-#pragma unroll
-  for (int u = 1; u < U; ++u) s += acc[u];
+  float s = acc0 + acc1;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[warp] = s;
   __syncthreads();
-  float t = 0.f;
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
+    float t = 0.f;
     for (uint32_t w = 0; w < T / 32; ++w) t += red[w];
-  return t;
+    *partial_out = t;
+  }
+  return ok;
 }
 
-/* Last CTA of the cluster: out[0] = partials added in rank order (binary64). */
+/* Rank 0: out[0] = partials added in rank order (binary64). */
 __device__ __forceinline__ void combine_sum(const lk_slot& d, const float* partial, int S) {
   if (threadIdx.x >= 32) return;
   const uint32_t lane = threadIdx.x;
@@ -130,8 +217,8 @@ __device__ __forceinline__ void combine_sum(const lk_slot& d, const float* parti
 }
 
 /* ---- uint8 histogram ---------------------------------------------------- */
-/* Shares below this many bytes per CTA use the per-warp-bin path, whose set-up
- * and read-out are cheap; larger shares use the conflict-free path. */
+/* Shares below this many bytes per CTA use per-warp bins, whose set-up and
+ * read-out are cheap; larger shares use the conflict-free lane-private path. */
 #define LK_HIST_SMALL_BYTES (64u * 1024u)
 #define LK_HIST_COPIES 4u      /* lane-private counter copies (16 KB each)   */
 
@@ -146,9 +233,9 @@ __device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
 }
 
-/* Lane-private counters: word ((v & 127) << 5) | lane of a copy holds bins v
- * (low 16 bits, v < 128) and v (high 16 bits, v >= 128) for this lane alone;
- * lane l only touches bank l. */
+/* Lane-private counters: word ((v & 127) << 5) | lane of a copy holds bin v
+ * (low 16 bits if v < 128, high 16 bits otherwise) for this lane alone; lane
+ * l only touches bank l. */
 __device__ __forceinline__ void count4_lane(uint32_t* lane_base, uint32_t w) {
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -157,122 +244,107 @@ __device__ __forceinline__ void count4_lane(uint32_t* lane_base, uint32_t w) {
   }
 }
 
-template <int U>
-__device__ __forceinline__ void hist_small(const lk_slot& d, uint64_t beg, uint64_t end, bool tail, uint32_t* sh,
-                                           uint32_t* acc) {
-  const uint32_t T = blockDim.x, W = T / 32;
-  for (uint32_t i = threadIdx.x; i < W * 256; i += T) sh[i] = 0;
-  __syncthreads();
-  uint32_t* bins = sh + (threadIdx.x >> 5) * 256;
-  const uint4* x = reinterpret_cast<const uint4*>(d.in0);
-  for (uint64_t base = beg + threadIdx.x; base < end; base += (uint64_t)U * T) {
-    uint4 v[U];
+/* Add the lane-private counters into tot_lo / tot_hi (rows owned by threads
+ * < 128: bin `row` and bin `row + 128`).  A warp's loads start at
+ * row-dependent columns so they spread over all banks. */
+__device__ __forceinline__ void hist_readout(const uint32_t* sh, uint32_t& tot_lo, uint32_t& tot_hi) {
+  for (uint32_t row = threadIdx.x; row < 128; row += blockDim.x) {
+    for (uint32_t c = 0; c < LK_HIST_COPIES; ++c) {
+      const uint4* rw = reinterpret_cast<const uint4*>(sh + c * 4096u + row * 32u);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + (uint64_t)u * T;
-      if (i < end) v[u] = ld_stream(x + i);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (base + (uint64_t)u * T < end) {
-        count4_warp(bins, v[u].x);
-        count4_warp(bins, v[u].y);
-        count4_warp(bins, v[u].z);
-        count4_warp(bins, v[u].w);
+      for (uint32_t j = 0; j < 8; ++j) {
+        const uint4 q = rw[(j + row) & 7u];
+        tot_lo += (q.x & 0xffffu) + (q.y & 0xffffu) + (q.z & 0xffffu) + (q.w & 0xffffu);
+        tot_hi += (q.x >> 16) + (q.y >> 16) + (q.z >> 16) + (q.w >> 16);
       }
     }
-  }
-  if (tail) {
-    const uint8_t* xb = reinterpret_cast<const uint8_t*>(d.in0);
-    for (uint64_t j = (d.n >> 4) * 16 + threadIdx.x; j < d.n; j += T) atomicAdd(&bins[xb[j]], 1u);
-  }
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < 256; v += T) {
-    uint32_t s = 0;
-    for (uint32_t w = 0; w < W; ++w) s += sh[w * 256 + v];
-    if (s) atomicAdd(&acc[v], s);
   }
 }
 
-template <int U>
-__device__ __forceinline__ void hist_large(const lk_slot& d, uint64_t beg, uint64_t end, bool tail, uint32_t* sh,
-                                           uint32_t* acc) {
-  const uint32_t T = blockDim.x, W = T / 32;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t copy = (threadIdx.x >> 5) % LK_HIST_COPIES;
-  uint32_t* lane_base = sh + copy * 4096u + lane;
-  /* a 16-bit counter takes at most 65535 increments between read-outs: every
-   * lane word is shared by ceil(W / copies) threads */
-  const uint32_t sharers = (W + LK_HIST_COPIES - 1) / LK_HIST_COPIES;
-  const uint64_t per_thread = 65535u / sharers / 16u;     /* vectors per thread per round */
-  const uint64_t chunk = per_thread * T;
-  const uint4* x = reinterpret_cast<const uint4*>(d.in0);
-  uint32_t tot_lo = 0, tot_hi = 0;   /* bins row and row+128, rows owned by threads < 128 */
-  uint64_t cbeg = beg;
-  do {
-    const uint64_t cend = (end - cbeg > chunk) ? cbeg + chunk : end;
-    uint4* z = reinterpret_cast<uint4*>(sh);
-    for (uint32_t i = threadIdx.x; i < LK_HIST_COPIES * 1024u; i += T) z[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    for (uint64_t base = cbeg + threadIdx.x; base < cend; base += (uint64_t)U * T) {
-      uint4 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t i = base + (uint64_t)u * T;
-        if (i < cend) v[u] = ld_stream(x + i);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (base + (uint64_t)u * T < cend) {
-          count4_lane(lane_base, v[u].x);
-          count4_lane(lane_base, v[u].y);
-          count4_lane(lane_base, v[u].z);
-          count4_lane(lane_base, v[u].w);
-        }
-      }
-    }
-    if (tail && cend == end) {
-      const uint8_t* xb = reinterpret_cast<const uint8_t*>(d.in0);
-      for (uint64_t j = (d.n >> 4) * 16 + threadIdx.x; j < d.n; j += T) {
-        const uint32_t v = xb[j];
-        red_add_shared(lane_base + ((v & 127u) << 5), 1u << ((v >> 7) << 4));
-      }
-    }
-    __syncthreads();
-    /* read-out: thread `row` < 128 adds the 32 lane words of its row in every
-     * copy, 16 bytes at a time, starting at a row-dependent column so that a
-     * warp's loads spread over all banks */
-    for (uint32_t row = threadIdx.x; row < 128; row += T) {
-      for (uint32_t c = 0; c < LK_HIST_COPIES; ++c) {
-        const uint4* rw = reinterpret_cast<const uint4*>(sh + c * 4096u + row * 32u);
-#pragma unroll
-        for (uint32_t j = 0; j < 8; ++j) {
-          const uint4 q = rw[(j + row) & 7u];
-          tot_lo += (q.x & 0xffffu) + (q.y & 0xffffu) + (q.z & 0xffffu) + (q.w & 0xffffu);
-          tot_hi += (q.x >> 16) + (q.y >> 16) + (q.z >> 16) + (q.w >> 16);
-        }
-      }
-    }
-    __syncthreads();
-    cbeg = cend;
-  } while (cbeg < end);
-  for (uint32_t row = threadIdx.x; row < 128; row += T) {
-    if (tot_lo) atomicAdd(&acc[row], tot_lo);
-    if (tot_hi) atomicAdd(&acc[row + 128], tot_hi);
-  }
+__device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
+  uint4* z = reinterpret_cast<uint4*>(sh);
+  for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
 }
 
-template <int U>
-__device__ __forceinline__ void body_hist(const lk_slot& d, int r, int S, uint32_t* sh, uint32_t* acc) {
+__device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                          uint32_t& phase, uint64_t deadline, uint32_t* acc) {
   const uint64_t nv = d.n >> 4;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   const bool tail = (r == S - 1) && (d.n & 15);
-  if ((end - beg) * 16 < LK_HIST_SMALL_BYTES) hist_small<U>(d, beg, end, tail, sh, acc);
-  else hist_large<U>(d, beg, end, tail, sh, acc);
+  const uint32_t T = blockDim.x, W = T / 32, lane = threadIdx.x & 31;
+  uint32_t* sh = reinterpret_cast<uint32_t*>(dsm);
+  const uint8_t* xb = reinterpret_cast<const uint8_t*>(d.in0);
+  bool ok;
+  if ((end - beg) * 16 < LK_HIST_SMALL_BYTES) {
+    hist_zero(sh, W * 256);
+    __syncthreads();
+    uint32_t* bins = sh + (threadIdx.x >> 5) * 256;
+    ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars, phase,
+                          deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                            for (uint32_t v = threadIdx.x; v < cnt; v += T) {
+                              const uint4 q = s0[v];
+                              count4_warp(bins, q.x);
+                              count4_warp(bins, q.y);
+                              count4_warp(bins, q.z);
+                              count4_warp(bins, q.w);
+                            }
+                          });
+    if (tail)
+      for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T) atomicAdd(&bins[xb[j]], 1u);
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < 256; v += T) {
+      uint32_t s = 0;
+      for (uint32_t w = 0; w < W; ++w) s += sh[w * 256 + v];
+      if (s) atomicAdd(&acc[v], s);
+    }
+    return ok;
+  }
+  /* large share: lane-private packed 16-bit counters.  A counter takes at
+   * most 65535 increments between read-outs; each lane word is shared by the
+   * ceil(W / copies) warps that use the same copy. */
+  const uint32_t copy = (threadIdx.x >> 5) % LK_HIST_COPIES;
+  uint32_t* lane_base = sh + copy * 4096u + lane;
+  const uint32_t sharers = (W + LK_HIST_COPIES - 1) / LK_HIST_COPIES;
+  const uint32_t limit = 65535u / sharers / 16u;   /* vectors per thread between read-outs */
+  uint32_t since = 0, tot_lo = 0, tot_hi = 0;
+  hist_zero(sh, LK_HIST_COPIES * 4096u);
+  __syncthreads();
+  ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars, phase,
+                        deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                          const uint32_t per = (cnt + T - 1) / T;
+                          if (since + per > limit) {   /* same decision on every thread */
+                            __syncthreads();
+                            hist_readout(sh, tot_lo, tot_hi);
+                            __syncthreads();
+                            hist_zero(sh, LK_HIST_COPIES * 4096u);
+                            __syncthreads();
+                            since = 0;
+                          }
+                          for (uint32_t v = threadIdx.x; v < cnt; v += T) {
+                            const uint4 q = s0[v];
+                            count4_lane(lane_base, q.x);
+                            count4_lane(lane_base, q.y);
+                            count4_lane(lane_base, q.z);
+                            count4_lane(lane_base, q.w);
+                          }
+                          since += per;
+                        });
+  if (tail)
+    for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T) {
+      const uint32_t v = xb[j];
+      red_add_shared(lane_base + ((v & 127u) << 5), 1u << ((v >> 7) << 4));
+    }
+  __syncthreads();
+  hist_readout(sh, tot_lo, tot_hi);
+  for (uint32_t row = threadIdx.x; row < 128; row += T) {
+    if (tot_lo) atomicAdd(&acc[row], tot_lo);
+    if (tot_hi) atomicAdd(&acc[row + 128], tot_hi);
+  }
+  return ok;
 }
 
-/* Last CTA: copy the accumulator out and return it to zero for reuse. */
+/* Rank 0: copy the accumulator out and return it to zero for reuse. */
 __device__ __forceinline__ void combine_hist(const lk_slot& d, uint32_t* acc) {
   int32_t* out = reinterpret_cast<int32_t*>(d.out);
   for (uint32_t v = threadIdx.x; v < 256; v += blockDim.x) {
@@ -390,10 +462,8 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   return ok;
 }
 
-/* Shared-memory bytes a body needs (histogram counters or GEMM stages). */
-__host__ __device__ constexpr uint32_t body_smem_bytes(int threads) {
-  return (uint32_t)(threads / 32) * 1024u > 65536u ? (uint32_t)(threads / 32) * 1024u : 65536u;
-}
+/* Dynamic shared memory every body launch asks for. */
+__host__ __device__ constexpr uint32_t body_smem_bytes(int) { return LK_SMEM_DYN; }
 
 }  // namespace lk
 #endif

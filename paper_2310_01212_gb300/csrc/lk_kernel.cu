@@ -237,38 +237,23 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
   }
 }
 
-/* Unroll depth (vectors in flight per thread per round) per body: the same
- * bytes in flight per SM for every block size. */
-template <int MAXT> struct Unroll {
-  static constexpr int two_streams = 2048 / MAXT;   /* add: 2 loads per vector   */
-  static constexpr int one_stream = 4096 / MAXT;    /* copy, sum                 */
-  static constexpr int hist = 1024 / MAXT;        /* counting, not loads, bounds it */
-};
-
 /* This CTA's share of descriptor d (rank r of S).  Returns an LK_DERR_* code
  * or 0.  `partial_out` receives the sum body's per-CTA partial. */
-template <int MAXT>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                         uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
+  const uint64_t deadline = gtime() + 2000000000ull;
+  bool ok = true;
   switch (op) {
-    case LK_OP_ADD_I32: body_add_copy<Unroll<MAXT>::two_streams, true>(d, r, S); return 0;
-    case LK_OP_COPY_I32: body_add_copy<Unroll<MAXT>::one_stream, false>(d, r, S); return 0;
-    case LK_OP_SUM_F32: {
-      const float p = body_sum_partial<Unroll<MAXT>::one_stream>(d, r, S, red);
-      if (threadIdx.x == 0) *partial_out = p;
-      return 0;
-    }
-    case LK_OP_HIST_U8:
-      body_hist<Unroll<MAXT>::hist>(d, r, S, reinterpret_cast<uint32_t*>(dsm), hist_acc);
-      return 0;
-    case LK_OP_GEMM64_F32:
-      return body_gemm(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, gtime() + 2000000000ull)
-                 ? 0
-                 : LK_DERR_STAGING;
-    case LK_OP_NOP: return 0;
+    case LK_OP_ADD_I32: ok = body_add(d, r, S, dsm, bars, phase, deadline); break;
+    case LK_OP_COPY_I32: ok = body_copy(d, r, S, dsm, bars, phase, deadline); break;
+    case LK_OP_SUM_F32: ok = body_sum(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
+    case LK_OP_HIST_U8: ok = body_hist(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
+    case LK_OP_GEMM64_F32: ok = body_gemm(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline); break;
+    case LK_OP_NOP: break;
     default: return LK_DERR_BADDESC;
   }
+  return ok ? 0 : LK_DERR_STAGING;
 }
 
 template <int MAXT>
@@ -277,7 +262,7 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
   __shared__ __align__(64) lk_slot s_desc;
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bars[2];
+  __shared__ __align__(8) uint64_t s_bars[LK_NUM_BARS];
   __shared__ uint64_t s_tstart;
   const uint32_t tid = threadIdx.x;
 
@@ -331,8 +316,7 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     } else if (rk == 0) {
       st_relaxed_sys(&a.cword[c].status, LK_ST_INIT);
     }
-    mbar_init(&s_bars[0], 1);
-    mbar_init(&s_bars[1], 1);
+    for (uint32_t i = 0; i < LK_NUM_BARS; ++i) mbar_init(&s_bars[i], 1);
     fence_barrier_init();
     red_release_sys_add(&a.ctrl->booted, 1u);
   }
@@ -394,7 +378,7 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+    const int berr = run_body(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -467,20 +451,18 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch* sc) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bars[2];
+  __shared__ __align__(8) uint64_t s_bars[LK_NUM_BARS];
   __shared__ int32_t s_last;
   const int r = blockIdx.x, S = gridDim.x;
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  if (op == LK_OP_GEMM64_F32) {
-    if (threadIdx.x == 0) {
-      mbar_init(&s_bars[0], 1);
-      mbar_init(&s_bars[1], 1);
-      fence_barrier_init();
-    }
-    __syncthreads();
+  if (op == LK_OP_NOP) return;
+  if (threadIdx.x == 0) {
+    for (uint32_t i = 0; i < LK_NUM_BARS; ++i) mbar_init(&s_bars[i], 1);
+    fence_barrier_init();
   }
+  __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
+  run_body(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -781,7 +763,7 @@ void pin_cpu(int cpu) {
 }
 cudaError_t launch_ordinary(const lk_slot& d, int grid, int threads, lk_scratch* sc, cudaStream_t s) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  const size_t smem = (op == LK_OP_HIST_U8 || op == LK_OP_GEMM64_F32) ? lk::body_smem_bytes(threads) : 0;
+  const size_t smem = op == LK_OP_NOP ? 0 : lk::body_smem_bytes(threads);
   if (threads <= 256) lk_ordinary<256><<<grid, threads, smem, s>>>(d, sc);
   else if (threads <= 512) lk_ordinary<512><<<grid, threads, smem, s>>>(d, sc);
   else lk_ordinary<1024><<<grid, threads, smem, s>>>(d, sc);
