@@ -312,6 +312,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lk", choices=["lk", "reference"])
     ap.add_argument("--items", type=int, default=ITEMS_PER_STEP)
+    ap.add_argument("--iso-periods", type=int, default=2000, help="critical periods (1 ms each) per isolation run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist = Dist()
@@ -445,6 +446,55 @@ def main():
     h2d = int(e2e_it["in0_bytes"].sum() + e2e_it["in1_bytes"].sum())
     d2h = int(e2e_it["out_bytes"].sum())
 
+    # ---- isolation: critical 16-SM cluster vs best-effort 132-SM cluster -----------
+    iso = wl.ISOLATION
+    crit_out = torch.zeros(4, device="cuda")
+    copy_src = torch.empty(iso["copy_n"], dtype=torch.int32, device="cuda")
+    copy_dst = torch.empty_like(copy_src)
+    hist_in = pools.u8[: iso["hist_n"]]
+    hist_out = torch.zeros(256, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    periods = args.iso_periods
+    iso_res = {}
+    for loaded in (False, True):
+        be_items = 0
+        if loaded:
+            # enough best-effort work to outlast the critical run: time one pair first
+            with lk.lk_init(iso["sizes"], device=dev, idle_lease_ns=5_000_000_000) as ctx:
+                probe_tr = wl.isolation_traces(1, 4, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out)
+                rc, rp = lk.lk_run_trace(ctx, probe_tr[1:], n_threads=1, closed_loop=True)
+            pair_ns = float(rp["t_complete_ns"][-1]) / 2.0
+            be_items = int(2 * periods * iso["period_ns"] / max(pair_ns, 1.0) * 1.1) + 4
+        tr = wl.isolation_traces(periods, be_items, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out,
+                                 loaded=loaded)
+        with lk.lk_init(iso["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000) as ctx:
+            rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000)
+        if rc != lk.LK_OK:
+            raise RuntimeError(f"isolation trace failed: {lk.lk_strerror(rc)}")
+        crit = rr[:periods]
+        lat_c = (crit["t_complete_ns"] - crit["t_submit_ns"]) / 1000.0
+        rel_c = (crit["t_complete_ns"] - tr["t_arrival_ns"][:periods]) / 1000.0
+        key = "loaded" if loaded else "alone"
+        iso_res[key + "_us"] = lat_summary(lat_c)
+        iso_res[key + "_release_to_complete_us"] = lat_summary(rel_c)
+        if loaded:
+            be = rr[periods:]
+            be_ops = tr["op"][periods:]
+            moved = np.where(be_ops == lk.LK_OP_COPY_I32, 8.0 * iso["copy_n"], float(iso["hist_n"] + 1024)).sum()
+            span = float(be["t_complete_ns"].max() - be["t_submit_ns"].min())
+            iso_res["best_effort_gbs"] = moved / span
+            iso_res["best_effort_items"] = int(be.size)
+            last_crit = float(crit["t_complete_ns"].max())
+            iso_res["load_covered_critical_run"] = bool(float(be["t_complete_ns"].max()) >= last_crit)
+    iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
+    iso_res["inflation_max"] = iso_res["loaded_us"]["max"] / iso_res["alone_us"]["max"]
+    iso_res["periods"] = periods
+    iso_sum_ok = abs(float(crit_out[0].cpu()) - oracle.sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())) <= \
+        1e-4 * oracle.abs_sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())
+    iso_copy_ok = bool(torch.equal(copy_dst[-(1 << 20):], copy_src[-(1 << 20):]))
+    iso_res["parity"] = {"critical_sum_ok": bool(iso_sum_ok), "copy_tail_ok": iso_copy_ok}
+    del copy_src, copy_dst
+
     # ---- body bandwidth (finite mode) and the roofline ------------------------------
     bw = body_bandwidth(pools, lk, n_sms)
     peaks, peak_src = measured_peaks()
@@ -502,6 +552,7 @@ def main():
         "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
                 "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy"},
+        "isolation": iso_res,
         "gpu_launches": args.steps,
         "gpu_launches_note": "one persistent-kernel launch per timed step; items need no launch",
         "clocks": clk,

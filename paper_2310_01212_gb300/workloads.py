@@ -12,6 +12,11 @@ Configurations (all seeded):
              one 64x64x64 float32 GEMM tile of N(0,1) values; Poisson
              arrivals at 20,000 per second; round-robin clusters; one host
              submitter thread per cluster.
+  isolation  a critical cluster of 16 SMs releases an FP32 sum over 1 MB
+             (262,144 N(0,1) values) every 1 ms, waiting for each; a
+             best-effort cluster of 132 SMs runs int32 copies of 4 GiB and
+             histograms of 256 MiB back to back; the critical latencies are
+             measured alone and under that load.
 Inputs of full_chip items are slices of device pools much larger than L2
 (129 MB on GB300) at random 16-byte-aligned offsets, so every item reads
 from HBM.
@@ -27,6 +32,8 @@ from . import lk, synth
 SMALL = dict(sizes=[2, 2], threads=256, items=10_000, n=4096, lo=-(1 << 20), hi=1 << 20, seed=0)
 FULL_CHIP = dict(sizes=[37, 37, 37, 37], threads=256, rate_per_s=20_000.0, n_add=65_536, n_hist=1 << 20,
                  n_sum=65_536, gemm_tiles=1, seed=0)
+ISOLATION = dict(sizes=[16, 132], threads=256, period_ns=1_000_000, crit_n=262_144, copy_n=1 << 30,
+                 hist_n=256 << 20, seed=0)
 OPS4 = (lk.LK_OP_ADD_I32, lk.LK_OP_HIST_U8, lk.LK_OP_SUM_F32, lk.LK_OP_GEMM64_F32)
 
 
@@ -201,3 +208,28 @@ def small_inputs(cfg: dict = SMALL):
     a = synth.int32_uniform(cfg["seed"], 1, N * n, cfg["lo"], cfg["hi"]).reshape(N, n)
     b = synth.int32_uniform(cfg["seed"], 2, N * n, cfg["lo"], cfg["hi"]).reshape(N, n)
     return a, b
+
+
+def isolation_traces(periods: int, be_items: int, crit_in, crit_out, copy_src, copy_dst, hist_in, hist_out,
+                     cfg: dict = ISOLATION, loaded: bool = True):
+    """Trace of the isolation configuration: cluster 0 releases a sum every
+    period (absolute release times); cluster 1 (if loaded) runs copies and
+    histograms alternately, all released at time 0 (each starts when the one
+    before it finished, in closed-loop mode)."""
+    crit = np.zeros(periods, dtype=lk.TRACE_ITEM_DTYPE)
+    crit["t_arrival_ns"] = np.arange(periods, dtype=np.uint64) * np.uint64(cfg["period_ns"])
+    crit["cluster"] = 0
+    crit["op"] = lk.LK_OP_SUM_F32
+    crit["n"] = cfg["crit_n"]
+    crit["in0"] = crit_in.data_ptr()
+    crit["out"] = crit_out.data_ptr()
+    if not loaded:
+        return crit
+    be = np.zeros(be_items, dtype=lk.TRACE_ITEM_DTYPE)
+    be["cluster"] = 1
+    copy = (np.arange(be_items) % 2) == 0
+    be["op"] = np.where(copy, lk.LK_OP_COPY_I32, lk.LK_OP_HIST_U8)
+    be["n"] = np.where(copy, copy_src.numel(), hist_in.numel())
+    be["in0"] = np.where(copy, copy_src.data_ptr(), hist_in.data_ptr())
+    be["out"] = np.where(copy, copy_dst.data_ptr(), hist_out.data_ptr())
+    return np.concatenate([crit, be])
