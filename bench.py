@@ -313,6 +313,8 @@ def main():
     ap.add_argument("--impl", default="lk", choices=["lk", "reference"])
     ap.add_argument("--items", type=int, default=ITEMS_PER_STEP)
     ap.add_argument("--iso-periods", type=int, default=2000, help="critical periods (1 ms each) per isolation run")
+    ap.add_argument("--batches", type=int, default=8, help="batches of the batching stream to time")
+    ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of arrivals per serving rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist = Dist()
@@ -446,6 +448,71 @@ def main():
     h2d = int(e2e_it["in0_bytes"].sum() + e2e_it["in1_bytes"].sum())
     d2h = int(e2e_it["out_bytes"].sum())
 
+    # ---- batching: one post per batch vs one CUDA graph of ordinary launches -------
+    from paper_2310_01212_gb300 import autotune
+
+    tuned = autotune.load()
+    bbat = [wl.batching_batch(pools, seed, b) for b in range(args.batches)]
+    par_items, par_meta = wl.batching_parity_batch(pools, seed)
+    torch.cuda.synchronize()
+    lk_s = []
+    with lk.lk_init([n_sms], device=dev, threads_per_cta=tuned["threads"], max_batch_units=1 << 16,
+                    idle_lease_ns=30_000_000_000) as ctx:
+        h = lk.lk_submit_batch(ctx, 0, par_items, max_parts=tuned["max_parts"], part_bytes=tuned["part_bytes"])
+        if lk.lk_wait(ctx, h, 60_000_000_000) != lk.LK_OK:
+            raise RuntimeError("parity batch did not finish")
+        # check now: the timed batches below write into the same output arenas
+        torch.cuda.current_stream().synchronize()
+        batch_bad = wl.check_batching_parity(pools, par_meta, oracle)
+        for items, _ in bbat:
+            t0 = time.perf_counter_ns()
+            h = lk.lk_submit_batch(ctx, 0, items, max_parts=tuned["max_parts"], part_bytes=tuned["part_bytes"])
+            if h is None or lk.lk_wait(ctx, h, 120_000_000_000) != lk.LK_OK:
+                raise RuntimeError("batch did not finish")
+            lk_s.append((time.perf_counter_ns() - t0) / 1e9)
+    graph_s = []
+    for items, _ in bbat:
+        ms = lk.lk_baseline_graph(items, n_sms, threads=tuned["threads"], reps=2, device=dev)
+        graph_s.append(float(ms[-1]) / 1e3)
+    bbytes = np.array([m["bytes"] for _, m in bbat])
+    bcount = np.array([len(it) for it, _ in bbat])
+    batching = {"batches": len(bbat), "items": int(bcount.sum()), "bytes": float(bbytes.sum()),
+                "items_per_batch": bcount.tolist(),
+                "lk_gbs": float(bbytes.sum() / np.sum(lk_s) / 1e9),
+                "graph_gbs": float(bbytes.sum() / np.sum(graph_s) / 1e9),
+                "lk_items_per_s": float(bcount.sum() / np.sum(lk_s)),
+                "graph_items_per_s": float(bcount.sum() / np.sum(graph_s)),
+                "lk_batch_ms": [round(1e3 * x, 3) for x in lk_s], "graph_batch_ms": [round(1e3 * x, 3) for x in graph_s],
+                "tuned": tuned, "cluster": f"{n_sms} SMs as one cluster",
+                "parity_mismatches": batch_bad, "parity_items": int(len(par_items)),
+                "sample": f"seeded prefix: {len(bbat)} batches of the 1M-descriptor stream"}
+
+    # ---- serving: continuous admission under open-loop arrivals, per rate ----------
+    scfg = wl.SERVING
+    arena = torch.empty(scfg["arena_bytes"], dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    serving = {"budget_bytes": scfg["budget_bytes"], "arena_bytes": scfg["arena_bytes"],
+               "chunk_bytes": scfg["chunk_bytes"], "window": scfg["window"], "producers": scfg["producers"],
+               "seconds_per_rate": args.serve_seconds, "partition": "4 clusters x 37 SMs", "rates": {}}
+    with lk.lk_init(scfg["sizes"], device=dev, threads_per_cta=scfg["threads"], idle_lease_ns=30_000_000_000) as ctx:
+        for rate in scfg["rates"]:
+            reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
+            rc, res = lk.lk_serve(ctx, reqs, n_producers=scfg["producers"], budget_bytes=scfg["budget_bytes"],
+                                  arena=arena, arena_bytes=scfg["arena_bytes"], window=scfg["window"],
+                                  chunk_bytes=scfg["chunk_bytes"], timeout_ns=300_000_000_000)
+            if rc != lk.LK_OK:
+                raise RuntimeError(f"serving at {rate}/s failed: {lk.lk_strerror(rc)}")
+            lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
+            wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
+            span = float(res["t_complete_ns"].max()) / 1e9
+            serving["rates"][str(rate)] = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
+                                           "admission_wait_us": lat_summary(wait_s),
+                                           "throughput_req_per_s": reqs.size / span,
+                                           "throughput_gbs": float(inb.sum()) / span / 1e9,
+                                           "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
+                                           "chunks": int(res["chunks"].sum())}
+    del arena
+
     # ---- isolation: critical 16-SM cluster vs best-effort 132-SM cluster -----------
     iso = wl.ISOLATION
     crit_out = torch.zeros(4, device="cuda")
@@ -552,6 +619,8 @@ def main():
         "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
                 "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy"},
+        "batching": batching,
+        "serving": serving,
         "isolation": iso_res,
         "gpu_launches": args.steps,
         "gpu_launches_note": "one persistent-kernel launch per timed step; items need no launch",

@@ -80,7 +80,11 @@ extern "C" {
 #define LK_OP_SUM_F32    3 /* out[0] = sum of n float32 (fixed order for a given n and cluster size) */
 #define LK_OP_GEMM64_F32 4 /* n tiles: out[t] = in0[t] x in1[t], 64x64 row-major float32 tiles, FFMA */
 #define LK_OP_COPY_I32   5 /* out[i] = in0[i], int32; n elements             */
-#define LK_OP_COUNT      6
+#define LK_OP_COMBINE_SUM  6 /* out[0] = binary64 sum of n float32 partials, one at the start of each */
+                             /* 16-byte slot of in0 (fixed order)            */
+#define LK_OP_COMBINE_HIST 7 /* out[v] = sum over j < n of in0[256 j + v] (n int32 histograms) */
+#define LK_OP_COUNT      8
+#define LK_OP_BATCH      8 /* a batch posted by lk_submit_batch (one descriptor, many items) */
 
 /* ---- device-side error reasons (lk_device_error) ---------------------- */
 #define LK_DERR_NONE     0
@@ -115,6 +119,9 @@ typedef struct {
   uint64_t boot_timeout_ns;    /* lk_init fails if the CTAs are not all up; 0 -> 10 s    */
   uint32_t exec_log_cap;       /* execution-log records kept per CTA (ring); 0 = no log  */
   uint32_t flags;              /* LK_INIT_* bits                                        */
+  uint32_t max_batch_units;    /* work units one batch may hold (lk_submit_batch);      */
+                               /* 0 -> 32768                                            */
+  uint32_t reserved;
 } lk_init_params;
 
 /* lk_init_params.flags: how descriptors reach a cluster's CTAs.
@@ -177,6 +184,100 @@ int lk_poll(lk_ctx* ctx, lk_handle h);
 /* Wait (Sec. III), blocking: spin until h finished or timeout_ns elapsed.
  * Returns LK_OK, LK_ETIMEDOUT, or lk_poll's errors. */
 int lk_wait(lk_ctx* ctx, lk_handle h, uint64_t timeout_ns);
+
+/* ---- batches: many descriptors in one mailbox post ---------------------- */
+/* Not in the paper: one post hands a cluster a whole list of items.  Each
+ * item is split into `parts` work units (a unit = one part of one item, run
+ * by one CTA); the cluster's CTAs claim units from an atomic ticket, so
+ * items of uneven size spread over the cluster.  Parts of a sum or histogram
+ * item are combined by the last part to finish (sums: binary64 in part
+ * order, so a result depends only on the item's n, its parts and the block
+ * size).  One completion covers the whole batch. */
+typedef struct {
+  const void* in0;        /* device pointers, as lk_submit                        */
+  const void* in1;
+  void* out;
+  uint32_t op;            /* LK_OP_NOP .. LK_OP_COPY_I32                          */
+  uint32_t parts;         /* CTAs sharing the item: 1..8, or 0 = from the tune    */
+  uint64_t n;             /* as lk_desc.n                                          */
+} lk_batch_item;          /* 40 bytes */
+
+typedef struct {
+  uint32_t max_parts;     /* cap on parts of an item (1..8, and at most the       */
+                          /* cluster size); 0 -> 8                                 */
+  uint32_t reserved;
+  uint64_t part_bytes;    /* an item with parts == 0 gets ceil(input bytes /       */
+                          /* part_bytes) parts, capped; 0 -> 4 MiB                 */
+} lk_batch_tune;
+
+/* Post `count` items (host array; copied by the call, so it may be reused at
+ * once) to `cluster` as one descriptor.  The expanded unit table lives in
+ * library-owned pinned host-mapped memory until the batch finishes; the
+ * items' data buffers follow lk_submit's ownership rule.  A batch starts
+ * only after every earlier descriptor of its cluster has finished.
+ * tune: NULL = defaults.  *h names the batch (lk_wait / lk_poll as usual).
+ * Errors: LK_EINVAL (an item fails lk_submit's checks, too many units, too
+ * many split sum / histogram items), LK_EAGAIN (ring or batch buffers busy),
+ * LK_ESTATE. */
+int lk_submit_batch(lk_ctx* ctx, int cluster, const lk_batch_item* items, uint32_t count,
+                    const lk_batch_tune* tune, lk_handle* h);
+
+/* The same items as one CUDA graph of ordinary launches (one kernel per item,
+ * the same bodies; grid = clamp(ceil(input bytes / 256 KiB), 1, max_ctas)
+ * CTAs of `threads` threads), captured once, then launched `reps` times with
+ * a synchronise after each.  ms[r] receives launch-to-synchronise-return time
+ * of repetition r (host clock).  Must not run while a full-chip context is
+ * alive.  Returns LK_OK, LK_EINVAL, LK_EDEVICE. */
+int lk_baseline_graph(int device, const lk_batch_item* items, uint32_t count, int max_ctas, int threads,
+                      int reps, float* ms);
+
+/* ---- serving: continuous admission of requests ------------------------- */
+/* Not in the paper.  Requests arrive over time from several host producer
+ * threads; one dispatcher admits them in arrival order while the bytes they
+ * hold (inputs, outputs, scratch) fit in a device-memory budget, splits each
+ * into chunks of at most chunk_bytes of input, and lets every cluster pull
+ * the next chunks as its in-flight window frees up, so requests that arrive
+ * while others run are interleaved with them.  A sum or histogram split into
+ * several chunks is finished by one LK_OP_COMBINE_* descriptor; results do
+ * not depend on what else runs (all clusters must have the same size). */
+typedef struct {
+  uint64_t t_arrival_ns;  /* arrival time relative to the run's start         */
+  uint32_t op;            /* LK_OP_ADD_I32 .. LK_OP_COPY_I32                  */
+  uint32_t producer;      /* host producer thread that injects it             */
+  uint64_t n;             /* as lk_desc.n                                      */
+  const void* in0;        /* device pointers, resident for the whole run      */
+  const void* in1;
+  void* out;              /* device output, or NULL: taken from the arena      */
+} lk_request;             /* 48 bytes */
+
+typedef struct {
+  uint64_t t_admit_ns;    /* admitted (budget granted), relative to start      */
+  uint64_t t_complete_ns; /* last descriptor of the request observed finished  */
+  void* out;              /* where the output was written                      */
+  int32_t status;         /* LK_OK or an LK_E* code                            */
+  uint32_t chunks;        /* descriptors the request ran as (without combine)  */
+} lk_request_result;      /* 32 bytes */
+
+typedef struct {
+  int n_producers;            /* >= 1; request.producer < n_producers             */
+  int window;                 /* chunks each cluster may hold at once; 0 -> 2     */
+  uint64_t chunk_bytes;       /* input bytes per chunk; 0 -> 16 MiB              */
+  uint64_t budget_bytes;      /* admission budget: bytes held by admitted,         */
+                              /* unfinished requests                              */
+  void* arena;                /* device memory (256-byte aligned) for outputs of    */
+                              /* requests with out == NULL and for the per-chunk   */
+                              /* partials of split sums and histograms             */
+  uint64_t arena_bytes;
+  uint64_t timeout_ns;        /* whole run; 0 -> 120 s                            */
+} lk_serve_params;
+
+/* Run the requests through the context's clusters (all of one size) and
+ * fill res[i] for each.  Outputs taken from the arena are released when the
+ * request completes (read them before the next call reuses the arena).
+ * Returns LK_OK if every request finished, LK_EINVAL, LK_ENOMEM (a request
+ * needs more arena or budget than exists), or the first error. */
+int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
+             lk_request_result* res);
 
 /* Refresh the idle lease without posting work.  LK_OK or LK_EINVAL. */
 int lk_heartbeat(lk_ctx* ctx);

@@ -353,6 +353,30 @@ __device__ __forceinline__ void combine_hist(const lk_slot& d, uint32_t* acc) {
   }
 }
 
+/* ---- combining chunk results (rank 0 of the cluster alone) ------------- */
+/* out[0] = binary64 sum of n float32 partials, one per 16-byte slot, added
+ * lane-strided then by a fixed shuffle tree: the order depends only on n. */
+__device__ __forceinline__ void body_combine_sum(const lk_slot& d, int r) {
+  if (r != 0 || threadIdx.x >= 32) return;
+  const float* p = reinterpret_cast<const float*>(d.in0);
+  double s = 0.0;
+  for (uint64_t q = threadIdx.x; q < d.n; q += 32) s += (double)__ldcg(p + 4 * q);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) *reinterpret_cast<float*>(d.out) = (float)s;
+}
+
+/* out[v] = sum over j < n of in0[256 j + v]: n int32 histograms. */
+__device__ __forceinline__ void body_combine_hist(const lk_slot& d, int r) {
+  if (r != 0) return;
+  const int32_t* h = reinterpret_cast<const int32_t*>(d.in0);
+  for (uint32_t v = threadIdx.x; v < 256; v += blockDim.x) {
+    uint32_t s = 0;
+    for (uint64_t j = 0; j < d.n; ++j) s += (uint32_t)__ldcg(h + 256 * j + v);
+    reinterpret_cast<int32_t*>(d.out)[v] = (int32_t)s;
+  }
+}
+
 /* ---- 64x64x64 float32 GEMM tiles ---------------------------------------- */
 /* Work unit = (tile, block of 64/U rows).  U > 1 only when there are fewer
  * tiles than CTAs, so that one tile can spread over up to 8 CTAs. */

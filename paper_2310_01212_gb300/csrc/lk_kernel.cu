@@ -250,10 +250,103 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
     case LK_OP_SUM_F32: ok = body_sum(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
     case LK_OP_HIST_U8: ok = body_hist(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
     case LK_OP_GEMM64_F32: ok = body_gemm(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline); break;
+    case LK_OP_COMBINE_SUM: body_combine_sum(d, r); break;
+    case LK_OP_COMBINE_HIST: body_combine_hist(d, r); break;
     case LK_OP_NOP: break;
     default: return LK_DERR_BADDESC;
   }
   return ok ? 0 : LK_DERR_STAGING;
+}
+
+/* A batch (lk_submit_batch): the CTAs of the cluster claim work units from
+ * the cluster's ticket until none is left.  Thread 0 claims and reads the
+ * unit's 48-byte entry from the host-mapped unit table; the whole CTA runs
+ * that part of that item.  Parts of a sum or histogram item combine through
+ * per-item state: the last part to finish writes the item's output (sums in
+ * binary64, in part order) and returns the state to zero.  Returns an
+ * LK_DERR_* code or 0. */
+__device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
+                                         uint64_t* bars, uint32_t& phase, float* red) {
+  __shared__ uint64_t s_unit[6];
+  __shared__ unsigned long long s_u;
+  __shared__ float s_part;
+  __shared__ int s_lastp;
+  lk_bcluster* bc = a.bcl + c;
+  uint32_t* my_hist = a.cta_hist + (size_t)(a.cl_start[c] + r) * 256u;
+  const lk_unit* units = reinterpret_cast<const lk_unit*>(d.in0);
+  const uint64_t nunits = d.n;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long u = atomicAdd(&bc->ticket, 1ull);
+      s_u = u;
+      if (u < nunits) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(units + u);
+        const ulonglong2 v0 = __ldcv(p), v1 = __ldcv(p + 1), v2 = __ldcv(p + 2);
+        s_unit[0] = v0.x; s_unit[1] = v0.y; s_unit[2] = v1.x;
+        s_unit[3] = v1.y; s_unit[4] = v2.x; s_unit[5] = v2.y;
+      }
+    }
+    __syncthreads();
+    if (s_u >= nunits) break;
+    const uint32_t op = (uint32_t)(s_unit[3] >> 56);
+    const uint32_t part = (uint32_t)(s_unit[4] & 0xffu);
+    const uint32_t parts = (uint32_t)((s_unit[4] >> 8) & 0xffu);
+    const uint64_t comb = s_unit[4] >> 16;
+    lk_slot it;
+    it.seq = d.seq;
+    it.cmd = LK_CMD_WORK + op;
+    it.flags = 0;
+    it.n = s_unit[3] & LK_LOW48;
+    it.in0 = s_unit[0];
+    it.in1 = s_unit[1];
+    it.out = s_unit[2];
+    it.aux = 0;
+    it.t_pick = 0;
+    const uint64_t deadline = gtime() + 2000000000ull;
+    bool ok = true;
+    if (op == LK_OP_SUM_F32) {
+      float* pout = parts > 1 ? &bc->sums[comb - 1].partial[part] : &s_part;
+      ok = body_sum(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
+      if (threadIdx.x == 0) {
+        if (parts == 1) {
+          *reinterpret_cast<float*>(it.out) = s_part;
+        } else {
+          lk_sum_state* st = &bc->sums[comb - 1];
+          __threadfence();
+          if (atomicAdd(&st->done, 1u) == parts - 1) {
+            __threadfence();
+            double sum = 0.0;
+            for (uint32_t q = 0; q < parts; ++q) sum += (double)__ldcg(&st->partial[q]);
+            *reinterpret_cast<float*>(it.out) = (float)sum;
+            st->done = 0;
+          }
+        }
+      }
+    } else if (op == LK_OP_HIST_U8) {
+      uint32_t* acc = parts > 1 ? bc->hists[comb - 1].bins : my_hist;
+      ok = body_hist(it, (int)part, (int)parts, dsm, bars, phase, deadline, acc);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_lastp = 1;
+        if (parts > 1) {
+          __threadfence();
+          s_lastp = atomicAdd(&bc->hists[comb - 1].done, 1u) == parts - 1;
+          if (s_lastp) __threadfence();
+        }
+      }
+      __syncthreads();
+      if (s_lastp) {
+        combine_hist(it, acc);
+        if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
+      }
+    } else {
+      const int e = run_body(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
+      ok = (e == 0);
+    }
+    __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
+    if (!ok) return LK_DERR_STAGING;
+  }
+  return 0;
 }
 
 template <int MAXT>
@@ -357,6 +450,12 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
         if (!err) relay_publish(&dc->relay[slot], k, dsc);
         else st_release_gpu(&dc->gen, LK_GEN_STOP);
       }
+      /* a batch starts once every earlier descriptor of the cluster finished
+       * (its ticket and combine state are then at rest) */
+      if (!err && dsc.cmd == LK_CMD_WORK + LK_OP_BATCH && k > 0 && known_done < k) {
+        const int ww = wait_word(a, &dc->dev_done, k, false, &known_done);
+        err = ww < 0 ? LK_DERR_STALL : ww;
+      }
       if (err) {
         if (err > 0) {
           set_error(a, c, (uint32_t)err);
@@ -378,7 +477,8 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = run_body(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+    const int berr = op == LK_OP_BATCH ? run_batch(a, d, c, r, dsm, s_bars, phase, s_red)
+                                       : run_body(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -399,6 +499,7 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
         else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
         __syncthreads();
         if (tid == 0) {
+          if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every rank has left the claim loop */
           /* one system-scope fence orders every output write (this CTA's,
            * and the other ranks' through their flags) before both stores */
           fence_acq_rel_sys();
@@ -865,6 +966,70 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
   return rc;
 }
 
+/* ---- a batch as one CUDA graph of ordinary launches ---------------------- */
+extern "C" int lk_baseline_graph(int device, const lk_batch_item* items, uint32_t count, int max_ctas, int threads,
+                                 int reps, float* ms) {
+  if ((count > 0 && !items) || max_ctas < 1 || max_ctas > LK_MAX_CTAS || threads < 64 || threads > 1024 ||
+      threads % 32 || reps < 1 || !ms)
+    return LK_EINVAL;
+  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1};
+  for (uint32_t i = 0; i < count; ++i) {
+    const lk_batch_item& it = items[i];
+    if (it.op >= LK_OP_COUNT) return LK_EINVAL;
+    const void* ins[2] = {it.in0, it.in1};
+    for (int j = 0; j < need[it.op]; ++j)
+      if (((uintptr_t)ins[j] & 15u) || (it.n > 0 && !ins[j])) return LK_EINVAL;
+    if ((uintptr_t)it.out & 15u) return LK_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  if (g_preload_err != cudaSuccess) return LK_EDEVICE;
+  cudaStream_t s = nullptr;
+  lk_scratch* sc = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = LK_OK;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = LK_EDEVICE;
+  if (rc == LK_OK && cudaMalloc(&sc, sizeof(lk_scratch)) != cudaSuccess) rc = LK_ENOMEM;
+  if (rc == LK_OK && (cudaMemsetAsync(sc, 0, sizeof(lk_scratch), s) != cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess))
+    rc = LK_EDEVICE;
+  if (rc == LK_OK) {
+    /* the kernels run one after another, so they can share one scratch block */
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LK_EDEVICE;
+    for (uint32_t i = 0; i < count && rc == LK_OK; ++i) {
+      const lk_batch_item& it = items[i];
+      if (it.op == LK_OP_NOP) continue;
+      uint64_t in_bytes = it.op == LK_OP_ADD_I32 ? 8 * it.n
+                          : it.op == LK_OP_HIST_U8 ? it.n
+                          : it.op == LK_OP_GEMM64_F32 ? 32768 * it.n
+                                                      : 4 * it.n;
+      int grid = (int)std::min<uint64_t>((uint64_t)max_ctas, std::max<uint64_t>(1, (in_bytes + 262143) / 262144));
+      lk_slot d;
+      memset(&d, 0, sizeof d);
+      d.cmd = LK_CMD_WORK + it.op;
+      d.n = it.n;
+      d.in0 = (uint64_t)(uintptr_t)it.in0;
+      d.in1 = (uint64_t)(uintptr_t)it.in1;
+      d.out = (uint64_t)(uintptr_t)it.out;
+      if (launch_ordinary(d, grid, threads, sc, s) != cudaSuccess) rc = LK_EDEVICE;
+    }
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc == LK_OK && e != cudaSuccess) rc = LK_EDEVICE;
+    if (rc == LK_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = LK_EDEVICE;
+  }
+  for (int r = 0; r < reps && rc == LK_OK; ++r) {
+    const uint64_t t0 = now_ns();
+    if (cudaGraphLaunch(exec, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) rc = LK_EDEVICE;
+    ms[r] = (float)((now_ns() - t0) / 1e6);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (sc) cudaFree(sc);
+  if (s) cudaStreamDestroy(s);
+  return rc;
+}
+
 /* ---- one ordinary launch that allocates nothing --------------------------
  * The sum and histogram bodies combine per-CTA results through a small
  * scratch block (arrival counter, 256 histogram bins, one partial per CTA).
@@ -884,7 +1049,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 extern "C" int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
                                  int ctas, int threads, void* stream) {
   if (!d || d->flags != 0 || device < 0 || device >= 256) return LK_EINVAL;
-  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1};
+  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1};
   if (d->op >= LK_OP_COUNT || n_in != need[d->op] || (n_in > 0 && !in)) return LK_EINVAL;
   if (ctas < 1 || ctas > LK_MAX_CTAS) return LK_EINVAL;   /* beyond the static scratch */
   if (threads < 64 || threads > 1024 || threads % 32) return LK_EINVAL;

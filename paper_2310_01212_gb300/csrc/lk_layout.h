@@ -122,6 +122,40 @@ typedef struct __attribute__((aligned(LK_LINE))) {
   float partial[LK_BCAST_DEPTH][LK_MAX_CTAS]; /* per-rank partial sums                  */
 } lk_dcluster;
 
+/* ---- batches (lk_submit_batch) ----------------------------------------- */
+/* One work unit = one part of one item; the host expands a batch's items
+ * into a unit table in pinned host-mapped memory (48 bytes per unit). */
+typedef struct {
+  uint64_t in0, in1, out;
+  uint64_t n_op;     /* op << 56 | n (n < 2^48)                                 */
+  uint64_t meta;     /* part (bits 0-7) | parts (8-15) | combine slot + 1 (16-47, */
+                     /* 0 = none: single-part item, or an op needing no combine)   */
+  uint64_t item;     /* index of the item in its batch                           */
+} lk_unit;
+
+#define LK_BATCH_SPLIT_SUMS 2048   /* multi-part sum items per batch        */
+#define LK_BATCH_SPLIT_HISTS 256   /* multi-part histogram items per batch  */
+#define LK_BATCH_BUFFERS 2         /* unit tables per cluster               */
+
+typedef struct {
+  uint32_t done;                   /* parts finished (the last one resets it) */
+  uint32_t pad;
+  float partial[8];
+} lk_sum_state;
+
+typedef struct {
+  uint32_t done;
+  uint32_t pad[3];
+  uint32_t bins[256];              /* zero at rest                            */
+} lk_hist_state;
+
+typedef struct __attribute__((aligned(LK_LINE))) {
+  unsigned long long ticket;       /* next unit to claim (rank 0 resets it)   */
+  uint8_t pad[LK_LINE - 8];
+  lk_sum_state sums[LK_BATCH_SPLIT_SUMS];
+  lk_hist_state hists[LK_BATCH_SPLIT_HISTS];
+} lk_bcluster;
+
 /* Everything the persistent kernel needs; passed by value at launch. */
 #define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
 
@@ -137,6 +171,8 @@ typedef struct {
   uint32_t* boot_count;          /* device: boot barrier counter                        */
   lk_exec_rec* log;              /* [G][log_cap] device, or NULL                        */
   uint64_t* log_count;           /* [G] device: records written per CTA                 */
+  lk_bcluster* bcl;              /* [C] device: batch tickets and combine state         */
+  uint32_t* cta_hist;            /* [total][256] device: single-part histogram bins     */
   int32_t num_clusters;
   int32_t grid;
   int32_t total;                 /* CTAs that join clusters (= sum of sizes)            */

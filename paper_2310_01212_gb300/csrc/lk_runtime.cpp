@@ -19,6 +19,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <deque>
+#include <map>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -72,6 +75,17 @@ struct lk_ctx {
   uint32_t log_cap = 0;
 
   Tail* tail = nullptr;          /* [C], host-only tickets */
+
+  /* batches: per cluster LK_BATCH_BUFFERS unit tables in host-mapped memory */
+  uint32_t max_units = 0;
+  lk_unit* units_h = nullptr;    /* [C][LK_BATCH_BUFFERS][max_units] */
+  lk_unit* units_d = nullptr;
+  struct BatchState {
+    std::mutex mu;
+    uint64_t next = 0;                          /* batches posted so far */
+    uint64_t seq_of[LK_BATCH_BUFFERS] = {0};    /* batch seq that last used each table */
+  };
+  BatchState* batch = nullptr;   /* [C] */
   lkb_launch* launch = nullptr;
   std::atomic<int> running{0};
 };
@@ -96,6 +110,8 @@ static int op_inputs(uint32_t op) {
     case LK_OP_SUM_F32: return 1;
     case LK_OP_GEMM64_F32: return 2;
     case LK_OP_COPY_I32: return 1;
+    case LK_OP_COMBINE_SUM: return 1;
+    case LK_OP_COMBINE_HIST: return 1;
     default: return -1;
   }
 }
@@ -127,6 +143,10 @@ static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in
     case LK_OP_GEMM64_F32:
       if (d->n > (1ull << 28)) return LK_EINVAL;
       if (d->n > 0 && !out) return LK_EINVAL;
+      break;
+    case LK_OP_COMBINE_SUM:
+    case LK_OP_COMBINE_HIST:
+      if (!out || d->n > (1ull << 20)) return LK_EINVAL;
       break;
     default:
       if (d->n > 0 && !out) return LK_EINVAL;
@@ -218,13 +238,17 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   ctx->log_cap = p->exec_log_cap;
   if (p->flags & ~(uint32_t)LK_INIT_DIRECT) return LK_EINVAL;
 
-  /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] */
+  /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] [unit tables (live only)] */
+  ctx->max_units = live ? (p->max_batch_units ? p->max_batch_units : 8192u) : 0u;
+  if (ctx->max_units > (1u << 22)) return LK_EINVAL;
   size_t off_ring = 0;
   size_t ring_bytes = (size_t)ctx->C * R * sizeof(lk_wire);
   size_t off_cw = live ? align_up(ring_bytes, LK_LINE) : 0;
   size_t off_ctrl = align_up(off_cw + ctx->C * sizeof(lk_cword), LK_LINE);
   size_t off_info = align_up(off_ctrl + sizeof(lk_ctrl), LK_LINE);
-  size_t mapped_bytes = align_up(off_info + ctx->G * sizeof(lk_cta_info), 4096);
+  size_t off_units = align_up(off_info + ctx->G * sizeof(lk_cta_info), LK_LINE);
+  size_t units_bytes = (size_t)ctx->C * LK_BATCH_BUFFERS * ctx->max_units * sizeof(lk_unit);
+  size_t mapped_bytes = align_up(off_units + units_bytes, 4096);
   rc = lkb_alloc_mapped(ctx->device, mapped_bytes, &ctx->mapped_h, &ctx->mapped_d);
   if (rc != LK_OK) return rc;
   char* mh = (char*)ctx->mapped_h;
@@ -232,6 +256,10 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   ctx->cword_h = (lk_cword*)(mh + off_cw);
   ctx->ctrl_h = (lk_ctrl*)(mh + off_ctrl);
   ctx->info_h = (lk_cta_info*)(mh + off_info);
+  if (ctx->max_units) {
+    ctx->units_h = (lk_unit*)(mh + off_units);
+    ctx->units_d = (lk_unit*)(md + off_units);
+  }
 
   /* device block: [ring (finite only)] dcl[C] cl_start pin_smid boot_smid boot_count log_count log */
   size_t d_ring = 0;
@@ -241,7 +269,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   size_t d_bsm = align_up(d_pin + (p->smids ? ctx->total : 0) * sizeof(int32_t), LK_LINE);
   size_t d_bcnt = align_up(d_bsm + ctx->G * sizeof(int32_t), LK_LINE);
   size_t d_lcnt = align_up(d_bcnt + sizeof(uint32_t), LK_LINE);
-  size_t d_log = align_up(d_lcnt + ctx->G * sizeof(uint64_t), LK_LINE);
+  size_t d_bcl = align_up(d_lcnt + ctx->G * sizeof(uint64_t), LK_LINE);
+  size_t d_chist = align_up(d_bcl + ctx->C * sizeof(lk_bcluster), LK_LINE);
+  size_t d_log = align_up(d_chist + (size_t)ctx->total * 256 * sizeof(uint32_t), LK_LINE);
   size_t dev_bytes = align_up(d_log + (size_t)ctx->G * ctx->log_cap * sizeof(lk_exec_rec), 4096);
   rc = lkb_alloc_device(ctx->device, dev_bytes, &ctx->dev_base);
   if (rc != LK_OK) return rc;
@@ -267,6 +297,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.boot_count = (uint32_t*)(db + d_bcnt);
   a.log_count = (uint64_t*)(db + d_lcnt);
   a.log = ctx->log_cap ? (lk_exec_rec*)(db + d_log) : nullptr;
+  a.bcl = (lk_bcluster*)(db + d_bcl);
+  a.cta_hist = (uint32_t*)(db + d_chist);
   a.num_clusters = ctx->C;
   a.grid = ctx->G;
   a.total = ctx->total;
@@ -281,7 +313,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if (live) ctx->ring_h = (lk_wire*)(mh + off_ring);
 
   ctx->tail = new (std::nothrow) Tail[ctx->C];
-  if (!ctx->tail) return LK_ENOMEM;
+  ctx->batch = new (std::nothrow) lk_ctx::BatchState[ctx->C];
+  if (!ctx->tail || !ctx->batch) return LK_ENOMEM;
   return LK_OK;
 }
 
@@ -290,6 +323,7 @@ static void teardown(lk_ctx* ctx) {
   if (ctx->dev_base) lkb_free_device(ctx->dev_base);
   if (ctx->mapped_h) lkb_free_mapped(ctx->mapped_h);
   delete[] ctx->tail;
+  delete[] ctx->batch;
   delete ctx;
 }
 
@@ -469,6 +503,81 @@ int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms) {
   teardown(ctx);
   if (rc != LK_OK) return rc;
   if (e != 0 && e != LK_DERR_LEASE) return LK_EDEVICE;
+  return LK_OK;
+}
+
+/* Input bytes of one item: what the split rule divides. */
+static uint64_t item_input_bytes(uint32_t op, uint64_t n) {
+  switch (op) {
+    case LK_OP_ADD_I32: return 8 * n;
+    case LK_OP_COPY_I32: return 4 * n;
+    case LK_OP_SUM_F32: return 4 * n;
+    case LK_OP_HIST_U8: return n;
+    case LK_OP_GEMM64_F32: return 32768 * n;
+    default: return 0;
+  }
+}
+
+int lk_submit_batch(lk_ctx* ctx, int cluster, const lk_batch_item* items, uint32_t count,
+                    const lk_batch_tune* tune, lk_handle* h) {
+  if (!ctx || !h || (count > 0 && !items) || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
+  if (!ctx->max_units) return LK_EINVAL;   /* finite-mode contexts take no batches */
+  uint32_t cap = tune && tune->max_parts ? tune->max_parts : 8u;
+  const uint64_t part_bytes = tune && tune->part_bytes ? tune->part_bytes : (4ull << 20);
+  if (cap > 8) return LK_EINVAL;
+  cap = std::min<uint32_t>(cap, (uint32_t)ctx->sizes[cluster]);
+  /* validate and count units, split sums and split histograms */
+  uint64_t units = 0;
+  uint32_t sums = 0, hists = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const lk_batch_item& it = items[i];
+    lk_desc d{it.op, 0, it.n, 0};
+    int rc = validate(&d, it.in0, it.in1, op_inputs(it.op), it.out);
+    if (rc != LK_OK) return rc;
+    if (it.parts > 8) return LK_EINVAL;
+    uint32_t parts = it.parts ? std::min(it.parts, cap)
+                              : (uint32_t)std::min<uint64_t>(cap, std::max<uint64_t>(1, (item_input_bytes(it.op, it.n) + part_bytes - 1) / part_bytes));
+    if (parts > 1 && it.op == LK_OP_SUM_F32) ++sums;
+    if (parts > 1 && it.op == LK_OP_HIST_U8) ++hists;
+    units += parts;
+  }
+  if (units > ctx->max_units || sums > LK_BATCH_SPLIT_SUMS || hists > LK_BATCH_SPLIT_HISTS) return LK_EINVAL;
+  if (!ctx_alive(ctx)) return LK_ESTATE;
+  beat(ctx);
+  lk_ctx::BatchState& bs = ctx->batch[cluster];
+  std::lock_guard<std::mutex> g(bs.mu);
+  const uint32_t b = (uint32_t)(bs.next % LK_BATCH_BUFFERS);
+  if (ld_acq(&ctx->cword_h[cluster].done) < bs.seq_of[b]) return LK_EAGAIN;   /* table still in use */
+  lk_unit* tab = ctx->units_h + ((size_t)cluster * LK_BATCH_BUFFERS + b) * ctx->max_units;
+  uint64_t u = 0;
+  uint32_t s_slot = 0, h_slot = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const lk_batch_item& it = items[i];
+    uint32_t parts = it.parts ? std::min(it.parts, cap)
+                              : (uint32_t)std::min<uint64_t>(cap, std::max<uint64_t>(1, (item_input_bytes(it.op, it.n) + part_bytes - 1) / part_bytes));
+    uint64_t comb = 0;
+    if (parts > 1 && it.op == LK_OP_SUM_F32) comb = ++s_slot;
+    if (parts > 1 && it.op == LK_OP_HIST_U8) comb = ++h_slot;
+    for (uint32_t p = 0; p < parts; ++p, ++u) {
+      lk_unit& un = tab[u];
+      un.in0 = (uint64_t)(uintptr_t)it.in0;
+      un.in1 = (uint64_t)(uintptr_t)it.in1;
+      un.out = (uint64_t)(uintptr_t)it.out;
+      un.n_op = ((uint64_t)it.op << 56) | (it.n & LK_LOW48);
+      un.meta = (uint64_t)p | ((uint64_t)parts << 8) | (comb << 16);
+      un.item = i;
+    }
+  }
+  /* the unit table is read by the device after it acquires the descriptor,
+   * which write_slot publishes behind a release fence */
+  lk_desc d{LK_OP_BATCH, 0, units, 0};
+  uint64_t seq = 0;
+  int rc = post(ctx, cluster, LK_CMD_WORK + LK_OP_BATCH, &d, ctx->units_d + (tab - ctx->units_h), nullptr, nullptr,
+                &seq);
+  if (rc != LK_OK) return rc;
+  bs.seq_of[b] = seq;
+  bs.next++;
+  *h = ((uint64_t)cluster << 48) | seq;
   return LK_OK;
 }
 
@@ -746,3 +855,255 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
 }
 
 }  // extern "C"
+
+/* ---------------------------------------------------------------------- */
+/* Serving: producers inject requests, one dispatcher admits, chunks and
+ * completes them.                                                          */
+namespace {
+
+/* First-fit allocator over [0, size) with coalescing of freed blocks. */
+class Arena {
+ public:
+  explicit Arena(uint64_t size) { if (size) free_[0] = size; }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    bytes = (bytes + 255) & ~255ull;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const uint64_t rest = it->second - bytes;
+        const uint64_t at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~255ull;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<uint64_t, uint64_t> free_;
+};
+
+struct ServeReq {
+  uint64_t in_bytes = 0, out_bytes = 0, scratch_bytes = 0, held = 0;
+  uint64_t unit = 1;          /* elements per alignment unit */
+  uint64_t elem_bytes = 4;    /* input bytes per element (per input) */
+  uint32_t chunks = 1, done_chunks = 0;
+  bool needs_combine = false, arena_out = false;
+  uint64_t out_off = 0, scratch_off = 0;
+  void* out = nullptr;
+  void* scratch = nullptr;
+};
+
+}  // namespace
+
+extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
+                        lk_request_result* res) {
+  if (!ctx || !p || (count > 0 && (!reqs || !res)) || p->n_producers < 1 || p->n_producers > 256) return LK_EINVAL;
+  for (int c = 1; c < ctx->C; ++c)
+    if (ctx->sizes[c] != ctx->sizes[0]) return LK_EINVAL;   /* results must not depend on the cluster */
+  const int window = p->window > 0 ? p->window : 2;
+  const uint64_t chunk_bytes = p->chunk_bytes ? p->chunk_bytes : (16ull << 20);
+  const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
+  if (chunk_bytes < 65536 || ((uintptr_t)p->arena & 255u)) return LK_EINVAL;
+  std::vector<ServeReq> st(count);
+  for (size_t i = 0; i < count; ++i) {
+    const lk_request& r = reqs[i];
+    if (r.producer >= (uint32_t)p->n_producers) return LK_EINVAL;
+    if (r.op < LK_OP_ADD_I32 || r.op > LK_OP_COPY_I32) return LK_EINVAL;
+    lk_desc d{r.op, 0, r.n, 0};
+    int rc = validate(&d, r.in0, r.in1, op_inputs(r.op), r.out ? r.out : (void*)(uintptr_t)256);
+    if (rc != LK_OK) return rc;
+    ServeReq& q = st[i];
+    switch (r.op) {
+      case LK_OP_ADD_I32: q.in_bytes = 8 * r.n; q.out_bytes = 4 * r.n; q.unit = 4; q.elem_bytes = 4; break;
+      case LK_OP_COPY_I32: q.in_bytes = 4 * r.n; q.out_bytes = 4 * r.n; q.unit = 4; q.elem_bytes = 4; break;
+      case LK_OP_SUM_F32: q.in_bytes = 4 * r.n; q.out_bytes = 16; q.unit = 4; q.elem_bytes = 4; break;
+      case LK_OP_HIST_U8: q.in_bytes = r.n; q.out_bytes = 1024; q.unit = 16; q.elem_bytes = 1; break;
+      default: q.in_bytes = 32768 * r.n; q.out_bytes = 16384 * r.n; q.unit = 1; q.elem_bytes = 32768; break;
+    }
+    /* elements per chunk: a whole number of alignment units */
+    const uint64_t per_elem = r.op == LK_OP_ADD_I32 ? 8 : q.elem_bytes;
+    uint64_t ce = std::max<uint64_t>(q.unit, chunk_bytes / per_elem / q.unit * q.unit);
+    q.chunks = (uint32_t)std::max<uint64_t>(1, (r.n + ce - 1) / ce);
+    q.needs_combine = q.chunks > 1 && (r.op == LK_OP_SUM_F32 || r.op == LK_OP_HIST_U8);
+    q.scratch_bytes = q.needs_combine ? (uint64_t)q.chunks * (r.op == LK_OP_SUM_F32 ? 16 : 1024) : 0;
+    q.arena_out = r.out == nullptr;
+    q.held = q.in_bytes + q.out_bytes + q.scratch_bytes;
+    const uint64_t need = (q.arena_out ? q.out_bytes + 256 : 0) + (q.scratch_bytes ? q.scratch_bytes + 256 : 0);
+    if (q.held > p->budget_bytes || need > p->arena_bytes) return LK_ENOMEM;
+    res[i] = lk_request_result{0, 0, nullptr, LK_PENDING, q.chunks};
+  }
+  if (!ctx_alive(ctx)) return LK_ESTATE;
+
+  /* producers: each releases its own requests at their arrival times */
+  std::mutex qmu;
+  std::deque<size_t> arrived;
+  std::atomic<uint64_t> start{0};
+  std::atomic<int> ready{0};
+  std::atomic<bool> stop{false};
+  std::vector<std::vector<size_t>> mine(p->n_producers);
+  for (size_t i = 0; i < count; ++i) mine[reqs[i].producer].push_back(i);
+  for (auto& v : mine)
+    std::stable_sort(v.begin(), v.end(), [&](size_t a, size_t b) { return reqs[a].t_arrival_ns < reqs[b].t_arrival_ns; });
+  auto producer = [&](int w) {
+    ready.fetch_add(1);
+    uint64_t t0;
+    while ((t0 = start.load(std::memory_order_acquire)) == 0) {}
+    for (size_t i : mine[w]) {
+      while (now_ns() < t0 + reqs[i].t_arrival_ns)
+        if (stop.load(std::memory_order_relaxed)) return;
+      std::lock_guard<std::mutex> g(qmu);
+      arrived.push_back(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 0; w < p->n_producers; ++w) th.emplace_back(producer, w);
+  while (ready.load() < p->n_producers) std::this_thread::yield();
+  const uint64_t t0 = now_ns();
+  start.store(t0, std::memory_order_release);
+
+  /* dispatcher */
+  Arena arena(p->arena_bytes);
+  uint64_t held = 0;
+  std::deque<size_t> waiting;                      /* arrived, not admitted (FIFO) */
+  std::deque<std::pair<size_t, uint32_t>> chunks;  /* admitted chunks to post     */
+  std::deque<size_t> combines;                     /* requests whose combine is due */
+  struct Fly { uint64_t seq; size_t req; bool combine; };
+  std::vector<std::deque<Fly>> fly(ctx->C);
+  size_t finished = 0;
+  int first_err = LK_OK;
+  int rr = 0;
+  auto complete = [&](size_t i, int status) {
+    ServeReq& q = st[i];
+    res[i].t_complete_ns = now_ns() - t0;
+    res[i].status = status;
+    res[i].out = q.out;
+    if (q.arena_out) arena.release(q.out_off, q.out_bytes);
+    if (q.scratch_bytes) arena.release(q.scratch_off, q.scratch_bytes);
+    held -= q.held;
+    ++finished;
+    if (status != LK_OK && first_err == LK_OK) first_err = status;
+  };
+  auto post_chunk = [&](int c, size_t i, uint32_t j, uint64_t* seq) -> int {
+    const lk_request& r = reqs[i];
+    ServeReq& q = st[i];
+    const uint64_t per_elem = r.op == LK_OP_ADD_I32 ? 8 : q.elem_bytes;
+    const uint64_t ce = std::max<uint64_t>(q.unit, chunk_bytes / per_elem / q.unit * q.unit);
+    const uint64_t e0 = (uint64_t)j * ce, e1 = std::min<uint64_t>(r.n, e0 + ce);
+    const uint64_t step = r.op == LK_OP_GEMM64_F32 ? 16384 : q.elem_bytes;   /* bytes per element of in0/in1/out */
+    const char* a0 = (const char*)r.in0;
+    const char* a1 = (const char*)r.in1;
+    char* o = (char*)q.out;
+    lk_desc d{r.op, 0, e1 - e0, 0};
+    const void* in0 = a0 ? a0 + e0 * step : nullptr;
+    const void* in1 = a1 ? a1 + e0 * step : nullptr;
+    void* out;
+    if (r.op == LK_OP_SUM_F32) out = q.needs_combine ? (char*)q.scratch + 16 * j : q.out;
+    else if (r.op == LK_OP_HIST_U8) out = q.needs_combine ? (char*)q.scratch + 1024 * j : q.out;
+    else out = o + e0 * (r.op == LK_OP_GEMM64_F32 ? 16384 : 4);
+    return post(ctx, c, LK_CMD_WORK + r.op, &d, in0, in1, out, seq);
+  };
+  while (finished < count) {
+    const uint64_t now = now_ns();
+    if (now - t0 > timeout) {
+      for (size_t i = 0; i < count; ++i)
+        if (res[i].status == LK_PENDING) res[i].status = LK_ETIMEDOUT;
+      if (first_err == LK_OK) first_err = LK_ETIMEDOUT;
+      break;
+    }
+    if (!ctx_alive(ctx)) {
+      int e = device_err_to_rc(dev_error(ctx));
+      for (size_t i = 0; i < count; ++i)
+        if (res[i].status == LK_PENDING) res[i].status = e ? e : LK_ESTATE;
+      if (first_err == LK_OK) first_err = e ? e : LK_ESTATE;
+      break;
+    }
+    {
+      std::lock_guard<std::mutex> g(qmu);
+      while (!arrived.empty()) {
+        waiting.push_back(arrived.front());
+        arrived.pop_front();
+      }
+    }
+    /* admission in arrival order while the budget and the arena allow */
+    while (!waiting.empty()) {
+      const size_t i = waiting.front();
+      ServeReq& q = st[i];
+      if (held + q.held > p->budget_bytes) break;
+      uint64_t oo = 0, so = 0;
+      if (q.arena_out && !arena.alloc(q.out_bytes, &oo)) break;
+      if (q.scratch_bytes && !arena.alloc(q.scratch_bytes, &so)) {
+        if (q.arena_out) arena.release(oo, q.out_bytes);
+        break;
+      }
+      q.out_off = oo;
+      q.scratch_off = so;
+      q.out = q.arena_out ? (char*)p->arena + oo : reqs[i].out;
+      q.scratch = q.scratch_bytes ? (char*)p->arena + so : nullptr;
+      held += q.held;
+      res[i].t_admit_ns = now_ns() - t0;
+      for (uint32_t j = 0; j < q.chunks; ++j) chunks.emplace_back(i, j);
+      waiting.pop_front();
+    }
+    /* clusters pull: each takes work while its window has room */
+    for (int k = 0; k < ctx->C; ++k) {
+      const int c = (rr + k) % ctx->C;
+      while ((int)fly[c].size() < window && (!combines.empty() || !chunks.empty())) {
+        uint64_t seq = 0;
+        if (!combines.empty()) {
+          const size_t i = combines.front();
+          ServeReq& q = st[i];
+          lk_desc d{reqs[i].op == LK_OP_SUM_F32 ? (uint32_t)LK_OP_COMBINE_SUM : (uint32_t)LK_OP_COMBINE_HIST, 0,
+                    q.chunks, 0};
+          if (post(ctx, c, LK_CMD_WORK + d.op, &d, q.scratch, nullptr, q.out, &seq) != LK_OK) break;
+          fly[c].push_back({seq, i, true});
+          combines.pop_front();
+        } else {
+          const auto cj = chunks.front();
+          if (post_chunk(c, cj.first, cj.second, &seq) != LK_OK) break;
+          fly[c].push_back({seq, cj.first, false});
+          chunks.pop_front();
+        }
+      }
+    }
+    rr = (rr + 1) % ctx->C;
+    /* completions (FIFO per cluster) */
+    for (int c = 0; c < ctx->C; ++c) {
+      if (fly[c].empty()) continue;
+      const uint64_t done = ld_acq(&ctx->cword_h[c].done);
+      while (!fly[c].empty() && fly[c].front().seq <= done) {
+        const Fly f = fly[c].front();
+        fly[c].pop_front();
+        ServeReq& q = st[f.req];
+        if (f.combine) {
+          complete(f.req, LK_OK);
+        } else if (++q.done_chunks == q.chunks) {
+          if (q.needs_combine) combines.push_back(f.req);
+          else complete(f.req, LK_OK);
+        }
+      }
+    }
+    if ((finished & 1023) == 0) beat(ctx);
+  }
+  stop.store(true);
+  for (auto& x : th) x.join();
+  beat(ctx);
+  return first_err;
+}

@@ -27,9 +27,11 @@ LK_ST_INIT, LK_ST_FINISHED, LK_ST_WORKING, LK_ST_NOP, LK_ST_EXITED, LK_ST_ERROR 
 LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
 LK_INIT_DIRECT = 1
 LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
+LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7
+LK_OP_BATCH = 8
 LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING = range(7)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
-             LK_OP_COPY_I32: 1}
+             LK_OP_COPY_I32: 1, 6: 1, 7: 1}
 OP_NAMES = {LK_OP_NOP: "nop", LK_OP_ADD_I32: "add_i32", LK_OP_HIST_U8: "hist_u8", LK_OP_SUM_F32: "sum_f32",
             LK_OP_GEMM64_F32: "gemm64_f32", LK_OP_COPY_I32: "copy_i32"}
 
@@ -47,7 +49,8 @@ class lk_init_params(ctypes.Structure):
                 ("threads_per_cta", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("backoff_base_ns", ctypes.c_uint64), ("backoff_cap_ns", ctypes.c_uint64),
                 ("idle_lease_ns", ctypes.c_uint64), ("boot_timeout_ns", ctypes.c_uint64),
-                ("exec_log_cap", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("exec_log_cap", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("max_batch_units", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class lk_desc(ctypes.Structure):
@@ -59,6 +62,28 @@ EXEC_REC_DTYPE = np.dtype([("seq", "<u8"), ("cluster", "<u4"), ("rank", "<u4"), 
                            ("order", "<u8"), ("t_pick_ns", "<u8"), ("t_start_ns", "<u8"), ("t_end_ns", "<u8"),
                            ("t_done_ns", "<u8")])
 assert EXEC_REC_DTYPE.itemsize == 64
+
+BATCH_ITEM_DTYPE = np.dtype([("in0", "<u8"), ("in1", "<u8"), ("out", "<u8"), ("op", "<u4"), ("parts", "<u4"),
+                             ("n", "<u8")])
+assert BATCH_ITEM_DTYPE.itemsize == 40
+
+
+class lk_batch_tune(ctypes.Structure):
+    _fields_ = [("max_parts", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("part_bytes", ctypes.c_uint64)]
+
+
+REQUEST_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("op", "<u4"), ("producer", "<u4"), ("n", "<u8"), ("in0", "<u8"),
+                          ("in1", "<u8"), ("out", "<u8")])
+REQUEST_RES_DTYPE = np.dtype([("t_admit_ns", "<u8"), ("t_complete_ns", "<u8"), ("out", "<u8"), ("status", "<i4"),
+                              ("chunks", "<u4")])
+assert REQUEST_DTYPE.itemsize == 48 and REQUEST_RES_DTYPE.itemsize == 32
+
+
+class lk_serve_params(ctypes.Structure):
+    _fields_ = [("n_producers", ctypes.c_int), ("window", ctypes.c_int), ("chunk_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
+                ("timeout_ns", ctypes.c_uint64)]
+
 
 TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op", "<u4"), ("n", "<u8"),
                              ("in0", "<u8"), ("in1", "<u8"), ("out", "<u8"), ("h_in0", "<u8"), ("h_in1", "<u8"),
@@ -111,6 +136,9 @@ def load(fake: bool = False) -> ctypes.CDLL:
             "lk_baseline_run_trace": (I, [I, P, SZ, I, ctypes.POINTER(I), I, I, I, I, P]),
             "lk_pingpong": (I, [I, I, ctypes.POINTER(U64)]),
             "lk_launch_noalloc": (I, [I, ctypes.POINTER(lk_desc), ctypes.POINTER(P), I, P, I, I, P]),
+            "lk_submit_batch": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(lk_batch_tune), ctypes.POINTER(U64)]),
+            "lk_serve": (I, [P, P, SZ, ctypes.POINTER(lk_serve_params), P]),
+            "lk_baseline_graph": (I, [I, P, ctypes.c_uint32, I, I, I, ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -137,12 +165,13 @@ def _ptr(x) -> int:
 
 def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
                 backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
-                boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0):
+                boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0,
+                max_batch_units: int = 0):
     """lk_init_params plus the arrays it points to (kept alive by the tuple)."""
     sz = (ctypes.c_int * len(sizes))(*sizes)
     sm = None if smids is None else (ctypes.c_int * len(smids))(*smids)
     p = lk_init_params(device, len(sizes), sz, sm, threads_per_cta, ring_depth, backoff_base_ns, backoff_cap_ns,
-                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags)
+                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags, max_batch_units, 0)
     return p, (sz, sm)
 
 
@@ -340,3 +369,55 @@ def lk_launch_noalloc(op: int, n: int, ins=(), out=None, ctas: int = 37, threads
     d = lk_desc(op, 0, n, 0)
     arr = (ctypes.c_void_p * max(1, len(ins)))(*[_ptr(i) for i in ins]) if ins else None
     return lib.lk_launch_noalloc(device, ctypes.byref(d), arr, len(ins), _ptr(out), ctas, threads, stream or 0)
+
+
+def batch_items(rows) -> np.ndarray:
+    """rows: iterable of (op, n, ins, out[, parts]) with pointers as ints or tensors."""
+    rows = list(rows)
+    a = np.zeros(len(rows), dtype=BATCH_ITEM_DTYPE)
+    for i, r in enumerate(rows):
+        op, n, ins, out = r[:4]
+        a[i]["op"], a[i]["n"] = op, n
+        a[i]["in0"] = _ptr(ins[0]) if len(ins) > 0 else 0
+        a[i]["in1"] = _ptr(ins[1]) if len(ins) > 1 else 0
+        a[i]["out"] = _ptr(out)
+        a[i]["parts"] = r[4] if len(r) > 4 else 0
+    return a
+
+
+def lk_submit_batch(ctx: Context, cluster: int, items: np.ndarray, max_parts: int = 0, part_bytes: int = 0) -> int | None:
+    """Post a batch (BATCH_ITEM_DTYPE array).  Returns the handle, or None if
+    the ring or the batch tables are busy (LK_EAGAIN)."""
+    items = np.ascontiguousarray(items, dtype=BATCH_ITEM_DTYPE)
+    t = lk_batch_tune(max_parts, 0, part_bytes)
+    h = ctypes.c_uint64()
+    rc = ctx.lib.lk_submit_batch(ctx.ptr, cluster, items.ctypes.data if items.size else None, items.size,
+                                 ctypes.byref(t), ctypes.byref(h))
+    if rc == LK_EAGAIN:
+        return None
+    if rc != LK_OK:
+        raise LkError(rc, "lk_submit_batch")
+    return h.value
+
+
+def lk_baseline_graph(items: np.ndarray, max_ctas: int, threads: int = 256, reps: int = 1, device: int = 0):
+    """The batch as one CUDA graph of ordinary launches; returns per-repetition ms."""
+    lib = load()
+    items = np.ascontiguousarray(items, dtype=BATCH_ITEM_DTYPE)
+    ms = (ctypes.c_float * reps)()
+    rc = lib.lk_baseline_graph(device, items.ctypes.data if items.size else None, items.size, max_ctas, threads,
+                               reps, ms)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_baseline_graph")
+    return np.frombuffer(ms, dtype=np.float32).copy()
+
+
+def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int, arena=None, arena_bytes: int = 0,
+             window: int = 0, chunk_bytes: int = 0, timeout_ns: int = 0):
+    """Serve REQUEST_DTYPE requests; returns (rc, REQUEST_RES_DTYPE results)."""
+    reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+    res = np.zeros(reqs.size, dtype=REQUEST_RES_DTYPE)
+    prm = lk_serve_params(n_producers, window, chunk_bytes, budget_bytes, _ptr(arena) or None, arena_bytes, timeout_ns)
+    rc = ctx.lib.lk_serve(ctx.ptr, reqs.ctypes.data if reqs.size else None, reqs.size, ctypes.byref(prm),
+                          res.ctypes.data if reqs.size else None)
+    return rc, res

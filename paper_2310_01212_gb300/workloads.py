@@ -12,6 +12,14 @@ Configurations (all seeded):
              one 64x64x64 float32 GEMM tile of N(0,1) values; Poisson
              arrivals at 20,000 per second; round-robin clusters; one host
              submitter thread per cluster.
+  batching   batches of int-log-uniform 1..4096 items, item sizes
+             log-uniform 1,024..16,777,216 elements, float32 sum / int32 add
+             50/50, one post per batch to a cluster of every SM; a seeded
+             prefix of the 1,000,000-descriptor stream.
+  serving    8 host producer threads, open-loop Poisson arrivals at 5k..200k
+             requests/s, request sizes log-uniform 4 KB..256 MB over the four
+             bodies (a GEMM request of S bytes is floor(S / 48 KB) >= 1 tiles),
+             admission by a 64 GB budget, 148 SMs as 4 clusters of 37.
   isolation  a critical cluster of 16 SMs releases an FP32 sum over 1 MB
              (262,144 N(0,1) values) every 1 ms, waiting for each; a
              best-effort cluster of 132 SMs runs int32 copies of 4 GiB and
@@ -32,6 +40,10 @@ from . import lk, synth
 SMALL = dict(sizes=[2, 2], threads=256, items=10_000, n=4096, lo=-(1 << 20), hi=1 << 20, seed=0)
 FULL_CHIP = dict(sizes=[37, 37, 37, 37], threads=256, rate_per_s=20_000.0, n_add=65_536, n_hist=1 << 20,
                  n_sum=65_536, gemm_tiles=1, seed=0)
+BATCHING = dict(max_count=4096, n_lo=1024, n_hi=16_777_216, seed=0)
+SERVING = dict(sizes=[37, 37, 37, 37], threads=256, producers=8, rates=(5_000, 10_000, 20_000, 50_000, 100_000, 200_000),
+               s_lo=4096, s_hi=256 << 20, budget_bytes=64 << 30, arena_bytes=24 << 30, chunk_bytes=16 << 20, window=2,
+               seed=0)
 ISOLATION = dict(sizes=[16, 132], threads=256, period_ns=1_000_000, crit_n=262_144, copy_n=1 << 30,
                  hist_n=256 << 20, seed=0)
 OPS4 = (lk.LK_OP_ADD_I32, lk.LK_OP_HIST_U8, lk.LK_OP_SUM_F32, lk.LK_OP_GEMM64_F32)
@@ -233,3 +245,131 @@ def isolation_traces(periods: int, be_items: int, crit_in, crit_out, copy_src, c
     be["in0"] = np.where(copy, copy_src.data_ptr(), hist_in.data_ptr())
     be["out"] = np.where(copy, copy_dst.data_ptr(), hist_out.data_ptr())
     return np.concatenate([crit, be])
+
+
+def batching_batch(pools: Pools, seed: int, b: int, cfg: dict = BATCHING, max_count: int | None = None):
+    """Batch b of the batching stream: (BATCH_ITEM_DTYPE array, meta).  Inputs
+    are slices of the pools at random 16-B-aligned offsets; add outputs land at
+    random offsets of the add arena and sum outputs in slots (outputs of
+    different items may overlap: this stream is for timing; parity uses
+    `batching_parity_batch`)."""
+    key = 50_000 + 100 * b
+    count = int(synth.log_uniform_int(seed, key, 1, 1, cfg["max_count"] if max_count is None else max_count)[0])
+    ops = np.where(synth.choice(seed, key + 1, count, 2) == 0, lk.LK_OP_SUM_F32, lk.LK_OP_ADD_I32).astype(np.uint32)
+    n = synth.log_uniform_int(seed, key + 2, count, cfg["n_lo"], cfg["n_hi"]).astype(np.uint64)
+    off0 = np.zeros(count, dtype=np.int64)
+    off1 = np.zeros(count, dtype=np.int64)
+    offo = np.zeros(count, dtype=np.int64)
+    u0 = synth.unit_open(seed, key + 3, count)
+    u1 = synth.unit_open(seed, key + 4, count)
+    u2 = synth.unit_open(seed, key + 5, count)
+    it = np.zeros(count, dtype=lk.BATCH_ITEM_DTYPE)
+    it["op"], it["n"] = ops, n
+    add_out = pools.out_add.view(-1)
+    for i in range(count):
+        k = int(n[i])
+        if ops[i] == lk.LK_OP_ADD_I32:
+            off0[i] = int(u0[i] * (pools.i32.numel() - k)) // 4 * 4
+            off1[i] = int(u1[i] * (pools.i32.numel() - k)) // 4 * 4
+            offo[i] = int(u2[i] * (add_out.numel() - k)) // 4 * 4
+        else:
+            off0[i] = int(u0[i] * (pools.f32.numel() - k)) // 4 * 4
+            offo[i] = i % pools.slots
+    m = ops == lk.LK_OP_ADD_I32
+    it["in0"][m] = pools.i32.data_ptr() + 4 * off0[m].astype(np.uint64)
+    it["in1"][m] = pools.i32.data_ptr() + 4 * off1[m].astype(np.uint64)
+    it["out"][m] = add_out.data_ptr() + 4 * offo[m].astype(np.uint64)
+    m = ~m
+    it["in0"][m] = pools.f32.data_ptr() + 4 * off0[m].astype(np.uint64)
+    it["out"][m] = pools.out_sum.data_ptr() + 16 * offo[m].astype(np.uint64)
+    bytes_ = np.where(ops == lk.LK_OP_ADD_I32, 12 * n, 4 * n + 4).astype(np.float64)
+    return it, dict(op=ops, n=n, off0=off0, off1=off1, offo=offo, bytes=float(bytes_.sum()))
+
+
+def batching_parity_batch(pools: Pools, seed: int, count: int = 48, n_hi: int = 1 << 20):
+    """A batch of the same mix whose items write disjoint outputs (add outputs
+    back to back in the add arena, sums in distinct slots), for oracle checks."""
+    ops = np.where(synth.choice(seed, 77_001, count, 2) == 0, lk.LK_OP_SUM_F32, lk.LK_OP_ADD_I32).astype(np.uint32)
+    n = synth.log_uniform_int(seed, 77_002, count, 1024, n_hi).astype(np.uint64)
+    u0 = synth.unit_open(seed, 77_003, count)
+    u1 = synth.unit_open(seed, 77_004, count)
+    it = np.zeros(count, dtype=lk.BATCH_ITEM_DTYPE)
+    it["op"], it["n"] = ops, n
+    meta = dict(op=ops, n=n, off0=np.zeros(count, np.int64), off1=np.zeros(count, np.int64),
+                offo=np.zeros(count, np.int64))
+    add_out = pools.out_add.view(-1)
+    cursor = 0
+    for i in range(count):
+        k = int(n[i])
+        if ops[i] == lk.LK_OP_ADD_I32:
+            meta["off0"][i] = int(u0[i] * (pools.i32.numel() - k)) // 4 * 4
+            meta["off1"][i] = int(u1[i] * (pools.i32.numel() - k)) // 4 * 4
+            meta["offo"][i] = cursor
+            cursor += (k + 3) // 4 * 4
+            it[i]["in0"] = pools.i32.data_ptr() + 4 * int(meta["off0"][i])
+            it[i]["in1"] = pools.i32.data_ptr() + 4 * int(meta["off1"][i])
+            it[i]["out"] = add_out.data_ptr() + 4 * int(meta["offo"][i])
+        else:
+            meta["off0"][i] = int(u0[i] * (pools.f32.numel() - k)) // 4 * 4
+            meta["offo"][i] = pools.slots - 1 - i
+            it[i]["in0"] = pools.f32.data_ptr() + 4 * int(meta["off0"][i])
+            it[i]["out"] = pools.out_sum.data_ptr() + 16 * int(meta["offo"][i])
+    return it, meta
+
+
+def check_batching_parity(pools: Pools, meta: dict, oracle) -> int:
+    """Number of items of a parity batch whose output differs from the oracle."""
+    bad = 0
+    add_out = pools.out_add.view(-1)
+    for i in range(meta["op"].size):
+        k = int(meta["n"][i])
+        if meta["op"][i] == lk.LK_OP_ADD_I32:
+            a = pools.i32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
+            b = pools.i32[int(meta["off1"][i]):int(meta["off1"][i]) + k].cpu().numpy()
+            o = add_out[int(meta["offo"][i]):int(meta["offo"][i]) + k].cpu().numpy()
+            bad += 0 if np.array_equal(o, oracle.add_i32(a, b)) else 1
+        else:
+            x = pools.f32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
+            o = float(pools.out_sum[int(meta["offo"][i]), 0].cpu())
+            bad += 0 if abs(o - oracle.sum_f32(x)) <= 1e-4 * oracle.abs_sum_f32(x) else 1
+    return bad
+
+
+def serving_requests(pools: Pools, seed: int, rate: float, seconds: float, cfg: dict = SERVING,
+                     s_hi: int | None = None, outputs=None):
+    """Open-loop Poisson requests at `rate` per second for `seconds`; inputs are
+    slices of the pools; outputs from the server's arena unless `outputs`
+    (a list of device tensors, one per request) is given.  Returns the
+    REQUEST_DTYPE array and the input bytes of each request."""
+    key = 90_000 + int(rate)
+    mean_gap = 1e9 / rate
+    count = max(1, int(rate * seconds))
+    t = np.cumsum(synth.exponential(seed, key, count, mean_gap)).astype(np.uint64)
+    ops = np.array([lk.LK_OP_ADD_I32, lk.LK_OP_HIST_U8, lk.LK_OP_SUM_F32, lk.LK_OP_GEMM64_F32],
+                   dtype=np.uint32)[synth.choice(seed, key + 1, count, 4)]
+    S = synth.log_uniform_int(seed, key + 2, count, cfg["s_lo"], cfg["s_hi"] if s_hi is None else s_hi)
+    n = np.where(ops == lk.LK_OP_HIST_U8, S, np.where(ops == lk.LK_OP_GEMM64_F32, np.maximum(1, S // 49152), S // 4))
+    n = n.astype(np.uint64)
+    u0 = synth.unit_open(seed, key + 3, count)
+    u1 = synth.unit_open(seed, key + 4, count)
+    r = np.zeros(count, dtype=lk.REQUEST_DTYPE)
+    r["t_arrival_ns"], r["op"], r["n"] = t, ops, n
+    r["producer"] = np.arange(count) % cfg["producers"]
+    for i in range(count):
+        k = int(n[i])
+        if ops[i] == lk.LK_OP_ADD_I32:
+            r[i]["in0"] = pools.i32.data_ptr() + 4 * (int(u0[i] * (pools.i32.numel() - k)) // 4 * 4)
+            r[i]["in1"] = pools.i32.data_ptr() + 4 * (int(u1[i] * (pools.i32.numel() - k)) // 4 * 4)
+        elif ops[i] == lk.LK_OP_HIST_U8:
+            r[i]["in0"] = pools.u8.data_ptr() + int(u0[i] * (pools.u8.numel() - k)) // 16 * 16
+        elif ops[i] == lk.LK_OP_SUM_F32:
+            r[i]["in0"] = pools.f32.data_ptr() + 4 * (int(u0[i] * (pools.f32.numel() - k)) // 4 * 4)
+        else:
+            t4 = 4096 * k
+            r[i]["in0"] = pools.f32.data_ptr() + 4 * (int(u0[i] * (pools.f32.numel() - t4)) // 4 * 4)
+            r[i]["in1"] = pools.f32.data_ptr() + 4 * (int(u1[i] * (pools.f32.numel() - t4)) // 4 * 4)
+        if outputs is not None:
+            r[i]["out"] = outputs[i].data_ptr()
+    in_bytes = np.where(ops == lk.LK_OP_ADD_I32, 8 * n, np.where(ops == lk.LK_OP_HIST_U8, n,
+                        np.where(ops == lk.LK_OP_SUM_F32, 4 * n, 32768 * n))).astype(np.float64)
+    return r, in_bytes

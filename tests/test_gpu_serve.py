@@ -1,0 +1,88 @@
+"""GPU parity of the serving loop (lk_serve): requests of uneven size arriving
+from 8 producers are admitted, split into chunks that interleave across the
+clusters, combined, and every output matches the oracle; each result is
+bit-identical when the request is served alone."""
+import numpy as np
+import pytest
+
+from gpu_util import gemm_ok, host, need_gpu, sum_ok
+from paper_2310_01212_gb300 import lk, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def served(native_built, oracle_lib):
+    torch = need_gpu()
+    pools = wl.Pools.create(5, i32_bytes=256 << 20, u8_bytes=256 << 20, f32_bytes=256 << 20, slots=4, n_add=16)
+    reqs, _ = wl.serving_requests(pools, 5, 40_000.0, 0.006, s_hi=24 << 20)
+    outs = []
+    for r in reqs:
+        op, n = int(r["op"]), int(r["n"])
+        if op == lk.LK_OP_ADD_I32:
+            outs.append(torch.zeros(n, dtype=torch.int32, device="cuda"))
+        elif op == lk.LK_OP_HIST_U8:
+            outs.append(torch.full((256,), -1, dtype=torch.int32, device="cuda"))
+        elif op == lk.LK_OP_SUM_F32:
+            outs.append(torch.full((4,), 7.0, device="cuda"))
+        else:
+            outs.append(torch.zeros((n, 64, 64), device="cuda"))
+    reqs["out"] = [o.data_ptr() for o in outs]
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")   # chunk scratch of split sums / histograms
+    torch.cuda.synchronize()
+    with lk.lk_init([8, 8, 8, 8], idle_lease_ns=10_000_000_000) as c:
+        rc, res = lk.lk_serve(c, reqs, n_producers=8, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
+                              window=2, chunk_bytes=1 << 20)
+    return torch, pools, reqs, outs, rc, res, arena
+
+
+def _inputs(pools, r):
+    op, n = int(r["op"]), int(r["n"])
+    def sl(t, ptr, count, esize):
+        off = (int(ptr) - t.data_ptr()) // esize
+        return t[off:off + count].cpu().numpy()
+    if op == lk.LK_OP_ADD_I32:
+        return sl(pools.i32, r["in0"], n, 4), sl(pools.i32, r["in1"], n, 4)
+    if op == lk.LK_OP_HIST_U8:
+        return (sl(pools.u8, r["in0"], n, 1),)
+    if op == lk.LK_OP_SUM_F32:
+        return (sl(pools.f32, r["in0"], n, 4),)
+    return sl(pools.f32, r["in0"], 4096 * n, 4).reshape(n, 64, 64), sl(pools.f32, r["in1"], 4096 * n, 4).reshape(n, 64, 64)
+
+
+def test_served_outputs_match_oracle(served, oracle_lib):
+    torch, pools, reqs, outs, rc, res, arena = served
+    assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+    assert reqs.size >= 100 and res["chunks"].max() > 1
+    for r, o in zip(reqs, outs):
+        op = int(r["op"])
+        ins = _inputs(pools, r)
+        got = host(o)
+        if op == lk.LK_OP_ADD_I32:
+            assert np.array_equal(got, oracle_lib.add_i32(*ins))
+        elif op == lk.LK_OP_HIST_U8:
+            assert np.array_equal(got.astype(np.int64), oracle_lib.hist_u8(*ins))
+        elif op == lk.LK_OP_SUM_F32:
+            assert sum_ok(got[0], ins[0], oracle_lib)
+        else:
+            assert gemm_ok(got, *ins, oracle_lib)
+
+
+def test_each_result_same_alone_and_in_the_mix(served):
+    torch, pools, reqs, outs, rc, res, arena = served
+    pick = [i for i in range(reqs.size) if int(reqs[i]["op"]) in (lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8)][:12]
+    pick += [i for i in range(reqs.size) if int(reqs[i]["op"]) == lk.LK_OP_ADD_I32][:4]
+    with lk.lk_init([8, 8, 8, 8], idle_lease_ns=10_000_000_000) as c:
+        for i in pick:
+            alone_out = torch.empty_like(outs[i])
+            one = reqs[i:i + 1].copy()
+            one["t_arrival_ns"] = 0
+            one["producer"] = 0
+            one["out"] = alone_out.data_ptr()
+            rc1, r1 = lk.lk_serve(c, one, n_producers=1, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
+                                  window=2, chunk_bytes=1 << 20)
+            assert rc1 == lk.LK_OK and r1["chunks"][0] == res["chunks"][i]
+            a, m = host(alone_out), host(outs[i])
+            if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32:
+                a, m = a[:1], m[:1]   # the result; the rest of the 16-byte slot is padding
+            assert np.array_equal(a, m), (i, int(reqs[i]["op"]))

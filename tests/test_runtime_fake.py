@@ -263,3 +263,121 @@ def test_finite_mode_runs_the_list(fake_env):
     assert ms >= 0
     assert sorted(log[log["cluster"] == 0]["seq"].tolist()) == [1, 1, 2, 2, 3, 3, 4, 4]
     assert sorted(log[log["cluster"] == 1]["seq"].tolist()) == [1, 2, 3]
+
+
+# ---- batches -------------------------------------------------------------------------
+def test_batch_posts_one_descriptor(fake_env):
+    with ctx_(sizes=(4,), exec_log_cap=16) as c:
+        items = lk.batch_items([(lk.LK_OP_ADD_I32, 1 << 20, (A, A), A), (lk.LK_OP_SUM_F32, 1000, (A,), A),
+                                (lk.LK_OP_NOP, 0, (), None)])
+        h = lk.lk_submit_batch(c, 0, items)
+        assert h is not None and lk.lk_wait(c, h) == lk.LK_OK
+        log, _ = lk.lk_exec_log(c)
+        assert set(log["op"].tolist()) == {lk.LK_OP_BATCH} and len(log) == 4
+        assert lk.lk_wait(c, lk.lk_submit_batch(c, 0, lk.batch_items([]))) == lk.LK_OK   # empty batch
+
+
+@pytest.mark.parametrize("bad", [
+    (lk.LK_OP_ADD_I32, 16, (A, A + 4), A),      # misaligned
+    (lk.LK_OP_SUM_F32, 16, (A,), None),         # sum needs an output
+    (9, 16, (A,), A),                           # unknown op
+    (lk.LK_OP_COPY_I32, 16, (A,), A, 9),        # more than 8 parts
+])
+def test_batch_item_checks(fake_env, bad):
+    with ctx_() as c:
+        with pytest.raises(lk.LkError) as e:
+            lk.lk_submit_batch(c, 0, lk.batch_items([bad]))
+        assert e.value.code == lk.LK_EINVAL
+
+
+def test_batch_unit_capacity(fake_env):
+    with ctx_(sizes=(8,), max_batch_units=64) as c:
+        ok = lk.batch_items([(lk.LK_OP_COPY_I32, 1 << 24, (A,), A, 8)] * 8)      # 64 units
+        assert lk.lk_wait(c, lk.lk_submit_batch(c, 0, ok)) == lk.LK_OK
+        with pytest.raises(lk.LkError):
+            lk.lk_submit_batch(c, 0, lk.batch_items([(lk.LK_OP_COPY_I32, 1 << 24, (A,), A, 8)] * 9))
+
+
+def test_batch_tables_busy_is_refused(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "300000"
+    with ctx_(sizes=(2,)) as c:
+        items = lk.batch_items([(lk.LK_OP_NOP, 0, (), None)])
+        h1 = lk.lk_submit_batch(c, 0, items)
+        h2 = lk.lk_submit_batch(c, 0, items)
+        assert h1 and h2
+        assert lk.lk_submit_batch(c, 0, items) is None     # both unit tables still in use
+        assert lk.lk_wait(c, h1) == lk.LK_OK
+        h3 = lk.lk_submit_batch(c, 0, items)
+        assert h3 is not None
+        assert lk.lk_wait(c, h3) == lk.LK_OK
+
+
+def test_split_rule_counts_units(fake_env):
+    # parts = ceil(input bytes / part_bytes) capped by max_parts and the cluster size
+    with ctx_(sizes=(4,), max_batch_units=10) as c:
+        items = lk.batch_items([(lk.LK_OP_SUM_F32, 1 << 20, (A,), A)] * 2)      # 4 MiB each
+        assert lk.lk_wait(c, lk.lk_submit_batch(c, 0, items, part_bytes=1 << 20)) == lk.LK_OK   # 4 + 4 units
+        with pytest.raises(lk.LkError):   # 3 items x 4 parts = 12 > 10
+            lk.lk_submit_batch(c, 0, lk.batch_items([(lk.LK_OP_SUM_F32, 1 << 20, (A,), A)] * 3), part_bytes=1 << 20)
+        assert lk.lk_wait(c, lk.lk_submit_batch(c, 0, lk.batch_items([(lk.LK_OP_SUM_F32, 1 << 20, (A,), A)] * 3),
+                                                max_parts=2, part_bytes=1 << 20)) == lk.LK_OK
+
+
+# ---- serving ---------------------------------------------------------------------------
+def _reqs(n, ops, sizes, producers=4, gap_ns=20_000, out=None):
+    r = np.zeros(n, dtype=lk.REQUEST_DTYPE)
+    r["t_arrival_ns"] = np.arange(n) * gap_ns
+    r["op"] = [ops[i % len(ops)] for i in range(n)]
+    r["producer"] = np.arange(n) % producers
+    r["n"] = [sizes[i % len(sizes)] for i in range(n)]
+    r["in0"] = A
+    r["in1"] = A
+    r["out"] = 0 if out is None else out
+    return r
+
+
+def test_serve_admits_chunks_and_combines(fake_env):
+    with ctx_(sizes=(2, 2, 2), exec_log_cap=4096) as c:
+        reqs = _reqs(60, [lk.LK_OP_ADD_I32, lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8, lk.LK_OP_GEMM64_F32],
+                     [1 << 10, 5 << 20, 3 << 20, 40])
+        rc, res = lk.lk_serve(c, reqs, n_producers=4, budget_bytes=1 << 34, arena=1 << 20, arena_bytes=1 << 34,
+                              chunk_bytes=1 << 20)
+        assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+        assert np.all(res["t_complete_ns"] >= res["t_admit_ns"])
+        assert np.all(res["t_admit_ns"] >= reqs["t_arrival_ns"])
+        # chunks: ceil(input bytes / 1 MiB) in whole alignment units
+        want = {lk.LK_OP_ADD_I32: 1, lk.LK_OP_SUM_F32: 20, lk.LK_OP_HIST_U8: 3, lk.LK_OP_GEMM64_F32: 2}
+        for r, q in zip(reqs, res):
+            assert q["chunks"] == want[int(r["op"])], (int(r["op"]), q["chunks"])
+        log, _ = lk.lk_exec_log(c, cap=1 << 16)
+        ops = log["op"]
+        # 15 split sums and 15 split histograms, each finished by one combine (2 ranks log each)
+        assert np.sum(ops == lk.LK_OP_COMBINE_SUM) == 2 * 15 and np.sum(ops == lk.LK_OP_COMBINE_HIST) == 2 * 15
+        # arena outputs were handed out and given back: all 256-byte aligned
+        assert np.all(res["out"] % 256 == 0)
+
+
+def test_serve_budget_limits_admission(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "2000"
+    with ctx_(sizes=(1, 1)) as c:
+        reqs = _reqs(8, [lk.LK_OP_COPY_I32], [1 << 20], producers=2, gap_ns=0)   # 8 MiB held each
+        rc, res = lk.lk_serve(c, reqs, n_producers=2, budget_bytes=8 << 20, arena=1 << 20, arena_bytes=1 << 30)
+        assert rc == lk.LK_OK
+        # one request fits the budget at a time: admissions are serialised
+        order = np.argsort(res["t_admit_ns"])
+        adm, comp = res["t_admit_ns"][order], res["t_complete_ns"][order]
+        assert np.all(adm[1:] >= comp[:-1])
+
+
+def test_serve_rejects_requests_larger_than_the_budget(fake_env):
+    with ctx_(sizes=(1,)) as c:
+        reqs = _reqs(1, [lk.LK_OP_COPY_I32], [1 << 20])
+        rc, _ = lk.lk_serve(c, reqs, n_producers=4, budget_bytes=1 << 20, arena=1 << 20, arena_bytes=1 << 30)
+        assert rc == lk.LK_ENOMEM
+
+
+def test_serve_needs_equal_clusters(fake_env):
+    with ctx_(sizes=(1, 2)) as c:
+        rc, _ = lk.lk_serve(c, _reqs(1, [lk.LK_OP_NOP + 1], [16]), n_producers=4, budget_bytes=1 << 30,
+                            arena=1 << 20, arena_bytes=1 << 30)
+        assert rc == lk.LK_EINVAL
