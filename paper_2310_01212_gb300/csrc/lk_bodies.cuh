@@ -53,7 +53,8 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 #define LK_SMEM_STREAM (128u * 1024u)  /* streaming stages                    */
 #define LK_SMEM_DYN (LK_SMEM_WORK + LK_SMEM_STREAM)
 #define LK_STAGES 4u
-#define LK_NUM_BARS 4u                 /* mbarriers: one per stage (GEMM uses two) */
+#define LK_GEMM_STAGES 6u              /* GEMM stages of 32 KB over the whole 192 KB */
+#define LK_NUM_BARS 6u                 /* mbarriers: one per stage                */
 
 /* Stream the 16-byte vectors [beg, end) of NIN inputs through the stages.
  * consume(v0, nv, s0, s1) runs on every thread for each chunk: vectors
@@ -389,11 +390,13 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
   return U;
 }
 
-/* Shared memory: two stages of (A rows 16 KB, B tile 16 KB); bars[2]. */
+/* Shared memory: LK_GEMM_STAGES stages of (A rows 16 KB, B tile 16 KB) over
+ * the whole dynamic shared memory; one mbarrier per stage. */
 #define LK_GEMM_STAGE_FLOATS 8192u
 
 /* Returns false if a staging copy did not complete before `deadline`.
  * `phase` holds one parity bit per stage and persists across descriptors. */
+template <bool FULL_UNROLL>
 __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float* sm, uint64_t* bars,
                                           uint32_t& phase, uint64_t deadline) {
   const uint64_t tiles = d.n;
@@ -406,32 +409,33 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   const float* B = reinterpret_cast<const float*>(d.in1);
   float* C = reinterpret_cast<float*>(d.out);
   const uint32_t T = blockDim.x;
-  auto issue = [&](uint64_t u, uint32_t st) {
-    if (threadIdx.x == 0) {
-      const uint64_t tile = u / U;
-      const uint32_t rb = (uint32_t)(u % U);
-      float* sA = sm + st * LK_GEMM_STAGE_FLOATS;
-      fence_proxy_async_smem();
-      mbar_expect_tx(&bars[st], rows * 256u + 16384u);
-      bulk_g2s(sA, A + tile * 4096 + (uint64_t)rb * rows * 64, rows * 256u, &bars[st]);
-      bulk_g2s(sA + 4096, B + tile * 4096, 16384u, &bars[st]);
-    }
+  auto issue = [&](uint64_t u) {   /* thread 0 */
+    const uint32_t st = (uint32_t)((u - beg) % LK_GEMM_STAGES);
+    const uint64_t tile = u / U;
+    const uint32_t rb = (uint32_t)(u % U);
+    float* sA = sm + st * LK_GEMM_STAGE_FLOATS;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bars[st], rows * 256u + 16384u);
+    bulk_g2s(sA, A + tile * 4096 + (uint64_t)rb * rows * 64, rows * 256u, &bars[st]);
+    bulk_g2s(sA + 4096, B + tile * 4096, 16384u, &bars[st]);
   };
   __shared__ int s_staged;
-  __syncthreads();          /* both stages are free: the previous use ended with a barrier */
-  issue(beg, 0);
+  __syncthreads();          /* every stage is free: the previous use ended with a barrier */
+  if (threadIdx.x == 0)
+    for (uint64_t u = beg; u < end && u < beg + LK_GEMM_STAGES; ++u) issue(u);
   bool ok = true;
   for (uint64_t u = beg; u < end; ++u) {
-    const uint32_t st = (uint32_t)((u - beg) & 1);
-    if (u + 1 < end) issue(u + 1, st ^ 1u);
+    const uint32_t st = (uint32_t)((u - beg) % LK_GEMM_STAGES);
     /* thread 0 alone decides whether the stage arrived in time, so that every
      * thread takes the same path through the barriers below */
     if (threadIdx.x == 0) {
       int arrived = mbar_wait(&bars[st], (phase >> st) & 1u, deadline);
       if (!arrived) {
         /* let this CTA's own copies land before giving up */
-        mbar_wait(&bars[st], (phase >> st) & 1u, deadline + 1000000000ull);
-        if (u + 1 < end) mbar_wait(&bars[st ^ 1u], (phase >> (st ^ 1u)) & 1u, deadline + 1000000000ull);
+        for (uint64_t v = u; v < end && v < u + LK_GEMM_STAGES; ++v) {
+          const uint32_t s2 = (uint32_t)((v - beg) % LK_GEMM_STAGES);
+          mbar_wait(&bars[s2], (phase >> s2) & 1u, deadline + 1000000000ull);
+        }
       }
       s_staged = arrived;
     }
@@ -440,6 +444,8 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
       ok = false;
       break;
     }
+    /* every thread finished unit u-1: refill its stage with unit u-1+STAGES */
+    if (threadIdx.x == 0 && u > beg && u - 1 + LK_GEMM_STAGES < end) issue(u - 1 + LK_GEMM_STAGES);
     /* the phase is complete: this wait returns at once and makes the copied
      * bytes visible to this thread */
     mbar_wait(&bars[st], (phase >> st) & 1u, deadline + 1000000000ull);
@@ -456,7 +462,7 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
-#pragma unroll 2
+#pragma unroll(FULL_UNROLL ? 16 : 2)
       for (uint32_t k = 0; k < 64; k += 4) {
         float av[4][4], bv[4][4];
 #pragma unroll
@@ -481,8 +487,8 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
       for (int i = 0; i < 4; ++i)
         *reinterpret_cast<float4*>(crow + i * 64) = make_float4(c[i][0], c[i][1], c[i][2], c[i][3]);
     }
-    __syncthreads();        /* stage st is free for unit u + 2 */
   }
+  __syncthreads();          /* every stage is free for the next body */
   return ok;
 }
 

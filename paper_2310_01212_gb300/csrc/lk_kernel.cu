@@ -238,7 +238,10 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
 }
 
 /* This CTA's share of descriptor d (rank r of S).  Returns an LK_DERR_* code
- * or 0.  `partial_out` receives the sum body's per-CTA partial. */
+ * or 0.  `partial_out` receives the sum body's per-CTA partial.  MAXT (the
+ * largest block size of the calling kernel) sets how far the GEMM's k loop is
+ * unrolled: fully at up to 256 threads, where the registers allow it. */
+template <int MAXT>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                         uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
@@ -249,7 +252,9 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
     case LK_OP_COPY_I32: ok = body_copy(d, r, S, dsm, bars, phase, deadline); break;
     case LK_OP_SUM_F32: ok = body_sum(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
     case LK_OP_HIST_U8: ok = body_hist(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
-    case LK_OP_GEMM64_F32: ok = body_gemm(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline); break;
+    case LK_OP_GEMM64_F32:
+      ok = body_gemm<(MAXT <= 256)>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline);
+      break;
     case LK_OP_COMBINE_SUM: body_combine_sum(d, r); break;
     case LK_OP_COMBINE_HIST: body_combine_hist(d, r); break;
     case LK_OP_NOP: break;
@@ -265,6 +270,7 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
  * per-item state: the last part to finish writes the item's output (sums in
  * binary64, in part order) and returns the state to zero.  Returns an
  * LK_DERR_* code or 0. */
+template <int MAXT>
 __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
                                          uint64_t* bars, uint32_t& phase, float* red) {
   __shared__ uint64_t s_unit[6];
@@ -340,7 +346,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
         if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
       }
     } else {
-      const int e = run_body(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
+      const int e = run_body<MAXT>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
       ok = (e == 0);
     }
     __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
@@ -477,8 +483,8 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = op == LK_OP_BATCH ? run_batch(a, d, c, r, dsm, s_bars, phase, s_red)
-                                       : run_body(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+    const int berr = op == LK_OP_BATCH ? run_batch<MAXT>(a, d, c, r, dsm, s_bars, phase, s_red)
+                                       : run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -563,7 +569,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
+  run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {
