@@ -61,6 +61,12 @@ def lib() -> ctypes.CDLL:
             l.lko_abs_sum_f32.restype = ctypes.c_double
             l.lko_gemm64_f32.argtypes = [P, P, P, S]
             l.lko_gemm64_abs_bound.argtypes = [P, P, P, S]
+            l.lko_spin_xor.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64]
+            l.lko_spin_xor.restype = ctypes.c_uint32
+            l.lko_lcg_jump.argtypes = [ctypes.c_uint32, ctypes.c_uint64]
+            l.lko_lcg_jump.restype = ctypes.c_uint32
+            l.lko_lcg_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64]
+            l.lko_lcg_brute.restype = ctypes.c_uint32
             l.lko_check_exec_log.argtypes = [S] + [P] * 6 + [ctypes.c_int32] + [P] * 6 + [ctypes.POINTER(CheckResult)]
             l.lko_check_exec_log.restype = ctypes.c_int64
             _lib = l
@@ -120,6 +126,18 @@ def gemm64_abs_bound(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     C = np.empty(A.shape, dtype=np.float64)
     lib().lko_gemm64_abs_bound(_p(A), _p(B), _p(C), A.size // 4096)
     return C
+
+
+def spin_xor(rank: int, threads: int, iters: int) -> int:
+    return int(lib().lko_spin_xor(rank, threads, iters))
+
+
+def lcg_jump(x0: int, iters: int) -> int:
+    return int(lib().lko_lcg_jump(x0, iters))
+
+
+def lcg_brute(x0: int, iters: int) -> int:
+    return int(lib().lko_lcg_brute(x0, iters))
 
 
 # violation codes of the execution-log checker (lk_oracle.h)

@@ -85,6 +85,36 @@ void lko_gemm64_abs_bound(const float* A, const float* B, double* bound, size_t 
   }
 }
 
+/* Affine map f(x) = a x + c (mod 2^32).  f applied k times is again affine;
+ * composing g after f gives (a_g a_f, a_g c_f + c_g).  Square-and-multiply
+ * over the bits of `iters` gives f^iters in O(log iters) compositions. */
+uint32_t lko_lcg_jump(uint32_t x0, uint64_t iters) {
+  uint32_t acc_a = 1u, acc_c = 0u;          /* identity map */
+  uint32_t pa = 1664525u, pc = 1013904223u; /* f^(2^bit) */
+  while (iters) {
+    if (iters & 1u) {                       /* acc <- p after acc */
+      acc_c = pa * acc_c + pc;
+      acc_a = pa * acc_a;
+    }
+    pc = pa * pc + pc;                      /* p <- p after p */
+    pa = pa * pa;
+    iters >>= 1;
+  }
+  return acc_a * x0 + acc_c;
+}
+
+uint32_t lko_lcg_brute(uint32_t x0, uint64_t iters) {
+  uint32_t x = x0;
+  for (uint64_t i = 0; i < iters; ++i) x = 1664525u * x + 1013904223u;
+  return x;
+}
+
+uint32_t lko_spin_xor(uint32_t rank, uint32_t threads, uint64_t iters) {
+  uint32_t r = 0;
+  for (uint32_t t = 0; t < threads; ++t) r ^= lko_lcg_jump(65536u * rank + t + 1u, iters);
+  return r;
+}
+
 /* ---------------------------------------------------------------------------
  * Execution-log checker.
  *

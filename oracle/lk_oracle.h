@@ -35,6 +35,18 @@ double lko_abs_sum_f32(const float* x, size_t n);
 void   lko_gemm64_f32(const float* A, const float* B, double* C, size_t tiles);
 void   lko_gemm64_abs_bound(const float* A, const float* B, double* bound, size_t tiles);
 
+/* The compute-bound loop of Sec. III ("a loop of 20k iterations ... no memory
+ * transfer or accesses"), made checkable: thread t of CTA r iterates the
+ * linear congruential map x <- 1664525 x + 1013904223 (mod 2^32) `iters`
+ * times from x0 = 65536 r + t + 1; a CTA's result is the XOR of its threads'
+ * final values.  The oracle jumps ahead by composing the affine map with
+ * itself (O(log iters)), never running the loop.
+ *   lko_spin_xor(r, threads, iters) -> XOR over t < threads of x_iters(r, t)
+ *   lko_lcg_brute(x0, iters)        -> the plain loop, for pinning small cases */
+uint32_t lko_spin_xor(uint32_t rank, uint32_t threads, uint64_t iters);
+uint32_t lko_lcg_jump(uint32_t x0, uint64_t iters);
+uint32_t lko_lcg_brute(uint32_t x0, uint64_t iters);
+
 /* Violation codes reported by lko_check_exec_log. */
 enum {
   LKO_OK = 0,

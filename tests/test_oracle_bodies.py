@@ -126,3 +126,31 @@ def test_gemm_abs_bound(oracle_lib):
     want = np.abs(A[0].astype(np.float64))[:, :, None] * np.abs(B[0].astype(np.float64))[None, :, :]
     assert np.allclose(bound[0], want.sum(axis=1), rtol=1e-13, atol=0)
     assert np.all(bound >= np.abs(oracle_lib.gemm64_f32(A, B)))
+
+
+# ---- the compute-bound loop (Sec. III) ----------------------------------------------
+@pytest.mark.parametrize("x0", [0, 1, 12345, 2**31 + 7, 2**32 - 1])
+@pytest.mark.parametrize("iters", [0, 1, 2, 3, 17, 1000, 20000, 65537])
+def test_lcg_jump_ahead_equals_the_loop(oracle_lib, x0, iters):
+    assert oracle_lib.lcg_jump(x0, iters) == oracle_lib.lcg_brute(x0, iters)
+
+
+def test_lcg_matches_python_integers(oracle_lib):
+    x = 99
+    for _ in range(50):
+        x = (1664525 * x + 1013904223) % 2**32
+    assert oracle_lib.lcg_jump(99, 50) == x
+
+
+def test_lcg_full_period_of_the_map(oracle_lib):
+    # Hull-Dobell: c odd and a - 1 divisible by 4 give period 2^32, so the map
+    # returns to its start after 2^32 steps and not after 2^31
+    assert oracle_lib.lcg_jump(5, 2**32) == 5
+    assert oracle_lib.lcg_jump(5, 2**31) != 5
+
+
+def test_spin_xor_is_xor_of_threads(oracle_lib):
+    want = 0
+    for t in range(7):
+        want ^= oracle_lib.lcg_brute(65536 * 3 + t + 1, 100)
+    assert oracle_lib.spin_xor(3, 7, 100) == want
