@@ -315,6 +315,7 @@ def main():
     ap.add_argument("--iso-periods", type=int, default=2000, help="critical periods (1 ms each) per isolation run")
     ap.add_argument("--batches", type=int, default=8, help="batches of the batching stream to time")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of arrivals per serving rate")
+    ap.add_argument("--phase-runs", type=int, default=100, help="runs of the paper's life-cycle measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist = Dist()
@@ -562,6 +563,26 @@ def main():
     iso_res["parity"] = {"critical_sum_ok": bool(iso_sum_ok), "copy_tail_ok": iso_copy_ok}
     del copy_src, copy_dst
 
+    # ---- the paper's life cycle (Sec. III, Tables 2-3): Init/Trigger/Wait/Dispose ----
+    PAPER = {"single_sm": {"LK": (509e6, 239, 190e3, 30e6), "CUDA": (496e6, 3.9e3, 175e3, 274e3)},
+             "full_gpu": {"LK": (503e6, 210, 190e3, 30e6), "CUDA": (497e6, 3.8e3, 176e3, 247e3)},
+             "worst_single_sm": {"LK": (521e6, 1.1e3, 203e3, 33e6), "CUDA": (501e6, 7.7e3, 176e3, 893e3)}}
+    phases = {"iters": 20000, "runs": args.phase_runs, "unit": "us (host CLOCK_MONOTONIC)",
+              "paper_context": "GTX 980 + i7 at 3.6 GHz, host cycles / 3.6e3 = us; Tables 2-3", "configs": {}}
+    names = ("init", "trigger", "wait", "dispose")
+    for label, nsm in (("single_sm", 1), ("full_gpu", n_sms)):
+        t_lk = lk.lk_phase_run(sms=nsm, iters=20000, runs=args.phase_runs, device=dev)
+        t_cu = lk.lk_baseline_phase_run(sms=nsm, iters=20000, runs=args.phase_runs, device=dev)
+        entry = {}
+        for sysname, t in (("LK", t_lk), ("CUDA", t_cu)):
+            entry[sysname] = {nm: {"avg": float(np.mean(t[nm + "_ns"])) / 1e3, "worst": float(np.max(t[nm + "_ns"])) / 1e3,
+                                   "first": float(t[nm + "_ns"][0]) / 1e3}
+                              for nm in names}
+        entry["paper_avg_us"] = {k: [round(v / 3.6e3, 3) for v in vals] for k, vals in PAPER[label].items()}
+        if label == "single_sm":
+            entry["paper_worst_us"] = {k: [round(v / 3.6e3, 3) for v in vals] for k, vals in PAPER["worst_single_sm"].items()}
+        phases["configs"][label] = entry
+
     # ---- body bandwidth (finite mode) and the roofline ------------------------------
     bw = body_bandwidth(pools, lk, n_sms)
     peaks, peak_src = measured_peaks()
@@ -619,6 +640,7 @@ def main():
         "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
                 "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy"},
+        "paper_phases": phases,
         "batching": batching,
         "serving": serving,
         "isolation": iso_res,

@@ -83,8 +83,12 @@ extern "C" {
 #define LK_OP_COMBINE_SUM  6 /* out[0] = binary64 sum of n float32 partials, one at the start of each */
                              /* 16-byte slot of in0 (fixed order)            */
 #define LK_OP_COMBINE_HIST 7 /* out[v] = sum over j < n of in0[256 j + v] (n int32 histograms) */
-#define LK_OP_COUNT      8
-#define LK_OP_BATCH      8 /* a batch posted by lk_submit_batch (one descriptor, many items) */
+#define LK_OP_SPIN       8 /* the compute-bound loop of Sec. III: every thread t of CTA r iterates */
+                           /* x <- 1664525 x + 1013904223 (mod 2^32) n times from 65536 r + t + 1; */
+                           /* no memory traffic; out (optional, uint32 per CTA) receives the XOR    */
+                           /* of the CTA's final values                                             */
+#define LK_OP_COUNT      9
+#define LK_OP_BATCH      9 /* a batch posted by lk_submit_batch (one descriptor, many items) */
 
 /* ---- device-side error reasons (lk_device_error) ---------------------- */
 #define LK_DERR_NONE     0
@@ -278,6 +282,28 @@ typedef struct {
  * needs more arena or budget than exists), or the first error. */
 int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
              lk_request_result* res);
+
+/* ---- the paper's life-cycle measurement (Sec. III, Tables 2-3) ---------- */
+typedef struct {
+  uint64_t init_ns;      /* LK: lk_init          | CUDA: cudaMalloc of the output  */
+  uint64_t trigger_ns;   /* LK: lk_submit        | CUDA: cudaLaunchKernel          */
+  uint64_t wait_ns;      /* LK: lk_wait          | CUDA: cudaStreamSynchronize     */
+  uint64_t dispose_ns;   /* LK: lk_dispose       | CUDA: cudaFree                  */
+} lk_phase_times;
+
+/* `runs` times: Init a context of one cluster of `sms` CTAs (`threads` each),
+ * Trigger one LK_OP_SPIN descriptor of `iters` iterations, Wait for it,
+ * Dispose; host CLOCK_MONOTONIC time of each phase into out[run].  out_dev
+ * (optional, device, `sms` uint32) receives the spin results of the last
+ * run.  Returns LK_OK or the first error. */
+int lk_phase_run(int device, int sms, int threads, uint64_t iters, int runs, void* out_dev, lk_phase_times* out);
+
+/* The traditional life cycle of the same work: Alloc (cudaMalloc of the
+ * output), Spawn (cudaLaunchKernel of the spin body, grid = sms CTAs of
+ * `threads`), Wait (cudaStreamSynchronize), Dispose (cudaFree), `runs`
+ * times.  out_dev as above. */
+int lk_baseline_phase_run(int device, int sms, int threads, uint64_t iters, int runs, void* out_dev,
+                          lk_phase_times* out);
 
 /* Refresh the idle lease without posting work.  LK_OK or LK_EINVAL. */
 int lk_heartbeat(lk_ctx* ctx);

@@ -354,6 +354,22 @@ __device__ __forceinline__ void combine_hist(const lk_slot& d, uint32_t* acc) {
   }
 }
 
+/* ---- the compute-bound loop (Sec. III) ----------------------------------- */
+__device__ __forceinline__ void body_spin(const lk_slot& d, int r, uint32_t* red) {
+  uint32_t x = 65536u * (uint32_t)r + threadIdx.x + 1u;
+#pragma unroll 1
+  for (uint64_t i = 0; i < d.n; ++i) x = 1664525u * x + 1013904223u;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x ^= __shfl_xor_sync(0xffffffffu, x, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0 && d.out) {
+    uint32_t v = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) v ^= red[w];
+    reinterpret_cast<uint32_t*>(d.out)[r] = v;
+  }
+}
+
 /* ---- combining chunk results (rank 0 of the cluster alone) ------------- */
 /* out[0] = binary64 sum of n float32 partials, one per 16-byte slot, added
  * lane-strided then by a fixed shuffle tree: the order depends only on n. */

@@ -257,6 +257,7 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
       break;
     case LK_OP_COMBINE_SUM: body_combine_sum(d, r); break;
     case LK_OP_COMBINE_HIST: body_combine_hist(d, r); break;
+    case LK_OP_SPIN: body_spin(d, r, reinterpret_cast<uint32_t*>(red)); break;
     case LK_OP_NOP: break;
     default: return LK_DERR_BADDESC;
   }
@@ -870,7 +871,7 @@ void pin_cpu(int cpu) {
 }
 cudaError_t launch_ordinary(const lk_slot& d, int grid, int threads, lk_scratch* sc, cudaStream_t s) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  const size_t smem = op == LK_OP_NOP ? 0 : lk::body_smem_bytes(threads);
+  const size_t smem = (op == LK_OP_NOP || op == LK_OP_SPIN) ? 0 : lk::body_smem_bytes(threads);
   if (threads <= 256) lk_ordinary<256><<<grid, threads, smem, s>>>(d, sc);
   else if (threads <= 512) lk_ordinary<512><<<grid, threads, smem, s>>>(d, sc);
   else lk_ordinary<1024><<<grid, threads, smem, s>>>(d, sc);
@@ -972,13 +973,48 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
   return rc;
 }
 
+/* ---- the traditional life cycle of the compute-bound loop (Sec. III) ------ */
+extern "C" int lk_baseline_phase_run(int device, int sms, int threads, uint64_t iters, int runs, void* out_dev,
+                                     lk_phase_times* out) {
+  if (sms < 1 || sms > LK_MAX_CTAS || runs < 1 || !out || threads < 64 || threads > 1024 || threads % 32 ||
+      iters > 0xffffffffull)
+    return LK_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  preload_all();
+  if (g_preload_err != cudaSuccess) return LK_EDEVICE;
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return LK_EDEVICE;
+  int rc = LK_OK;
+  for (int r = 0; r < runs && rc == LK_OK; ++r) {
+    void* buf = nullptr;
+    const uint64_t t0 = now_ns();
+    if (cudaMalloc(&buf, (size_t)sms * sizeof(uint32_t)) != cudaSuccess) { rc = LK_ENOMEM; break; }
+    const uint64_t t1 = now_ns();
+    lk_slot d;
+    memset(&d, 0, sizeof d);
+    d.cmd = LK_CMD_WORK + LK_OP_SPIN;
+    d.n = iters;
+    d.out = (uint64_t)(uintptr_t)(r == runs - 1 && out_dev ? out_dev : buf);
+    cudaError_t e = launch_ordinary(d, sms, threads, nullptr, s);
+    const uint64_t t2 = now_ns();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const uint64_t t3 = now_ns();
+    if (cudaFree(buf) != cudaSuccess && e == cudaSuccess) e = cudaErrorUnknown;
+    const uint64_t t4 = now_ns();
+    if (e != cudaSuccess) rc = LK_EDEVICE;
+    out[r] = lk_phase_times{t1 - t0, t2 - t1, t3 - t2, t4 - t3};
+  }
+  cudaStreamDestroy(s);
+  return rc;
+}
+
 /* ---- a batch as one CUDA graph of ordinary launches ---------------------- */
 extern "C" int lk_baseline_graph(int device, const lk_batch_item* items, uint32_t count, int max_ctas, int threads,
                                  int reps, float* ms) {
   if ((count > 0 && !items) || max_ctas < 1 || max_ctas > LK_MAX_CTAS || threads < 64 || threads > 1024 ||
       threads % 32 || reps < 1 || !ms)
     return LK_EINVAL;
-  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1};
+  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1, 0};
   for (uint32_t i = 0; i < count; ++i) {
     const lk_batch_item& it = items[i];
     if (it.op >= LK_OP_COUNT) return LK_EINVAL;
@@ -1055,7 +1091,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 extern "C" int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
                                  int ctas, int threads, void* stream) {
   if (!d || d->flags != 0 || device < 0 || device >= 256) return LK_EINVAL;
-  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1};
+  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1, 0};
   if (d->op >= LK_OP_COUNT || n_in != need[d->op] || (n_in > 0 && !in)) return LK_EINVAL;
   if (ctas < 1 || ctas > LK_MAX_CTAS) return LK_EINVAL;   /* beyond the static scratch */
   if (threads < 64 || threads > 1024 || threads % 32) return LK_EINVAL;

@@ -112,6 +112,7 @@ static int op_inputs(uint32_t op) {
     case LK_OP_COPY_I32: return 1;
     case LK_OP_COMBINE_SUM: return 1;
     case LK_OP_COMBINE_HIST: return 1;
+    case LK_OP_SPIN: return 0;
     default: return -1;
   }
 }
@@ -147,6 +148,9 @@ static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in
     case LK_OP_COMBINE_SUM:
     case LK_OP_COMBINE_HIST:
       if (!out || d->n > (1ull << 20)) return LK_EINVAL;
+      break;
+    case LK_OP_SPIN:
+      if (d->n > 0xffffffffull) return LK_EINVAL;   /* out is optional */
       break;
     default:
       if (d->n > 0 && !out) return LK_EINVAL;
@@ -578,6 +582,37 @@ int lk_submit_batch(lk_ctx* ctx, int cluster, const lk_batch_item* items, uint32
   bs.seq_of[b] = seq;
   bs.next++;
   *h = ((uint64_t)cluster << 48) | seq;
+  return LK_OK;
+}
+
+int lk_phase_run(int device, int sms, int threads, uint64_t iters, int runs, void* out_dev, lk_phase_times* out) {
+  if (sms < 1 || runs < 1 || !out || iters > 0xffffffffull) return LK_EINVAL;
+  for (int r = 0; r < runs; ++r) {
+    lk_init_params p;
+    memset(&p, 0, sizeof p);
+    p.device = device;
+    p.num_clusters = 1;
+    p.sms_per_cluster = &sms;
+    p.threads_per_cta = threads;
+    p.ring_depth = 64;
+    p.max_batch_units = 16;
+    lk_ctx* ctx = nullptr;
+    const uint64_t t0 = now_ns();
+    int rc = lk_init(&ctx, &p);
+    const uint64_t t1 = now_ns();
+    if (rc != LK_OK) return rc;
+    lk_desc d{LK_OP_SPIN, 0, iters, 0};
+    lk_handle h = 0;
+    rc = lk_submit(ctx, 0, &d, nullptr, 0, r == runs - 1 ? out_dev : nullptr, &h);
+    const uint64_t t2 = now_ns();
+    if (rc == LK_OK) rc = lk_wait(ctx, h, 60000000000ull);
+    const uint64_t t3 = now_ns();
+    int rd = lk_dispose(ctx, 30000000000ull);
+    const uint64_t t4 = now_ns();
+    if (rc != LK_OK) return rc;
+    if (rd != LK_OK) return rd;
+    out[r] = lk_phase_times{t1 - t0, t2 - t1, t3 - t2, t4 - t3};
+  }
   return LK_OK;
 }
 

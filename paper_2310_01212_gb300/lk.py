@@ -28,10 +28,11 @@ LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
 LK_INIT_DIRECT = 1
 LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
 LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7
-LK_OP_BATCH = 8
+LK_OP_SPIN = 8
+LK_OP_BATCH = 9
 LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING = range(7)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
-             LK_OP_COPY_I32: 1, 6: 1, 7: 1}
+             LK_OP_COPY_I32: 1, 6: 1, 7: 1, 8: 0}
 OP_NAMES = {LK_OP_NOP: "nop", LK_OP_ADD_I32: "add_i32", LK_OP_HIST_U8: "hist_u8", LK_OP_SUM_F32: "sum_f32",
             LK_OP_GEMM64_F32: "gemm64_f32", LK_OP_COPY_I32: "copy_i32"}
 
@@ -138,6 +139,8 @@ def load(fake: bool = False) -> ctypes.CDLL:
             "lk_launch_noalloc": (I, [I, ctypes.POINTER(lk_desc), ctypes.POINTER(P), I, P, I, I, P]),
             "lk_submit_batch": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(lk_batch_tune), ctypes.POINTER(U64)]),
             "lk_serve": (I, [P, P, SZ, ctypes.POINTER(lk_serve_params), P]),
+            "lk_phase_run": (I, [I, I, I, U64, I, P, P]),
+            "lk_baseline_phase_run": (I, [I, I, I, U64, I, P, P]),
             "lk_baseline_graph": (I, [I, P, ctypes.c_uint32, I, I, I, ctypes.POINTER(ctypes.c_float)]),
         }
         for name, (res, args) in sig.items():
@@ -421,3 +424,26 @@ def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int
     rc = ctx.lib.lk_serve(ctx.ptr, reqs.ctypes.data if reqs.size else None, reqs.size, ctypes.byref(prm),
                           res.ctypes.data if reqs.size else None)
     return rc, res
+
+
+PHASE_DTYPE = np.dtype([("init_ns", "<u8"), ("trigger_ns", "<u8"), ("wait_ns", "<u8"), ("dispose_ns", "<u8")])
+
+
+def lk_phase_run(sms: int, iters: int, runs: int, threads: int = 256, out=None, device: int = 0, fake: bool = False):
+    """The paper's life cycle on LK (Init/Trigger/Wait/Dispose per run)."""
+    lib = load(fake)
+    res = np.zeros(runs, dtype=PHASE_DTYPE)
+    rc = lib.lk_phase_run(device, sms, threads, iters, runs, _ptr(out) or None, res.ctypes.data)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_phase_run")
+    return res
+
+
+def lk_baseline_phase_run(sms: int, iters: int, runs: int, threads: int = 256, out=None, device: int = 0):
+    """The traditional life cycle (Alloc/Spawn/Wait/Dispose per run)."""
+    lib = load()
+    res = np.zeros(runs, dtype=PHASE_DTYPE)
+    rc = lib.lk_baseline_phase_run(device, sms, threads, iters, runs, _ptr(out) or None, res.ctypes.data)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_baseline_phase_run")
+    return res

@@ -381,3 +381,10 @@ def test_serve_needs_equal_clusters(fake_env):
         rc, _ = lk.lk_serve(c, _reqs(1, [lk.LK_OP_NOP + 1], [16]), n_producers=4, budget_bytes=1 << 30,
                             arena=1 << 20, arena_bytes=1 << 30)
         assert rc == lk.LK_EINVAL
+
+
+def test_phase_run_on_fake(fake_env):
+    res = lk.lk_phase_run(sms=2, iters=100, runs=5, fake=True)
+    assert res.size == 5
+    for f in ("init_ns", "trigger_ns", "wait_ns", "dispose_ns"):
+        assert np.all(res[f] > 0)
