@@ -363,6 +363,7 @@ def main():
         if rc != lk.LK_OK:
             raise RuntimeError(f"trace failed: {lk.lk_strerror(rc)}")
         if last:
+            last_res = res
             log, dropped = lk.lk_exec_log(ctx)
             ops = traces[s][1]["op"]
             n_posted = [int(np.sum(np.arange(items_per_step) % 4 == c)) for c in range(4)]
@@ -421,11 +422,39 @@ def main():
         rc, r1 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT) as ctx:
         rc, r3 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
+    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_MAILBOX) as ctx:
+        rc, r4 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True)
     rc2, r2 = lk.lk_baseline_run_trace(nop, sizes, threads=cfg["threads"], n_threads=1, device=dev)
     skip = nop.size // 20   # first items warm the path
     nop_lk = (r1["t_complete_ns"] - r1["t_submit_ns"])[skip:] / 1000.0
     nop_direct = (r3["t_complete_ns"] - r3["t_submit_ns"])[skip:] / 1000.0
+    nop_mbox = (r4["t_complete_ns"] - r4["t_submit_ns"])[skip:] / 1000.0
     nop_base = (r2["t_complete_ns"] - r2["t_submit_ns"])[skip:] / 1000.0
+
+    # ---- the paper's one-deep mailbox against the ring (Sec. II.D, Table 1) ---------
+    # one SM (the paper's cluster), closed-loop NOPs; then the last timed step's
+    # mixed trace (open loop, Poisson arrivals) through one-deep mailboxes
+    mbox = {}
+    nop1 = nop[: nop.size // 2].copy()
+    nop1["cluster"] = 0
+    for key, fl in (("ring_1sm", 0), ("mailbox_1sm", lk.LK_INIT_MAILBOX)):
+        with lk.lk_init([1], device=dev, idle_lease_ns=5_000_000_000, flags=fl) as ctx:
+            rc, r = lk.lk_run_trace(ctx, nop1, n_threads=1, closed_loop=True)
+        if rc != lk.LK_OK:
+            raise RuntimeError(f"1-SM NOP trace failed: {lk.lk_strerror(rc)}")
+        mbox[key + "_nop_us"] = lat_summary((r["t_complete_ns"] - r["t_submit_ns"])[skip // 2:] / 1000.0)
+    last_trace = traces[-1][0]
+    with lk.lk_init(sizes, device=dev, threads_per_cta=cfg["threads"], idle_lease_ns=5_000_000_000,
+                    flags=lk.LK_INIT_MAILBOX) as ctx:
+        rc, r = lk.lk_run_trace(ctx, last_trace, n_threads=len(sizes))
+    if rc != lk.LK_OK:
+        raise RuntimeError(f"mailbox trace failed: {lk.lk_strerror(rc)}")
+    mbox["mixed_trace_mailbox"] = {
+        "submit_to_complete_us": lat_summary((r["t_complete_ns"] - r["t_submit_ns"]) / 1000.0),
+        "arrival_to_complete_us": lat_summary((r["t_complete_ns"] - last_trace["t_arrival_ns"]) / 1000.0)}
+    mbox["mixed_trace_ring_last_step"] = {
+        "submit_to_complete_us": lat_summary((last_res["t_complete_ns"] - last_res["t_submit_ns"]) / 1000.0),
+        "arrival_to_complete_us": lat_summary((last_res["t_complete_ns"] - last_trace["t_arrival_ns"]) / 1000.0)}
 
     # ---- end to end: host buffers, copies inside the timed path ---------------------
     lim = 256 << 20
@@ -629,7 +658,8 @@ def main():
         "max_us": mx,
         "baseline_launch_sync_us": lat_summary(base),
         "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
-                            "launch_sync": lat_summary(nop_base)},
+                            "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base)},
+        "paper_mailbox_vs_ring": mbox,
         "pingpong_floor_us": lat_summary(rtt),
         "throughput_items_per_s": items_all / wall_all,
         "wall_ms_per_step": 1000.0 * wall_all / args.steps,

@@ -136,6 +136,18 @@ typedef struct {
  * relay hop, but every extra reader of the ring's cache line delays the
  * host's stores to it). */
 #define LK_INIT_DIRECT 1u
+/* LK_INIT_MAILBOX: the paper's own one-deep mailbox pair per cluster
+ * (Sec. II.D, Table 1) instead of the ring.  The host writes the descriptor's
+ * words, then release-stores to_GPU = THREAD_WORK + op; the master answers
+ * from_GPU = THREAD_WORKING, relays the descriptor to the other CTAs and, once
+ * all have finished, writes THREAD_FINISHED.  The host that observes FINISHED
+ * (in lk_poll, lk_wait, lk_sync or a later lk_submit) re-arms with
+ * to_GPU = THREAD_NOP, and the master acknowledges with from_GPU = THREAD_NOP;
+ * only then does the mailbox take the next descriptor.  So at most one
+ * descriptor per cluster is in flight, and lk_submit returns LK_EAGAIN until
+ * the previous one has finished and its re-arm was acknowledged.  Cannot be
+ * combined with LK_INIT_DIRECT (LK_EINVAL). */
+#define LK_INIT_MAILBOX 2u
 
 /* A work descriptor.  The in/out pointers travel beside it. */
 typedef struct {
@@ -176,7 +188,8 @@ int lk_init(lk_ctx** out, const lk_init_params* p);
  *   the descriptor reaches the device through the mailbox ring only.
  * On success *h names the descriptor.
  * Errors: LK_EINVAL (cluster, op, n_in, alignment, n too large),
- * LK_EAGAIN (ring full: nothing was posted), LK_ESTATE (context not running). */
+ * LK_EAGAIN (ring full, or with LK_INIT_MAILBOX the mailbox not idle yet:
+ * nothing was posted), LK_ESTATE (context not running). */
 int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in, int n_in,
               void* out, lk_handle* h);
 
@@ -330,7 +343,9 @@ int lk_cluster_info(lk_ctx* ctx, int cluster, int* smids, int cap);
 /* from_GPU status of `cluster` (Table 1): LK_ST_INIT after boot until the
  * first post, LK_ST_WORKING while posted descriptors are unfinished,
  * LK_ST_FINISHED once all of them finished, LK_ST_EXITED / LK_ST_ERROR after
- * the cluster's CTAs returned.  LK_EINVAL for a bad cluster. */
+ * the cluster's CTAs returned.  With LK_INIT_MAILBOX the word the master
+ * writes is returned as it is, LK_ST_NOP (re-arm acknowledged) included.
+ * LK_EINVAL for a bad cluster. */
 int lk_status(lk_ctx* ctx, int cluster);
 
 /* First device-side error reason (LK_DERR_*), or LK_EINVAL. */

@@ -4,7 +4,8 @@
  *
  * It plays the device's side of the mailbox protocol over the same memory
  * layout as the persistent kernel: per cluster, one thread acquires ring
- * slots in FIFO order, reports WORKING / FINISHED in the from_GPU words,
+ * slots in FIFO order (or, with LK_INIT_MAILBOX, runs the one-deep four-phase
+ * mailbox handshake), reports WORKING / FINISHED in the from_GPU words,
  * release-stores `done`, writes execution-log records for every rank, honours
  * EXIT, the abort word and the idle lease.  Work bodies are not run: this
  * backend exists to test the host runtime (tickets, ring-full refusals,
@@ -115,35 +116,59 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
   const uint64_t drop_after = env_u64("LK_FAKE_DROP_AFTER", ~0ull);
   const uint64_t fail_after = env_u64("LK_FAKE_FAIL_AFTER", ~0ull);
   const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
+  const bool mailbox = (a.flags & LK_KFLAG_MAILBOX) != 0;
+  uint64_t finished = 0;
   int err = 0;
-  for (uint64_t k = 0;; ++k) {
-    const lk_wire* s = ring + (k & a.ring_mask);
-    const uint64_t tag = lk_lap_tag(k, a.ring_log2);
+  /* bounded wait for `ready` (abort, idle lease), as the kernel's waits */
+  auto wait_for = [&](auto ready) {
     uint64_t hb = ld_acq(&a.ctrl->heartbeat);
     uint64_t t_last = now_ns();
-    uint64_t w[6];
-    auto current = [&]() {
-      for (int i = 0; i < 6; ++i) w[i] = __atomic_load_n(&s->w[i], __ATOMIC_RELAXED);
-      for (int i = 0; i < 6; ++i)
-        if ((w[i] >> LK_TAG_SHIFT) != tag) return false;
-      __atomic_thread_fence(__ATOMIC_ACQUIRE);
-      return true;
-    };
-    while (!current()) {
-      if (ld_acq(&a.ctrl->abort)) { err = LK_DERR_ABORT; break; }
+    while (!ready()) {
+      if (ld_acq(&a.ctrl->abort)) return (int)LK_DERR_ABORT;
       uint64_t t = now_ns();
       if (t - t_last > a.lease_ns) {
         uint64_t h = ld_acq(&a.ctrl->heartbeat);
-        if (h == hb) { err = LK_DERR_LEASE; break; }
+        if (h == hb) return (int)LK_DERR_LEASE;
         hb = h;
         t_last = t;
       }
       std::this_thread::yield();
     }
-    if (err) break;
-    lk_slot dsc;
-    lk_wire_decode(w, k + 1, &dsc);
-    const uint32_t cmd = dsc.cmd;
+    return 0;
+  };
+  for (uint64_t k = 0;; ++k) {
+    uint32_t cmd = 0;
+    if (mailbox) {
+      /* the one-deep mailbox: acknowledge the host's re-arm, then take work */
+      lk_mbox* mb = a.mbox + c;
+      if (k > 0) {
+        err = wait_for([&] { return ld_acq(&mb->to_gpu) == (uint64_t)LK_CMD_NOP; });
+        if (err) break;
+        st_rel(&a.cword[c].status, (uint64_t)LK_ST_NOP);
+      }
+      uint64_t v = 0;
+      err = wait_for([&] {
+        v = ld_acq(&mb->to_gpu);
+        return v == (uint64_t)LK_CMD_EXIT || v >= (uint64_t)LK_CMD_WORK;
+      });
+      if (err) break;
+      cmd = (uint32_t)v;
+    } else {
+      const lk_wire* s = ring + (k & a.ring_mask);
+      const uint64_t tag = lk_lap_tag(k, a.ring_log2);
+      uint64_t w[6];
+      err = wait_for([&] {
+        for (int i = 0; i < 6; ++i) w[i] = __atomic_load_n(&s->w[i], __ATOMIC_RELAXED);
+        for (int i = 0; i < 6; ++i)
+          if ((w[i] >> LK_TAG_SHIFT) != tag) return false;
+        __atomic_thread_fence(__ATOMIC_ACQUIRE);
+        return true;
+      });
+      if (err) break;
+      lk_slot dsc;
+      lk_wire_decode(w, k + 1, &dsc);
+      cmd = dsc.cmd;
+    }
     if (cmd == LK_CMD_EXIT) break;
     if (k >= fail_after) { err = LK_DERR_BADDESC; break; }
     const uint64_t t_pick = now_ns();
@@ -168,10 +193,12 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       }
     }
     if (k < drop_after) {
-      st_rel(&a.cword[c].done, k + 1);
+      finished = k + 1;
+      if (!mailbox) st_rel(&a.cword[c].done, k + 1);
       st_rel(&a.cword[c].status, (uint64_t)LK_ST_FINISHED);
     }
   }
+  if (mailbox) st_rel(&a.cword[c].done, finished);
   if (err) set_error(a, c, (uint32_t)err);
   st_rel(&a.cword[c].status, (uint64_t)(err ? LK_ST_ERROR : LK_ST_EXITED));
   __atomic_fetch_add(&a.ctrl->exited, (uint32_t)ctas.size(), __ATOMIC_ACQ_REL);

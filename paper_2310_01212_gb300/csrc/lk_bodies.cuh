@@ -357,8 +357,17 @@ __device__ __forceinline__ void combine_hist(const lk_slot& d, uint32_t* acc) {
 /* ---- the compute-bound loop (Sec. III) ----------------------------------- */
 __device__ __forceinline__ void body_spin(const lk_slot& d, int r, uint32_t* red) {
   uint32_t x = 65536u * (uint32_t)r + threadIdx.x + 1u;
+  /* eight dependent steps per trip: a one-step trip spends most of its time
+   * on the 64-bit counter and the back edge, not on the multiply-add chain */
+  const uint64_t n = d.n;
+  uint64_t i = 0;
 #pragma unroll 1
-  for (uint64_t i = 0; i < d.n; ++i) x = 1664525u * x + 1013904223u;
+  for (; i + 8 <= n; i += 8) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x = 1664525u * x + 1013904223u;
+  }
+#pragma unroll 1
+  for (; i < n; ++i) x = 1664525u * x + 1013904223u;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) x ^= __shfl_xor_sync(0xffffffffu, x, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;

@@ -102,6 +102,72 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, 
   return 0;
 }
 
+/* One-deep mailbox (LK_INIT_MAILBOX, Sec. II.D, Table 1), master thread
+ * only.  Descriptor k+1 is taken in up to two steps:
+ *   1. (k > 0) the re-arm of the four-phase handshake: wait for
+ *      to_GPU = THREAD_NOP, which the host writes once it saw
+ *      THREAD_FINISHED for descriptor k, and acknowledge with
+ *      from_GPU = THREAD_NOP;
+ *   2. wait for to_GPU = THREAD_EXIT or THREAD_WORK + op; after the acquire
+ *      fence, read the descriptor's words (a second round trip over the host
+ *      link: the ring's lap tags exist to save it) and answer
+ *      from_GPU = THREAD_WORKING.
+ * Both waits are bounded like take_from_ring's.  Returns 0 or LK_DERR_*. */
+__device__ __noinline__ int wait_to_gpu(const lk_kargs& a, const uint64_t* p, bool want_nop, uint64_t* v_out) {
+  Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
+  uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+  uint64_t t_last = gtime();
+  uint64_t v;
+  for (uint32_t it = 1;; ++it) {
+    v = ld_relaxed_sys(p);
+    if (want_nop ? v == LK_CMD_NOP : (v == LK_CMD_EXIT || v >= LK_CMD_WORK)) break;
+    if ((it & 63) == 0) {
+      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+      const uint64_t now = gtime();
+      if (now - t_last > a.lease_ns) {
+        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+        if (h == hb) return LK_DERR_LEASE;
+        hb = h;
+        t_last = now;
+      }
+    }
+    bo.pause();
+  }
+  fence_acq_rel_sys();
+  *v_out = v;
+  return 0;
+}
+
+__device__ __noinline__ int take_from_mailbox(const lk_kargs& a, int c, uint64_t k, lk_slot& out) {
+  lk_mbox* mb = a.mbox + c;
+  uint64_t v = 0;
+  if (k > 0) {
+    const int err = wait_to_gpu(a, &mb->to_gpu, true, &v);
+    if (err) return err;
+    st_relaxed_sys(&a.cword[c].status, LK_ST_NOP);
+  }
+  const int err = wait_to_gpu(a, &mb->to_gpu, false, &v);
+  if (err) return err;
+  uint64_t w[6] = {0, 0, 0, 0, 0, 0};
+  if (v != LK_CMD_EXIT) {
+    ld_relaxed_sys_v2(&mb->n, w[0], w[1]);
+    ld_relaxed_sys_v2(&mb->in1, w[2], w[3]);
+    ld_relaxed_sys_v2(&mb->aux, w[4], w[5]);
+  }
+  out.seq = k + 1;
+  out.cmd = (uint32_t)v;
+  out.flags = (uint32_t)w[5];
+  out.n = w[0];
+  out.in0 = w[1];
+  out.in1 = w[2];
+  out.out = w[3];
+  out.aux = w[4];
+  out.t_pick = 0;
+  if (v == LK_CMD_EXIT) return 0;
+  st_relaxed_sys(&a.cword[c].status, LK_ST_WORKING);
+  return 0;
+}
+
 /* Relay (LK_INIT_RELAY): the master copies descriptor k into relay slot
  * k mod D as six lap-tagged words (the host ring's format, tag = relay lap),
  * after the acquire-release fence that followed its ring probe, so members
@@ -426,6 +492,7 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
   const int c = s_cl, r = s_rank, S = s_size;
   const bool master = (r == 0);
   const bool relay = (a.flags & LK_KFLAG_DIRECT) == 0;
+  const bool mailbox = (a.flags & LK_KFLAG_MAILBOX) != 0;   /* implies relay */
   lk_dcluster* dc = a.dcl + c;
   const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
   uint32_t phase = 0;
@@ -440,7 +507,10 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
       lk_slot dsc;
       const lk_wire* w = ring + (k & a.ring_mask);
       const uint64_t tag = lk_lap_tag(k, a.ring_log2);
-      if (!relay || master) {
+      if (master && mailbox) {
+        err = take_from_mailbox(a, c, k, dsc);
+        if (!err) dsc.t_pick = gtime();
+      } else if (!relay || master) {
         err = take_from_ring(a, w, tag, k + 1, dsc);
         if (!err) dsc.t_pick = gtime();
       } else {
@@ -512,7 +582,8 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
           fence_acq_rel_sys();
           asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&dc->dev_done), "l"(k + 1) : "memory");
           known_done = k + 1;
-          st_relaxed_sys(&a.cword[c].done, d.seq);
+          if (mailbox) st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);   /* the host re-arms */
+          else st_relaxed_sys(&a.cword[c].done, d.seq);
           t_done = gtime();
         }
       }
@@ -542,6 +613,12 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     }
   }
   if (tid == 0) {
+    if (master && mailbox) {
+      /* completions the host has not consumed through FINISHED yet stay
+       * visible after the status word below overwrites it */
+      st_relaxed_sys(&a.cword[c].done, known_done);
+      fence_acq_rel_sys();
+    }
     if (master) st_relaxed_sys(&a.cword[c].status, final_err ? LK_ST_ERROR : LK_ST_EXITED);
     red_release_sys_add(&a.ctrl->exited, 1u);
   }

@@ -89,6 +89,20 @@ typedef struct __attribute__((aligned(LK_LINE))) {
   uint8_t pad1[LK_LINE - 16];
 } lk_cword;
 
+/* The paper's one-deep to_GPU mailbox of a cluster (LK_INIT_MAILBOX).  The
+ * host writes the descriptor's words, then release-stores `to_gpu`
+ * (THREAD_NOP, THREAD_EXIT or THREAD_WORK + op, Table 1); the master acquires
+ * `to_gpu` and only then reads the words.  The from_GPU side is the
+ * cluster's `status` word (lk_cword). */
+typedef struct __attribute__((aligned(LK_LINE))) {
+  uint64_t n, in0;        /* word pairs on 16-byte boundaries: one vector load each */
+  uint64_t in1, out;
+  uint64_t aux, flags;
+  uint64_t seq;           /* host's count of posts (diagnostic; the device counts its own) */
+  uint64_t to_gpu;
+  uint8_t pad[LK_LINE - 64];
+} lk_mbox;
+
 typedef struct __attribute__((aligned(LK_LINE))) {
   uint64_t abort;                /* host writes non-zero: every device wait returns     */
   uint8_t pad0[LK_LINE - 8];
@@ -158,10 +172,12 @@ typedef struct __attribute__((aligned(LK_LINE))) {
 
 /* Everything the persistent kernel needs; passed by value at launch. */
 #define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
+#define LK_KFLAG_MAILBOX 2u      /* the master takes work from lk_mbox, not the ring   */
 
 typedef struct {
   lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */
   lk_cword* cword;               /* [C] host-mapped                                     */
+  lk_mbox* mbox;                 /* [C] host-mapped (LK_KFLAG_MAILBOX), else NULL       */
   lk_ctrl* ctrl;                 /* host-mapped                                         */
   lk_cta_info* info;             /* [G] host-mapped                                     */
   lk_dcluster* dcl;              /* [C] device                                          */

@@ -76,6 +76,11 @@ struct lk_ctx {
 
   Tail* tail = nullptr;          /* [C], host-only tickets */
 
+  /* one-deep mailbox mode (LK_INIT_MAILBOX) */
+  bool mailbox = false;
+  lk_mbox* mbox_h = nullptr;     /* [C] host-mapped to_GPU mailboxes */
+  Tail* rearmed = nullptr;       /* [C] descriptors whose FINISHED the host consumed */
+
   /* batches: per cluster LK_BATCH_BUFFERS unit tables in host-mapped memory */
   uint32_t max_units = 0;
   lk_unit* units_h = nullptr;    /* [C][LK_BATCH_BUFFERS][max_units] */
@@ -186,9 +191,61 @@ static bool ctx_alive(lk_ctx* ctx) {
   return true;
 }
 
+/* One-deep mailbox (LK_INIT_MAILBOX): the host half of the four-phase
+ * handshake (Sec. II.D, Table 1).  If the cluster's from_GPU word reads
+ * THREAD_FINISHED for the newest post, consume that completion once (a CAS
+ * on `rearmed`): publish it in the host-side `done` word that every wait
+ * path reads, then re-arm with to_GPU = THREAD_NOP.  FINISHED can only mean
+ * the newest post: the next post waits for the master's NOP acknowledgement
+ * of this re-arm. */
+static void mbox_observe(lk_ctx* ctx, int c) {
+  const uint64_t t = ctx->tail[c].t.load(std::memory_order_acquire);
+  uint64_t r = ctx->rearmed[c].t.load(std::memory_order_acquire);
+  if (r >= t) return;
+  if (ld_acq(&ctx->cword_h[c].status) != LK_ST_FINISHED) return;
+  if (!ctx->rearmed[c].t.compare_exchange_strong(r, t, std::memory_order_acq_rel)) return;
+  st_rel(&ctx->cword_h[c].done, t);
+  st_rel(&ctx->mbox_h[c].to_gpu, (uint64_t)LK_CMD_NOP);
+}
+
+/* Finished descriptors of cluster c (FIFO: every seq <= the value). */
+static uint64_t cl_done(lk_ctx* ctx, int c) {
+  if (ctx->mailbox) mbox_observe(ctx, c);
+  return ld_acq(&ctx->cword_h[c].done);
+}
+
+/* Mailbox post: only when the previous descriptor finished, was re-armed and
+ * the master acknowledged the re-arm (from_GPU = THREAD_NOP); the CAS on the
+ * tail makes one of several racing producers the owner.  The descriptor's
+ * words are stored first; the release store of to_GPU publishes them. */
+static int post_mailbox(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
+                        void* out, uint64_t* seq_out) {
+  Tail& tl = ctx->tail[c];
+  uint64_t t = tl.t.load(std::memory_order_acquire);
+  for (;;) {
+    if (t > 0) {
+      if (cl_done(ctx, c) < t) return LK_EAGAIN;
+      if (ld_acq(&ctx->cword_h[c].status) != LK_ST_NOP) return LK_EAGAIN;
+    }
+    if (tl.t.compare_exchange_weak(t, t + 1, std::memory_order_acq_rel, std::memory_order_acquire)) break;
+  }
+  lk_mbox* mb = &ctx->mbox_h[c];
+  st_rlx(&mb->n, d ? d->n : 0);
+  st_rlx(&mb->in0, (uint64_t)(uintptr_t)in0);
+  st_rlx(&mb->in1, (uint64_t)(uintptr_t)in1);
+  st_rlx(&mb->out, (uint64_t)(uintptr_t)out);
+  st_rlx(&mb->aux, d ? d->aux : 0);
+  st_rlx(&mb->flags, (uint64_t)(d ? d->flags : 0));
+  st_rlx(&mb->seq, t + 1);
+  st_rel(&mb->to_gpu, (uint64_t)cmd);
+  *seq_out = t + 1;
+  return LK_OK;
+}
+
 /* Ticket + publish.  Returns LK_OK / LK_EAGAIN. */
 static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
                 void* out, uint64_t* seq_out) {
+  if (ctx->mailbox) return post_mailbox(ctx, c, cmd, d, in0, in1, out, seq_out);
   Tail& tl = ctx->tail[c];
   uint64_t t = tl.t.load(std::memory_order_relaxed);
   for (;;) {
@@ -240,7 +297,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   ctx->R_log2 = 0;
   while ((1u << ctx->R_log2) < R) ctx->R_log2++;
   ctx->log_cap = p->exec_log_cap;
-  if (p->flags & ~(uint32_t)LK_INIT_DIRECT) return LK_EINVAL;
+  if (p->flags & ~(uint32_t)(LK_INIT_DIRECT | LK_INIT_MAILBOX)) return LK_EINVAL;
+  if ((p->flags & LK_INIT_DIRECT) && (p->flags & LK_INIT_MAILBOX)) return LK_EINVAL;
+  ctx->mailbox = live && (p->flags & LK_INIT_MAILBOX);
 
   /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] [unit tables (live only)] */
   ctx->max_units = live ? (p->max_batch_units ? p->max_batch_units : 8192u) : 0u;
@@ -252,7 +311,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   size_t off_info = align_up(off_ctrl + sizeof(lk_ctrl), LK_LINE);
   size_t off_units = align_up(off_info + ctx->G * sizeof(lk_cta_info), LK_LINE);
   size_t units_bytes = (size_t)ctx->C * LK_BATCH_BUFFERS * ctx->max_units * sizeof(lk_unit);
-  size_t mapped_bytes = align_up(off_units + units_bytes, 4096);
+  size_t off_mbox = align_up(off_units + units_bytes, LK_LINE);
+  size_t mbox_bytes = ctx->mailbox ? ctx->C * sizeof(lk_mbox) : 0;
+  size_t mapped_bytes = align_up(off_mbox + mbox_bytes, 4096);
   rc = lkb_alloc_mapped(ctx->device, mapped_bytes, &ctx->mapped_h, &ctx->mapped_d);
   if (rc != LK_OK) return rc;
   char* mh = (char*)ctx->mapped_h;
@@ -263,6 +324,10 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if (ctx->max_units) {
     ctx->units_h = (lk_unit*)(mh + off_units);
     ctx->units_d = (lk_unit*)(md + off_units);
+  }
+  if (ctx->mailbox) {
+    ctx->mbox_h = (lk_mbox*)(mh + off_mbox);
+    for (int c = 0; c < ctx->C; ++c) ctx->mbox_h[c].to_gpu = LK_CMD_NOP;   /* idle */
   }
 
   /* device block: [ring (finite only)] dcl[C] cl_start pin_smid boot_smid boot_count log_count log */
@@ -292,6 +357,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   memset(&a, 0, sizeof a);
   a.ring = (lk_wire*)(live ? (void*)(md + off_ring) : (void*)(db + d_ring));
   a.cword = (lk_cword*)(md + off_cw);
+  a.mbox = ctx->mailbox ? (lk_mbox*)(md + off_mbox) : nullptr;
   a.ctrl = (lk_ctrl*)(md + off_ctrl);
   a.info = (lk_cta_info*)(md + off_info);
   a.dcl = (lk_dcluster*)(db + d_dcl);
@@ -309,7 +375,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.ring_mask = R - 1;
   a.ring_log2 = ctx->R_log2;
   a.log_cap = ctx->log_cap;
-  a.flags = (p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u;
+  a.flags = ((p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u) | (ctx->mailbox ? LK_KFLAG_MAILBOX : 0u);
   a.backoff_base_ns = p->backoff_base_ns;
   a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;
   a.lease_ns = p->idle_lease_ns ? p->idle_lease_ns : 10000000000ull;
@@ -317,8 +383,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if (live) ctx->ring_h = (lk_wire*)(mh + off_ring);
 
   ctx->tail = new (std::nothrow) Tail[ctx->C];
+  ctx->rearmed = new (std::nothrow) Tail[ctx->C];
   ctx->batch = new (std::nothrow) lk_ctx::BatchState[ctx->C];
-  if (!ctx->tail || !ctx->batch) return LK_ENOMEM;
+  if (!ctx->tail || !ctx->rearmed || !ctx->batch) return LK_ENOMEM;
   return LK_OK;
 }
 
@@ -327,6 +394,7 @@ static void teardown(lk_ctx* ctx) {
   if (ctx->dev_base) lkb_free_device(ctx->dev_base);
   if (ctx->mapped_h) lkb_free_mapped(ctx->mapped_h);
   delete[] ctx->tail;
+  delete[] ctx->rearmed;
   delete[] ctx->batch;
   delete ctx;
 }
@@ -404,15 +472,15 @@ int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in,
 }
 
 static int poll_seq(lk_ctx* ctx, int c, uint64_t seq) {
-  if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+  if (cl_done(ctx, c) >= seq) return LK_OK;
   uint32_t e = dev_error(ctx);
   if (e != 0) {
     /* the cluster may still have finished it before stopping */
-    if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+    if (cl_done(ctx, c) >= seq) return LK_OK;
     return device_err_to_rc(e);
   }
   if (ld_acq(&ctx->ctrl_h->exited) != 0 || !ctx->running.load(std::memory_order_relaxed)) {
-    if (ld_acq(&ctx->cword_h[c].done) >= seq) return LK_OK;
+    if (cl_done(ctx, c) >= seq) return LK_OK;
     return LK_ESTATE;
   }
   return LK_PENDING;
@@ -448,12 +516,12 @@ int lk_wait(lk_ctx* ctx, lk_handle h, uint64_t timeout_ns) {
   int c;
   uint64_t s;
   if (decode(ctx, h, &c, &s) != LK_OK) return LK_EINVAL;
-  if (ld_acq(&ctx->cword_h[c].done) >= s) return LK_OK;
+  if (cl_done(ctx, c) >= s) return LK_OK;
   beat(ctx);
   uint64_t t0 = now_ns();
   uint64_t last_beat = t0;
   for (uint32_t i = 0;; ++i) {
-    if (ld_acq(&ctx->cword_h[c].done) >= s) return LK_OK;
+    if (cl_done(ctx, c) >= s) return LK_OK;
     if ((i & 255) == 255) {
       int rc = poll_seq(ctx, c, s);
       if (rc != LK_PENDING) return rc;
@@ -551,7 +619,7 @@ int lk_submit_batch(lk_ctx* ctx, int cluster, const lk_batch_item* items, uint32
   lk_ctx::BatchState& bs = ctx->batch[cluster];
   std::lock_guard<std::mutex> g(bs.mu);
   const uint32_t b = (uint32_t)(bs.next % LK_BATCH_BUFFERS);
-  if (ld_acq(&ctx->cword_h[cluster].done) < bs.seq_of[b]) return LK_EAGAIN;   /* table still in use */
+  if (cl_done(ctx, cluster) < bs.seq_of[b]) return LK_EAGAIN;   /* table still in use */
   lk_unit* tab = ctx->units_h + ((size_t)cluster * LK_BATCH_BUFFERS + b) * ctx->max_units;
   uint64_t u = 0;
   uint32_t s_slot = 0, h_slot = 0;
@@ -632,7 +700,7 @@ int lk_status(lk_ctx* ctx, int cluster) {
    * Table 1's WORKING / FINISHED follow from the ring counters, which saves
    * the device two system-scope stores per descriptor */
   const uint64_t st = ld_acq(&ctx->cword_h[cluster].status);
-  if (st == LK_ST_EXITED || st == LK_ST_ERROR) return (int)st;
+  if (st == LK_ST_EXITED || st == LK_ST_ERROR || ctx->mailbox) return (int)st;
   const uint64_t tail = ctx->tail[cluster].t.load(std::memory_order_acquire);
   if (tail == 0) return LK_ST_INIT;
   return ld_acq(&ctx->cword_h[cluster].done) >= tail ? LK_ST_FINISHED : LK_ST_WORKING;
@@ -844,7 +912,7 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
       for (int c = w; c < ctx->C; c += n_threads) {
         auto& pq = pend[c];
         if (head[c] == pq.size()) continue;
-        uint64_t done = ld_acq(&ctx->cword_h[c].done);
+        uint64_t done = cl_done(ctx, c);
         if (done < pq[head[c]].first) {
           if (dev_error(ctx) != 0 || ld_acq(&ctx->ctrl_h->exited) != 0) {
             int rc = device_err_to_rc(dev_error(ctx));
@@ -1122,7 +1190,7 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
     /* completions (FIFO per cluster) */
     for (int c = 0; c < ctx->C; ++c) {
       if (fly[c].empty()) continue;
-      const uint64_t done = ld_acq(&ctx->cword_h[c].done);
+      const uint64_t done = cl_done(ctx, c);
       while (!fly[c].empty() && fly[c].front().seq <= done) {
         const Fly f = fly[c].front();
         fly[c].pop_front();

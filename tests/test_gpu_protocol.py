@@ -36,7 +36,7 @@ def check_log(oracle, ctx, log, sizes, n_posted, posted_op=None):
     return res, pinned
 
 
-@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT])
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX])
 def test_config_small_closed_loop(torch_ready, oracle_lib, flags):
     """4 SMs as 2 clusters of 2, 256 threads; 10,000 closed-loop int32 adds of
     4096 elements, values uniform in [-2^20, 2^20], seed 0, round-robin."""
@@ -102,7 +102,7 @@ def test_explicit_smid_lists(torch_ready, oracle_lib):
             assert r["smid"] == lists[r["cluster"]][r["rank"]]
 
 
-@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT])
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX])
 def test_many_producers_mixed_bodies(torch_ready, oracle_lib, flags):
     torch = torch_ready
     sizes = [8, 8, 8, 8]
@@ -193,6 +193,24 @@ def test_status_words_follow_table1(torch_ready):
         lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0))
         assert lk.lk_status(c, 0) == lk.LK_ST_FINISHED
         assert lk.lk_status(c, 1) == lk.LK_ST_INIT
+
+
+def test_mailbox_status_words_follow_table1(torch_ready):
+    """One-deep mailbox: INIT, WORKING/FINISHED around a descriptor, then the
+    master's NOP acknowledgement of the host's re-arm (Table 1)."""
+    with lk.lk_init([1, 1], idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_MAILBOX) as c:
+        assert lk.lk_status(c, 0) == lk.LK_ST_INIT
+        h = lk.lk_submit(c, 0, lk.LK_OP_SPIN, 1 << 20)     # ~2.5 ms of work
+        assert lk.lk_submit(c, 0, lk.LK_OP_NOP, 0) is None   # one deep
+        t0 = time.monotonic()
+        while lk.lk_status(c, 0) != lk.LK_ST_WORKING:
+            assert time.monotonic() - t0 < 2.0
+        assert lk.lk_wait(c, h) == lk.LK_OK
+        t0 = time.monotonic()
+        while lk.lk_status(c, 0) != lk.LK_ST_NOP:
+            assert time.monotonic() - t0 < 2.0
+        assert lk.lk_status(c, 1) == lk.LK_ST_INIT
+        assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)) == lk.LK_OK
 
 
 def test_baseline_launches_and_pingpong(torch_ready, oracle_lib):

@@ -14,7 +14,7 @@ def torch_ready(native_built):
     return need_gpu()
 
 
-@pytest.mark.parametrize("S,iters,threads", [(1, 20000, 256), (3, 1, 128), (8, 0, 256), (37, 5000, 512)])
+@pytest.mark.parametrize("S,iters,threads", [(1, 20000, 256), (3, 1, 128), (8, 0, 256), (37, 5000, 512), (5, 7, 256), (2, 9, 1024), (6, 20003, 256)])
 def test_spin_matches_closed_form(torch_ready, oracle_lib, S, iters, threads):
     torch = torch_ready
     out = torch.zeros(S, dtype=torch.int32, device="cuda")
@@ -32,9 +32,9 @@ def test_phase_runs_compute_the_same(torch_ready, oracle_lib):
     a = torch.zeros(4, dtype=torch.int32, device="cuda")
     b = torch.zeros(4, dtype=torch.int32, device="cuda")
     torch.cuda.current_stream().synchronize()
-    t_lk = lk.lk_phase_run(sms=4, iters=20000, runs=3, out=a)
-    t_cu = lk.lk_baseline_phase_run(sms=4, iters=20000, runs=3, out=b)
-    want = [oracle_lib.spin_xor(r, 256, 20000) for r in range(4)]
+    t_lk = lk.lk_phase_run(sms=4, iters=20005, runs=3, out=a)
+    t_cu = lk.lk_baseline_phase_run(sms=4, iters=20005, runs=3, out=b)
+    want = [oracle_lib.spin_xor(r, 256, 20005) for r in range(4)]
     assert host(a).view(np.uint32).tolist() == want
     assert host(b).view(np.uint32).tolist() == want
     assert np.all(t_lk["wait_ns"] > 0) and np.all(t_cu["wait_ns"] > 0)

@@ -388,3 +388,96 @@ def test_phase_run_on_fake(fake_env):
     assert res.size == 5
     for f in ("init_ns", "trigger_ns", "wait_ns", "dispose_ns"):
         assert np.all(res[f] > 0)
+
+
+# ---- the paper's one-deep mailbox (LK_INIT_MAILBOX, Sec. II.D, Table 1) ----------
+def test_mailbox_four_phase_handshake(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "200000"
+    with ctx_(sizes=(2, 1), flags=lk.LK_INIT_MAILBOX) as c:
+        assert lk.lk_status(c, 0) == lk.LK_ST_INIT
+        h1 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert h1 is not None and h1 & 0xffff == 1
+        time.sleep(0.05)
+        assert lk.lk_status(c, 0) == lk.LK_ST_WORKING          # master answered
+        assert lk.lk_submit(c, 0, lk.LK_OP_NOP, 0) is None    # one deep: EAGAIN
+        assert lk.lk_submit(c, 1, lk.LK_OP_NOP, 0) is not None   # other mailbox unaffected
+        assert lk.lk_poll(c, h1) == lk.LK_PENDING
+        assert lk.lk_wait(c, h1) == lk.LK_OK                   # saw FINISHED, re-armed
+        # the master acknowledges the re-arm with from_GPU = THREAD_NOP
+        t0 = time.monotonic()
+        while lk.lk_status(c, 0) != lk.LK_ST_NOP:
+            assert time.monotonic() - t0 < 2.0
+        h2 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+        assert h2 is not None and h2 & 0xffff == 2
+        assert lk.lk_wait(c, h2) == lk.LK_OK
+        assert lk.lk_sync(c) == lk.LK_OK
+
+
+def test_mailbox_rejects_direct(fake_env):
+    with pytest.raises(lk.LkError) as e:
+        ctx_(flags=lk.LK_INIT_MAILBOX | lk.LK_INIT_DIRECT)
+    assert e.value.code == lk.LK_EINVAL
+
+
+def test_mailbox_multi_producer_exec_log_passes_checker(fake_env, oracle_lib):
+    """Racing producers drive the handshake themselves (a refused post
+    re-arms a FINISHED mailbox); every descriptor runs once, in order."""
+    import oracle
+
+    sizes = (2, 3)
+    c = ctx_(sizes=sizes, exec_log_cap=1024, flags=lk.LK_INIT_MAILBOX)
+    posted = {}
+    lock = threading.Lock()
+
+    def producer(p):
+        for j in range(60):
+            cl = (p + j) % 2
+            op = (lk.LK_OP_NOP, lk.LK_OP_COPY_I32)[j % 2]
+            while True:
+                h = lk.lk_submit(c, cl, op, 64 if op else 0, (A,) if op else (), A if op else None)
+                if h is not None:
+                    break
+            with lock:
+                posted[(h >> 48, h & 0xffffffffffff)] = op
+
+    th = [threading.Thread(target=producer, args=(p,)) for p in range(3)]
+    [t.start() for t in th]
+    [t.join() for t in th]
+    assert lk.lk_sync(c) == lk.LK_OK
+    log, dropped = lk.lk_exec_log(c)
+    assert dropped == 0
+    n_posted = [sum(1 for (cl, _) in posted if cl == k) for k in range(2)]
+    assert sum(n_posted) == 180
+    posted_op = [posted[(k, s)] for k in range(2) for s in range(1, n_posted[k] + 1)]
+    pinned = sum((lk.lk_cluster_info(c, k) for k in range(2)), [])
+    res = oracle.check_exec_log(log["seq"], log["cluster"], log["rank"], log["smid"], log["op"], log["order"],
+                                sizes, n_posted, pinned_smid=pinned, posted_op=posted_op)
+    assert res["violations"] == 0, res
+    assert c.dispose() == lk.LK_OK
+
+
+def test_mailbox_trace_runner_and_dispose(fake_env):
+    with ctx_(sizes=(1, 2), flags=lk.LK_INIT_MAILBOX) as c:
+        n = 200
+        items = np.zeros(n, dtype=lk.TRACE_ITEM_DTYPE)
+        items["cluster"] = np.arange(n) % 2
+        items["op"] = lk.LK_OP_NOP
+        for closed in (True, False):
+            rc, res = lk.lk_run_trace(c, items, n_threads=2, closed_loop=closed)
+            assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+
+
+def test_mailbox_lost_completion_and_lease(fake_env):
+    fake_env["LK_FAKE_DROP_AFTER"] = "1"
+    c = ctx_(sizes=(1,), flags=lk.LK_INIT_MAILBOX, idle_lease_ns=200_000_000)
+    h1 = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    assert lk.lk_wait(c, h1) == lk.LK_OK
+    t0 = time.monotonic()
+    while (h2 := lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)) is None:
+        assert time.monotonic() - t0 < 2.0
+    assert lk.lk_wait(c, h2, timeout_ns=50_000_000) == lk.LK_ETIMEDOUT   # FINISHED never comes
+    assert lk.lk_submit(c, 0, lk.LK_OP_NOP, 0) is None                   # still one deep
+    time.sleep(0.8)                                                      # no heartbeat: the lease ends
+    assert lk.lk_device_error(c) == lk.LK_DERR_LEASE
+    assert lk.lk_poll(c, h1) == lk.LK_OK
+    assert c.dispose() == lk.LK_OK
