@@ -552,40 +552,59 @@ def main():
     hist_out = torch.zeros(256, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     periods = args.iso_periods
-    iso_res = {}
-    for loaded in (False, True):
-        be_items = 0
-        if loaded:
-            # enough best-effort work to outlast the critical run: time one pair first
-            with lk.lk_init(iso["sizes"], device=dev, idle_lease_ns=5_000_000_000) as ctx:
-                probe_tr = wl.isolation_traces(1, 4, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out)
-                rc, rp = lk.lk_run_trace(ctx, probe_tr[1:], n_threads=1, closed_loop=True)
-            pair_ns = float(rp["t_complete_ns"][-1]) / 2.0
-            be_items = int(2 * periods * iso["period_ns"] / max(pair_ns, 1.0) * 1.1) + 4
-        tr = wl.isolation_traces(periods, be_items, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out,
-                                 loaded=loaded)
-        with lk.lk_init(iso["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000) as ctx:
-            rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000)
-        if rc != lk.LK_OK:
-            raise RuntimeError(f"isolation trace failed: {lk.lk_strerror(rc)}")
-        crit = rr[:periods]
-        lat_c = (crit["t_complete_ns"] - crit["t_submit_ns"]) / 1000.0
-        rel_c = (crit["t_complete_ns"] - tr["t_arrival_ns"][:periods]) / 1000.0
-        key = "loaded" if loaded else "alone"
-        iso_res[key + "_us"] = lat_summary(lat_c)
-        iso_res[key + "_release_to_complete_us"] = lat_summary(rel_c)
-        if loaded:
-            be = rr[periods:]
-            be_ops = tr["op"][periods:]
-            moved = np.where(be_ops == lk.LK_OP_COPY_I32, 8.0 * iso["copy_n"], float(iso["hist_n"] + 1024)).sum()
-            span = float(be["t_complete_ns"].max() - be["t_submit_ns"].min())
-            iso_res["best_effort_gbs"] = moved / span
-            iso_res["best_effort_items"] = int(be.size)
-            last_crit = float(crit["t_complete_ns"].max())
-            iso_res["load_covered_critical_run"] = bool(float(be["t_complete_ns"].max()) >= last_crit)
+
+    def iso_run(init_kw):
+        """Critical periods alone, then under best-effort load, on one layout."""
+        out = {}
+        for loaded in (False, True):
+            be_items = 0
+            if loaded:
+                # enough best-effort work to outlast the critical run: time one pair first
+                with lk.lk_init(init_kw["sizes"], device=dev, idle_lease_ns=5_000_000_000,
+                                **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
+                    probe_tr = wl.isolation_traces(1, 4, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out)
+                    rc, rp = lk.lk_run_trace(ctx, probe_tr[1:], n_threads=1, closed_loop=True)
+                pair_ns = float(rp["t_complete_ns"][-1]) / 2.0
+                be_items = int(2 * periods * iso["period_ns"] / max(pair_ns, 1.0) * 1.1) + 4
+            tr = wl.isolation_traces(periods, be_items, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out,
+                                     loaded=loaded)
+            with lk.lk_init(init_kw["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000,
+                            **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
+                rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000)
+            if rc != lk.LK_OK:
+                raise RuntimeError(f"isolation trace failed: {lk.lk_strerror(rc)}")
+            crit = rr[:periods]
+            lat_c = (crit["t_complete_ns"] - crit["t_submit_ns"]) / 1000.0
+            rel_c = (crit["t_complete_ns"] - tr["t_arrival_ns"][:periods]) / 1000.0
+            key = "loaded" if loaded else "alone"
+            out[key + "_us"] = lat_summary(lat_c)
+            out[key + "_release_to_complete_us"] = lat_summary(rel_c)
+            if loaded:
+                be = rr[periods:]
+                be_ops = tr["op"][periods:]
+                moved = np.where(be_ops == lk.LK_OP_COPY_I32, 8.0 * iso["copy_n"], float(iso["hist_n"] + 1024)).sum()
+                span = float(be["t_complete_ns"].max() - be["t_submit_ns"].min())
+                out["best_effort_gbs"] = moved / span
+                out["best_effort_items"] = int(be.size)
+                last_crit = float(crit["t_complete_ns"].max())
+                out["load_covered_critical_run"] = bool(float(be["t_complete_ns"].max()) >= last_crit)
+        return out
+
+    iso_res = iso_run({"sizes": iso["sizes"]})
+    # several persistent CTAs per SM (Sec. II.C's next step): the critical
+    # cluster's 16 CTAs share SMs 0-15 with a best-effort cluster that spans
+    # every SM, instead of owning 16 SMs the best-effort work cannot use
+    with lk.lk_init([n_sms], device=dev, idle_lease_ns=5_000_000_000) as ctx:
+        sm_ids = lk.lk_cluster_info(ctx, 0)          # the SM ids the GPU reports, ascending
+    nc = iso["sizes"][0]
+    co = iso_run({"sizes": [nc, n_sms], "ctas_per_sm": 2, "smids": sm_ids[:nc] + sm_ids})
+    co["inflation_p999"] = co["loaded_us"]["p999"] / co["alone_us"]["p999"]
+    co["layout"] = (f"ctas_per_sm = 2; critical: one CTA on each of the {nc} lowest SM ids; best effort: "
+                    f"one CTA on every one of the {n_sms} SMs (the other CTA of the critical SMs)")
     iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
     iso_res["inflation_max"] = iso_res["loaded_us"]["max"] / iso_res["alone_us"]["max"]
     iso_res["periods"] = periods
+    iso_res["coresident"] = co
     iso_sum_ok = abs(float(crit_out[0].cpu()) - oracle.sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())) <= \
         1e-4 * oracle.abs_sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())
     iso_copy_ok = bool(torch.equal(copy_dst[-(1 << 20):], copy_src[-(1 << 20):]))

@@ -109,10 +109,14 @@ typedef uint64_t lk_handle;
 typedef struct {
   int device;                  /* CUDA device ordinal                                   */
   int num_clusters;            /* >= 1                                                  */
-  const int* sms_per_cluster;  /* [num_clusters], each >= 1, total <= SM count           */
+  const int* sms_per_cluster;  /* [num_clusters] CTAs of each cluster, each >= 1; total */
+                               /* <= SM count x ctas_per_sm                             */
   const int* smids;            /* optional: the SM ids of cluster 0, then cluster 1, ... */
-                               /* (total entries); NULL = clusters are cut from the     */
-                               /* observed SM ids sorted ascending                      */
+                               /* (total entries; an id appears at most ctas_per_sm     */
+                               /* times, its k-th appearance naming the SM's k-th CTA); */
+                               /* NULL = clusters are cut from the observed CTAs in     */
+                               /* slot-major order: every SM's first CTA by ascending   */
+                               /* SM id, then every SM's second CTA                     */
   int threads_per_cta;         /* multiple of 32 in [64, 1024]; 0 -> 256                 */
   int ring_depth;              /* descriptors queued per cluster, power of two; 0 -> 1024 */
   uint64_t backoff_base_ns;    /* first __nanosleep of a spin back-off (0 = pure spin)   */
@@ -124,8 +128,11 @@ typedef struct {
   uint32_t exec_log_cap;       /* execution-log records kept per CTA (ring); 0 = no log  */
   uint32_t flags;              /* LK_INIT_* bits                                        */
   uint32_t max_batch_units;    /* work units one batch may hold (lk_submit_batch);      */
-                               /* 0 -> 32768                                            */
-  uint32_t reserved;
+                               /* 0 -> 8192                                             */
+  uint32_t ctas_per_sm;        /* persistent CTAs on each SM: 0 or 1 -> one (Sec. II.C); */
+                               /* 2 -> two, each with half the shared memory (the      */
+                               /* "multiple persistent threads" model Sec. II.C leaves  */
+                               /* for later); 2 needs threads_per_cta <= 256            */
 } lk_init_params;
 
 /* lk_init_params.flags: how descriptors reach a cluster's CTAs.

@@ -211,20 +211,28 @@ int lkb_launch_kernel(int, const lk_kargs* ap, int threads, lkb_launch** out) {
   lkb_launch* l = new lkb_launch();
   l->t0 = now_ns();
   const int sms = fake_sms();
-  /* boot: CTA g lands on SM (5g + 3) mod sms; clusters from sorted SM ids */
+  /* boot: CTA g lands on SM (5g + 3) mod sms (CTAs g and g + sms share an
+   * SM); clusters from the slot-major order of (slot, SM id), as on the GPU */
+  if (a.grid > (a.ctas_per_sm == 2 ? 2 : 1) * sms) return LK_EDEVICE;
   std::vector<int> host_start(a.num_clusters + 1);
   memcpy(host_start.data(), a.cl_start, sizeof(int) * (a.num_clusters + 1));
-  std::vector<int> sm_of(a.grid);
-  for (int g = 0; g < a.grid; ++g) sm_of[g] = (5 * g + 3) % sms;
+  std::vector<int> sm_of(a.grid), slot_of(a.grid, 0);
+  for (int g = 0; g < a.grid; ++g) {
+    sm_of[g] = (5 * g + 3) % sms;
+    for (int q = 0; q < g; ++q) slot_of[g] += sm_of[q] == sm_of[g];
+  }
   std::vector<int> order(a.grid);
   for (int g = 0; g < a.grid; ++g) order[g] = g;
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return sm_of[x] < sm_of[y]; });
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    return slot_of[x] != slot_of[y] ? slot_of[x] < slot_of[y] : sm_of[x] < sm_of[y];
+  });
   std::vector<std::vector<int>> ctas(a.num_clusters), smids(a.num_clusters);
   for (int g = 0; g < a.grid; ++g) {
     int pos = -1;
     if (a.pin_smid) {
-      for (int i = 0; i < a.total; ++i)
-        if (a.pin_smid[i] == sm_of[g]) pos = i;
+      int seen = 0;
+      for (int i = 0; i < a.total && pos < 0; ++i)
+        if (a.pin_smid[i] == sm_of[g] && seen++ == slot_of[g]) pos = i;
     } else {
       pos = (int)(std::find(order.begin(), order.end(), g) - order.begin());
     }
@@ -237,6 +245,7 @@ int lkb_launch_kernel(int, const lk_kargs* ap, int threads, lkb_launch** out) {
     a.info[g].cluster = c;
     a.info[g].rank = r;
     a.info[g].smid = sm_of[g];
+    a.info[g].slot = slot_of[g];
   }
   for (int c = 0; c < a.num_clusters; ++c) {
     int size = host_start[c + 1] - host_start[c];

@@ -26,8 +26,9 @@
  *   sum_f32   per-thread float accumulators, warp shuffles, per-CTA partial;
  *             rank 0 adds the partials in rank order in binary64
  *   gemm64    64x64x64 float32 tiles staged into shared memory by TMA bulk
- *             copies (two stages so the next tile loads while this one
- *             computes), 4x4 register micro-tiles, FFMA in k order
+ *             copies (six 32 KB stages, three with two CTAs per SM, so later
+ *             tiles load while this one computes), 4x4 register micro-tiles,
+ *             FFMA in k order
  * Used by the persistent kernel and by the ordinary-launch baseline kernels.
  */
 #ifndef LK_BODIES_CUH
@@ -49,12 +50,28 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 }
 
 /* ---- shared-memory layout of a CTA ------------------------------------- */
+/* With one CTA per SM (P = 1) a CTA owns 192 KB: a 64 KB work region
+ * (histogram counters) and a 128 KB ring of LK_STAGES streaming stages; the
+ * GEMM stages span all of it.  With two CTAs per SM (P = 2) each CTA owns
+ * half of every region, so the bytes in flight per SM stay the same. */
 #define LK_SMEM_WORK (64u * 1024u)     /* histogram counters or GEMM stages   */
 #define LK_SMEM_STREAM (128u * 1024u)  /* streaming stages                    */
 #define LK_SMEM_DYN (LK_SMEM_WORK + LK_SMEM_STREAM)
 #define LK_STAGES 4u
-#define LK_GEMM_STAGES 6u              /* GEMM stages of 32 KB over the whole 192 KB */
+#define LK_GEMM_STAGE_FLOATS 8192u     /* one GEMM stage: A rows 16 KB + B tile 16 KB */
+#define LK_HIST_COPIES 4u              /* lane-private counter copies (16 KB each), P = 1 */
 #define LK_NUM_BARS 6u                 /* mbarriers: one per stage                */
+
+template <int P>
+struct SmemCfg {
+  static_assert(P == 1 || P == 2, "one or two CTAs per SM");
+  static constexpr uint32_t work_bytes = LK_SMEM_WORK / P;
+  static constexpr uint32_t stream_bytes = LK_SMEM_STREAM / P;
+  static constexpr uint32_t dyn_bytes = work_bytes + stream_bytes;
+  static constexpr uint32_t gemm_stages = dyn_bytes / (LK_GEMM_STAGE_FLOATS * 4u);   /* 6 or 3 */
+  static constexpr uint32_t hist_copies = LK_HIST_COPIES / P;
+  static_assert(gemm_stages <= LK_NUM_BARS, "one mbarrier per stage");
+};
 
 /* Stream the 16-byte vectors [beg, end) of NIN inputs through the stages.
  * consume(v0, nv, s0, s1) runs on every thread for each chunk: vectors
@@ -64,11 +81,11 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
  * holds one parity bit per mbarrier and persists across descriptors.
  * Returns false, on every thread alike, if a stage did not arrive before
  * `deadline`; this CTA's copies in flight are allowed to land first. */
-template <int NIN, bool STORE, class F>
+template <int NIN, bool STORE, int P, class F>
 __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint64_t beg, uint64_t end,
                                        unsigned char* stage_mem, uint64_t* bars, uint32_t& phase, uint64_t deadline,
                                        F&& consume) {
-  constexpr uint32_t stage_vec = LK_SMEM_STREAM / LK_STAGES / NIN / 16u;   /* vectors per input per chunk */
+  constexpr uint32_t stage_vec = SmemCfg<P>::stream_bytes / LK_STAGES / NIN / 16u;   /* vectors per input per chunk */
   const uint64_t total = end > beg ? end - beg : 0;
   const uint64_t nch = (total + stage_vec - 1) / stage_vec;
   if (nch == 0) return true;
@@ -122,6 +139,7 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
 }
 
 /* ---- int32 add / copy -------------------------------------------------- */
+template <int P>
 __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                          uint32_t& phase, uint64_t deadline) {
   const uint64_t n = d.n, nv = n >> 2;
@@ -129,8 +147,8 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
   share(nv, r, S, beg, end);
   int4* o = reinterpret_cast<int4*>(d.out);
   const uint32_t T = blockDim.x;
-  const bool ok = stream<2, false>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
-                                   beg, end, dsm + LK_SMEM_WORK, bars, phase, deadline,
+  const bool ok = stream<2, false, P>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
+                                   beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase, deadline,
                                    [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
                                      const int4* a = reinterpret_cast<const int4*>(s0);
                                      const int4* b = reinterpret_cast<const int4*>(s1);
@@ -145,13 +163,14 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
   return ok;
 }
 
+template <int P>
 __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                           uint32_t& phase, uint64_t deadline) {
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   uint4* o = reinterpret_cast<uint4*>(d.out);
-  const bool ok = stream<1, true>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars,
+  const bool ok = stream<1, true, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars,
                                   phase, deadline, [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4*) {
                                     if (threadIdx.x == 0) {
                                       bulk_s2g(o + v0, s0, cnt * 16u);
@@ -167,6 +186,7 @@ __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsign
 }
 
 /* ---- float32 sum: this CTA's partial (valid in thread 0) ---------------- */
+template <int P>
 __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                          uint32_t& phase, uint64_t deadline, float* red, float* partial_out) {
   const uint64_t n = d.n, nv = n >> 2;
@@ -174,7 +194,7 @@ __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigne
   share(nv, r, S, beg, end);
   const uint32_t T = blockDim.x;
   float acc0 = 0.f, acc1 = 0.f;
-  const bool ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK,
+  const bool ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes,
                                    bars, phase, deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                                      const float4* x = reinterpret_cast<const float4*>(s0);
                                      uint32_t v = threadIdx.x;
@@ -221,7 +241,6 @@ __device__ __forceinline__ void combine_sum(const lk_slot& d, const float* parti
 /* Shares below this many bytes per CTA use per-warp bins, whose set-up and
  * read-out are cheap; larger shares use the conflict-free lane-private path. */
 #define LK_HIST_SMALL_BYTES (64u * 1024u)
-#define LK_HIST_COPIES 4u      /* lane-private counter copies (16 KB each)   */
 
 __device__ __forceinline__ void count4_warp(uint32_t* bins, uint32_t w) {
   atomicAdd(&bins[w & 0xffu], 1u);
@@ -248,9 +267,10 @@ __device__ __forceinline__ void count4_lane(uint32_t* lane_base, uint32_t w) {
 /* Add the lane-private counters into tot_lo / tot_hi (rows owned by threads
  * < 128: bin `row` and bin `row + 128`).  A warp's loads start at
  * row-dependent columns so they spread over all banks. */
+template <int P>
 __device__ __forceinline__ void hist_readout(const uint32_t* sh, uint32_t& tot_lo, uint32_t& tot_hi) {
   for (uint32_t row = threadIdx.x; row < 128; row += blockDim.x) {
-    for (uint32_t c = 0; c < LK_HIST_COPIES; ++c) {
+    for (uint32_t c = 0; c < SmemCfg<P>::hist_copies; ++c) {
       const uint4* rw = reinterpret_cast<const uint4*>(sh + c * 4096u + row * 32u);
 #pragma unroll
       for (uint32_t j = 0; j < 8; ++j) {
@@ -267,6 +287,7 @@ __device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
   for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
 }
 
+template <int P>
 __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                           uint32_t& phase, uint64_t deadline, uint32_t* acc) {
   const uint64_t nv = d.n >> 4;
@@ -281,7 +302,7 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
     hist_zero(sh, W * 256);
     __syncthreads();
     uint32_t* bins = sh + (threadIdx.x >> 5) * 256;
-    ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars, phase,
+    ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase,
                           deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                             for (uint32_t v = threadIdx.x; v < cnt; v += T) {
                               const uint4 q = s0[v];
@@ -304,21 +325,22 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   /* large share: lane-private packed 16-bit counters.  A counter takes at
    * most 65535 increments between read-outs; each lane word is shared by the
    * ceil(W / copies) warps that use the same copy. */
-  const uint32_t copy = (threadIdx.x >> 5) % LK_HIST_COPIES;
+  constexpr uint32_t copies = SmemCfg<P>::hist_copies;
+  const uint32_t copy = (threadIdx.x >> 5) % copies;
   uint32_t* lane_base = sh + copy * 4096u + lane;
-  const uint32_t sharers = (W + LK_HIST_COPIES - 1) / LK_HIST_COPIES;
+  const uint32_t sharers = (W + copies - 1) / copies;
   const uint32_t limit = 65535u / sharers / 16u;   /* vectors per thread between read-outs */
   uint32_t since = 0, tot_lo = 0, tot_hi = 0;
-  hist_zero(sh, LK_HIST_COPIES * 4096u);
+  hist_zero(sh, copies * 4096u);
   __syncthreads();
-  ok = stream<1, false>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + LK_SMEM_WORK, bars, phase,
+  ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase,
                         deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                           const uint32_t per = (cnt + T - 1) / T;
                           if (since + per > limit) {   /* same decision on every thread */
                             __syncthreads();
-                            hist_readout(sh, tot_lo, tot_hi);
+                            hist_readout<P>(sh, tot_lo, tot_hi);
                             __syncthreads();
-                            hist_zero(sh, LK_HIST_COPIES * 4096u);
+                            hist_zero(sh, copies * 4096u);
                             __syncthreads();
                             since = 0;
                           }
@@ -337,7 +359,7 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
       red_add_shared(lane_base + ((v & 127u) << 5), 1u << ((v >> 7) << 4));
     }
   __syncthreads();
-  hist_readout(sh, tot_lo, tot_hi);
+  hist_readout<P>(sh, tot_lo, tot_hi);
   for (uint32_t row = threadIdx.x; row < 128; row += T) {
     if (tot_lo) atomicAdd(&acc[row], tot_lo);
     if (tot_hi) atomicAdd(&acc[row + 128], tot_hi);
@@ -415,13 +437,12 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
   return U;
 }
 
-/* Shared memory: LK_GEMM_STAGES stages of (A rows 16 KB, B tile 16 KB) over
- * the whole dynamic shared memory; one mbarrier per stage. */
-#define LK_GEMM_STAGE_FLOATS 8192u
+/* Shared memory: SmemCfg<P>::gemm_stages stages of (A rows 16 KB, B tile
+ * 16 KB) over the whole dynamic shared memory; one mbarrier per stage. */
 
 /* Returns false if a staging copy did not complete before `deadline`.
  * `phase` holds one parity bit per stage and persists across descriptors. */
-template <bool FULL_UNROLL>
+template <bool FULL_UNROLL, int P>
 __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float* sm, uint64_t* bars,
                                           uint32_t& phase, uint64_t deadline) {
   const uint64_t tiles = d.n;
@@ -434,8 +455,9 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   const float* B = reinterpret_cast<const float*>(d.in1);
   float* C = reinterpret_cast<float*>(d.out);
   const uint32_t T = blockDim.x;
+  constexpr uint32_t nstages = SmemCfg<P>::gemm_stages;
   auto issue = [&](uint64_t u) {   /* thread 0 */
-    const uint32_t st = (uint32_t)((u - beg) % LK_GEMM_STAGES);
+    const uint32_t st = (uint32_t)((u - beg) % nstages);
     const uint64_t tile = u / U;
     const uint32_t rb = (uint32_t)(u % U);
     float* sA = sm + st * LK_GEMM_STAGE_FLOATS;
@@ -447,18 +469,18 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   __shared__ int s_staged;
   __syncthreads();          /* every stage is free: the previous use ended with a barrier */
   if (threadIdx.x == 0)
-    for (uint64_t u = beg; u < end && u < beg + LK_GEMM_STAGES; ++u) issue(u);
+    for (uint64_t u = beg; u < end && u < beg + nstages; ++u) issue(u);
   bool ok = true;
   for (uint64_t u = beg; u < end; ++u) {
-    const uint32_t st = (uint32_t)((u - beg) % LK_GEMM_STAGES);
+    const uint32_t st = (uint32_t)((u - beg) % nstages);
     /* thread 0 alone decides whether the stage arrived in time, so that every
      * thread takes the same path through the barriers below */
     if (threadIdx.x == 0) {
       int arrived = mbar_wait(&bars[st], (phase >> st) & 1u, deadline);
       if (!arrived) {
         /* let this CTA's own copies land before giving up */
-        for (uint64_t v = u; v < end && v < u + LK_GEMM_STAGES; ++v) {
-          const uint32_t s2 = (uint32_t)((v - beg) % LK_GEMM_STAGES);
+        for (uint64_t v = u; v < end && v < u + nstages; ++v) {
+          const uint32_t s2 = (uint32_t)((v - beg) % nstages);
           mbar_wait(&bars[s2], (phase >> s2) & 1u, deadline + 1000000000ull);
         }
       }
@@ -470,7 +492,7 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
       break;
     }
     /* every thread finished unit u-1: refill its stage with unit u-1+STAGES */
-    if (threadIdx.x == 0 && u > beg && u - 1 + LK_GEMM_STAGES < end) issue(u - 1 + LK_GEMM_STAGES);
+    if (threadIdx.x == 0 && u > beg && u - 1 + nstages < end) issue(u - 1 + nstages);
     /* the phase is complete: this wait returns at once and makes the copied
      * bytes visible to this thread */
     mbar_wait(&bars[st], (phase >> st) & 1u, deadline + 1000000000ull);
@@ -517,8 +539,8 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   return ok;
 }
 
-/* Dynamic shared memory every body launch asks for. */
-__host__ __device__ constexpr uint32_t body_smem_bytes(int) { return LK_SMEM_DYN; }
+/* Dynamic shared memory a CTA asks for when P CTAs share an SM. */
+__host__ __device__ constexpr uint32_t body_smem_bytes(int P) { return P == 2 ? SmemCfg<2>::dyn_bytes : SmemCfg<1>::dyn_bytes; }
 
 }  // namespace lk
 #endif

@@ -306,20 +306,21 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
 /* This CTA's share of descriptor d (rank r of S).  Returns an LK_DERR_* code
  * or 0.  `partial_out` receives the sum body's per-CTA partial.  MAXT (the
  * largest block size of the calling kernel) sets how far the GEMM's k loop is
- * unrolled: fully at up to 256 threads, where the registers allow it. */
-template <int MAXT>
+ * unrolled: fully at up to 256 threads with one CTA per SM, where the
+ * registers allow it.  P (CTAs per SM) sets the shared-memory budget. */
+template <int MAXT, int P>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                         uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
   const uint64_t deadline = gtime() + 2000000000ull;
   bool ok = true;
   switch (op) {
-    case LK_OP_ADD_I32: ok = body_add(d, r, S, dsm, bars, phase, deadline); break;
-    case LK_OP_COPY_I32: ok = body_copy(d, r, S, dsm, bars, phase, deadline); break;
-    case LK_OP_SUM_F32: ok = body_sum(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
-    case LK_OP_HIST_U8: ok = body_hist(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
+    case LK_OP_ADD_I32: ok = body_add<P>(d, r, S, dsm, bars, phase, deadline); break;
+    case LK_OP_COPY_I32: ok = body_copy<P>(d, r, S, dsm, bars, phase, deadline); break;
+    case LK_OP_SUM_F32: ok = body_sum<P>(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
+    case LK_OP_HIST_U8: ok = body_hist<P>(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
     case LK_OP_GEMM64_F32:
-      ok = body_gemm<(MAXT <= 256)>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline);
+      ok = body_gemm<(MAXT <= 256 && P == 1), P>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline);
       break;
     case LK_OP_COMBINE_SUM: body_combine_sum(d, r); break;
     case LK_OP_COMBINE_HIST: body_combine_hist(d, r); break;
@@ -337,7 +338,7 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
  * per-item state: the last part to finish writes the item's output (sums in
  * binary64, in part order) and returns the state to zero.  Returns an
  * LK_DERR_* code or 0. */
-template <int MAXT>
+template <int MAXT, int P>
 __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
                                          uint64_t* bars, uint32_t& phase, float* red) {
   __shared__ uint64_t s_unit[6];
@@ -379,7 +380,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
     bool ok = true;
     if (op == LK_OP_SUM_F32) {
       float* pout = parts > 1 ? &bc->sums[comb - 1].partial[part] : &s_part;
-      ok = body_sum(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
+      ok = body_sum<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
       if (threadIdx.x == 0) {
         if (parts == 1) {
           *reinterpret_cast<float*>(it.out) = s_part;
@@ -397,7 +398,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
       }
     } else if (op == LK_OP_HIST_U8) {
       uint32_t* acc = parts > 1 ? bc->hists[comb - 1].bins : my_hist;
-      ok = body_hist(it, (int)part, (int)parts, dsm, bars, phase, deadline, acc);
+      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, acc);
       __syncthreads();
       if (threadIdx.x == 0) {
         s_lastp = 1;
@@ -413,7 +414,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
         if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
       }
     } else {
-      const int e = run_body<MAXT>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
+      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
       ok = (e == 0);
     }
     __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
@@ -422,8 +423,8 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
   return 0;
 }
 
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
+template <int MAXT, int P>
+__global__ void __launch_bounds__(MAXT, P) lk_persistent(const lk_kargs a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(64) lk_slot s_desc;
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
@@ -433,35 +434,67 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
   const uint32_t tid = threadIdx.x;
 
   /* ---- boot: read %smid, exchange, join a cluster --------------------- */
+  __shared__ int32_t s_sm, s_slot, s_pos;
   if (tid == 0) {
     s_err = 0;
+    s_slot = 0;
+    s_pos = 0;
     const uint32_t sm = smid();
+    s_sm = (int32_t)sm;
     a.boot_smid[blockIdx.x] = (int32_t)sm;
     __threadfence();
     atomicAdd(a.boot_count, 1u);
     const uint64_t t0 = gtime();
-    int err = 0;
     while (ld_acquire_gpu32(a.boot_count) < (uint32_t)a.grid) {
       if (gtime() - t0 > a.boot_timeout_ns) {
-        err = LK_DERR_BOOT;
+        s_err = LK_DERR_BOOT;
         break;
       }
     }
+  }
+  __syncthreads();
+  /* Position of this CTA in the slot-major order of (slot, SM id): slot s of
+   * an SM is the CTA with the s-th lowest block index among those that landed
+   * on it, and every SM's slot 0 comes before any slot 1.  With one CTA per
+   * SM this is the order of SM ids.  The whole CTA counts, over a copy of the
+   * exchanged ids in shared memory (at most 2 x 152 of them). */
+  if (!s_err) {
+    int32_t* all = reinterpret_cast<int32_t*>(dsm);
+    for (int j = (int)tid; j < a.grid; j += (int)blockDim.x) all[j] = __ldcg(a.boot_smid + j);
+    __syncthreads();
+    const int32_t my_sm = s_sm;
+    int below = 0;
+    for (int j = (int)tid; j < (int)blockIdx.x; j += (int)blockDim.x) below += all[j] == my_sm;
+    if (below) atomicAdd(&s_slot, below);
+    __syncthreads();
+    const int my_slot = s_slot;
+    if (!a.pin_smid) {
+      int before = 0;
+      for (int j = (int)tid; j < a.grid; j += (int)blockDim.x) {
+        int sj = 0;
+        for (int q = 0; q < j; ++q) sj += all[q] == all[j];
+        before += (sj < my_slot) || (sj == my_slot && all[j] < my_sm);
+      }
+      if (before) atomicAdd(&s_pos, before);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const int err = s_err;
+    const uint32_t sm = (uint32_t)s_sm;
     int c = -1, rk = -1;
     if (!err) {
       int pos = -1;
       if (a.pin_smid) {
+        /* slot s of an SM takes the (s+1)-th occurrence of its id in the list */
+        int seen = 0;
         for (int i = 0; i < a.total; ++i)
-          if (a.pin_smid[i] == (int32_t)sm) {
+          if (a.pin_smid[i] == (int32_t)sm && seen++ == s_slot) {
             pos = i;
             break;
           }
       } else {
-        pos = 0;
-        for (int j = 0; j < a.grid; ++j) {
-          const int32_t o = __ldcg(a.boot_smid + j);
-          if (o < (int32_t)sm || (o == (int32_t)sm && j < (int)blockIdx.x)) ++pos;
-        }
+        pos = s_pos < a.total ? s_pos : -1;
       }
       if (pos >= 0) {
         c = 0;
@@ -476,9 +509,9 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     st_relaxed_sys32(&inf->cluster, c);
     st_relaxed_sys32(&inf->rank, rk);
     st_relaxed_sys32(&inf->smid, (int32_t)sm);
+    st_relaxed_sys32(&inf->slot, s_slot);
     if (err) {
       set_error(a, c, (uint32_t)err);
-      s_err = err;
     } else if (rk == 0) {
       st_relaxed_sys(&a.cword[c].status, LK_ST_INIT);
     }
@@ -554,8 +587,8 @@ __global__ void __launch_bounds__(MAXT, 1) lk_persistent(const lk_kargs a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = op == LK_OP_BATCH ? run_batch<MAXT>(a, d, c, r, dsm, s_bars, phase, s_red)
-                                       : run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+    const int berr = op == LK_OP_BATCH ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
+                                       : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -647,7 +680,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
+  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -691,8 +724,9 @@ cudaError_t g_preload_err = cudaSuccess;
 void preload_all() {
   std::call_once(g_preload_once, [] {
     cudaFuncAttributes fa;
-    const void* fns[] = {(const void*)lk_persistent<256>,  (const void*)lk_persistent<512>,
-                         (const void*)lk_persistent<1024>, (const void*)lk_ordinary<256>,
+    const void* fns[] = {(const void*)lk_persistent<256, 1>,  (const void*)lk_persistent<512, 1>,
+                         (const void*)lk_persistent<1024, 1>, (const void*)lk_persistent<256, 2>,
+                         (const void*)lk_ordinary<256>,
                          (const void*)lk_ordinary<512>,    (const void*)lk_ordinary<1024>,
                          (const void*)lk_pingpong_kernel};
     for (const void* f : fns) {
@@ -701,19 +735,19 @@ void preload_all() {
     }
     /* ordinary launches of the histogram / GEMM bodies take 64 KB of shared memory */
     const void* ord[] = {(const void*)lk_ordinary<256>, (const void*)lk_ordinary<512>, (const void*)lk_ordinary<1024>};
-    const int ord_t[] = {256, 512, 1024};
     for (int i = 0; i < 3; ++i) {
       cudaError_t e = cudaFuncSetAttribute(ord[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)lk::body_smem_bytes(ord_t[i]));
+                                           (int)lk::body_smem_bytes(1));
       if (e != cudaSuccess && g_preload_err == cudaSuccess) g_preload_err = e;
     }
   });
 }
 
-const void* persistent_fn(int threads) {
-  if (threads <= 256) return (const void*)lk_persistent<256>;
-  if (threads <= 512) return (const void*)lk_persistent<512>;
-  return (const void*)lk_persistent<1024>;
+const void* persistent_fn(int threads, int per_sm) {
+  if (per_sm == 2) return threads <= 256 ? (const void*)lk_persistent<256, 2> : nullptr;
+  if (threads <= 256) return (const void*)lk_persistent<256, 1>;
+  if (threads <= 512) return (const void*)lk_persistent<512, 1>;
+  return (const void*)lk_persistent<1024, 1>;
 }
 
 /* Allocations are recycled, never returned to the driver while the process
@@ -878,14 +912,17 @@ int lkb_launch_kernel(int device, const lk_kargs* a, int threads, lkb_launch** o
   if (g_preload_err != cudaSuccess) return LK_EDEVICE;
   cudaDeviceProp p;
   if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return LK_EDEVICE;
-  const void* fn = persistent_fn(threads);
-  /* one CTA per SM: ask for more than half of the SM's shared memory */
-  size_t dyn = std::max<size_t>(lk::body_smem_bytes(threads), p.sharedMemPerMultiprocessor / 2);
+  const int want = a->ctas_per_sm == 2 ? 2 : 1;
+  const void* fn = persistent_fn(threads, want);
+  if (!fn) return LK_EINVAL;
+  /* exactly `want` CTAs per SM: ask for more than 1/(want+1) of the SM's
+   * shared memory (one CTA: more than half; two: more than a third) */
+  size_t dyn = std::max<size_t>(lk::body_smem_bytes(want), p.sharedMemPerMultiprocessor / (want + 1) + 1);
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
     return LK_EDEVICE;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, dyn) != cudaSuccess) return LK_EDEVICE;
-  if (per_sm != 1 || a->grid > p.multiProcessorCount) return LK_EDEVICE;
+  if (per_sm != want || a->grid > want * p.multiProcessorCount) return LK_EDEVICE;
   lkb_launch* l = new lkb_launch{device, nullptr, nullptr, nullptr};
   if (cudaStreamCreateWithFlags(&l->s, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&l->e0) != cudaSuccess || cudaEventCreate(&l->e1) != cudaSuccess) {

@@ -119,7 +119,7 @@ typedef struct {
   int32_t cluster;               /* -1: CTA not used (explicit SM lists)                */
   int32_t rank;
   int32_t smid;
-  int32_t pad;
+  int32_t slot;                  /* 0, or 1 for the second CTA on its SM                */
 } lk_cta_info;
 
 /* Per-cluster state in device memory.  `flag[r]` is the number of
@@ -196,6 +196,7 @@ typedef struct {
   uint32_t ring_log2;            /* log2 R                                              */
   uint32_t log_cap;
   uint32_t flags;
+  int32_t ctas_per_sm;           /* 1, or 2: two persistent CTAs share each SM          */
   uint64_t backoff_base_ns;
   uint64_t backoff_cap_ns;
   uint64_t lease_ns;

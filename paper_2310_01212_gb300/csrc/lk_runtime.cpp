@@ -56,6 +56,7 @@ struct lk_ctx {
   int G = 0;          /* CTAs launched */
   int total = 0;      /* CTAs that join clusters */
   int T = 256;        /* threads per CTA */
+  int per_sm = 1;     /* persistent CTAs per SM */
   uint32_t R = 1024;  /* ring depth */
   int sm_count = 0;
   bool finite = false;
@@ -278,19 +279,22 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
     ctx->cl_start[c + 1] = ctx->cl_start[c] + ctx->sizes[c];
   }
   ctx->total = ctx->cl_start[ctx->C];
-  if (ctx->total > props.sm_count || ctx->total > LK_MAX_CTAS) return LK_EINVAL;
+  if (p->ctas_per_sm > 2) return LK_EINVAL;
+  ctx->per_sm = p->ctas_per_sm == 2 ? 2 : 1;
+  if (ctx->total > ctx->per_sm * props.sm_count || ctx->total > LK_MAX_CTAS) return LK_EINVAL;
   if (p->smids) {
     std::vector<int> seen(props.sm_count, 0);
     for (int i = 0; i < ctx->total; ++i) {
-      if (p->smids[i] < 0 || p->smids[i] >= props.sm_count || seen[p->smids[i]]) return LK_EINVAL;
-      seen[p->smids[i]] = 1;
+      if (p->smids[i] < 0 || p->smids[i] >= props.sm_count || seen[p->smids[i]] >= ctx->per_sm) return LK_EINVAL;
+      seen[p->smids[i]]++;
     }
-    ctx->G = props.sm_count;   /* one CTA on every SM; those not listed return at boot */
+    ctx->G = ctx->per_sm * props.sm_count;   /* every CTA slot of every SM; those not listed return at boot */
   } else {
     ctx->G = ctx->total;
   }
   ctx->T = p->threads_per_cta ? p->threads_per_cta : 256;
   if (ctx->T < 64 || ctx->T > 1024 || ctx->T % 32) return LK_EINVAL;
+  if (ctx->per_sm == 2 && ctx->T > 256) return LK_EINVAL;
   uint32_t R = ring_depth_override ? ring_depth_override : (p->ring_depth ? (uint32_t)p->ring_depth : 1024u);
   if (R < 2 || (R & (R - 1)) || R > (1u << 24)) return LK_EINVAL;
   ctx->R = R;
@@ -376,6 +380,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.ring_log2 = ctx->R_log2;
   a.log_cap = ctx->log_cap;
   a.flags = ((p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u) | (ctx->mailbox ? LK_KFLAG_MAILBOX : 0u);
+  a.ctas_per_sm = ctx->per_sm;
   a.backoff_base_ns = p->backoff_base_ns;
   a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;
   a.lease_ns = p->idle_lease_ns ? p->idle_lease_ns : 10000000000ull;

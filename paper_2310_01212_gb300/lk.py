@@ -52,7 +52,7 @@ class lk_init_params(ctypes.Structure):
                 ("backoff_base_ns", ctypes.c_uint64), ("backoff_cap_ns", ctypes.c_uint64),
                 ("idle_lease_ns", ctypes.c_uint64), ("boot_timeout_ns", ctypes.c_uint64),
                 ("exec_log_cap", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("max_batch_units", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_batch_units", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
 
 class lk_desc(ctypes.Structure):
@@ -170,12 +170,12 @@ def _ptr(x) -> int:
 def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
                 backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
                 boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0,
-                max_batch_units: int = 0):
+                max_batch_units: int = 0, ctas_per_sm: int = 0):
     """lk_init_params plus the arrays it points to (kept alive by the tuple)."""
     sz = (ctypes.c_int * len(sizes))(*sizes)
     sm = None if smids is None else (ctypes.c_int * len(smids))(*smids)
     p = lk_init_params(device, len(sizes), sz, sm, threads_per_cta, ring_depth, backoff_base_ns, backoff_cap_ns,
-                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags, max_batch_units, 0)
+                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags, max_batch_units, ctas_per_sm)
     return p, (sz, sm)
 
 

@@ -10,6 +10,9 @@ from paper_2310_01212_gb300 import lk, synth
 pytestmark = pytest.mark.gpu
 
 SIZES = [0, 1, 3, 4, 5, 17, 1023, 4096, 65536 + 7, (1 << 20) + 13]
+# (CTAs in the cluster, persistent CTAs per SM): two per SM halves every
+# shared-memory region (streaming stages, histogram copies, GEMM stages)
+SP = [(1, 1), (2, 1), (37, 1), (2, 2), (37, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -17,8 +20,8 @@ def torch_ready(native_built):
     return need_gpu()
 
 
-@pytest.mark.parametrize("S", [1, 2, 37])
-def test_add_copy_bit_exact(torch_ready, oracle_lib, S):
+@pytest.mark.parametrize("S,per_sm", SP)
+def test_add_copy_bit_exact(torch_ready, oracle_lib, S, per_sm):
     torch = torch_ready
     cases = []
     for i, n in enumerate(SIZES):
@@ -27,7 +30,7 @@ def test_add_copy_bit_exact(torch_ready, oracle_lib, S):
         cases.append((n, a, b, to_dev(a), to_dev(b), torch.zeros(max(n, 1), dtype=torch.int32, device="cuda"),
                       torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")))
     torch.cuda.current_stream().synchronize()
-    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000, ctas_per_sm=per_sm) as c:
         hs = []
         for n, a, b, da, db, oa, oc in cases:
             hs.append(lk.lk_submit(c, 0, lk.LK_OP_ADD_I32, n, (da, db), oa))
@@ -39,8 +42,8 @@ def test_add_copy_bit_exact(torch_ready, oracle_lib, S):
         assert np.array_equal(host(oc)[:n], oracle_lib.copy_i32(a)), n
 
 
-@pytest.mark.parametrize("S", [1, 2, 37])
-def test_hist_bit_exact(torch_ready, oracle_lib, S):
+@pytest.mark.parametrize("S,per_sm", SP)
+def test_hist_bit_exact(torch_ready, oracle_lib, S, per_sm):
     torch = torch_ready
     cases = []
     for i, n in enumerate(SIZES):
@@ -52,7 +55,7 @@ def test_hist_bit_exact(torch_ready, oracle_lib, S):
     x = x[synth.permutation(12, 99, x.size)]
     cases.append((x, to_dev(x), torch.full((256,), -1, dtype=torch.int32, device="cuda")))
     torch.cuda.current_stream().synchronize()
-    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000, ctas_per_sm=per_sm) as c:
         hs = [lk.lk_submit(c, 0, lk.LK_OP_HIST_U8, x.size, (dx,), out) for x, dx, out in cases]
         for h in hs:
             assert lk.lk_wait(c, h) == lk.LK_OK
@@ -60,8 +63,8 @@ def test_hist_bit_exact(torch_ready, oracle_lib, S):
         assert np.array_equal(host(out).astype(np.int64), oracle_lib.hist_u8(x)), x.size
 
 
-@pytest.mark.parametrize("S", [1, 2, 37])
-def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S):
+@pytest.mark.parametrize("S,per_sm", SP)
+def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S, per_sm):
     torch = torch_ready
     cases = []
     for i, n in enumerate(SIZES):
@@ -72,7 +75,7 @@ def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S):
         x = ((np.arange(n) % 7) - 3).astype(np.float32)
         cases.append((x, to_dev(x), torch.full((4,), 7.0, device="cuda"), True))
     torch.cuda.current_stream().synchronize()
-    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000, ctas_per_sm=per_sm) as c:
         hs = [lk.lk_submit(c, 0, lk.LK_OP_SUM_F32, x.size, (dx,), out) for x, dx, out, _ in cases]
         for h in hs:
             assert lk.lk_wait(c, h) == lk.LK_OK
@@ -84,8 +87,8 @@ def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S):
             assert sum_ok(got, x, oracle_lib), (x.size, got, oracle_lib.sum_f32(x))
 
 
-@pytest.mark.parametrize("S", [1, 2, 37])
-def test_gemm_tiles(torch_ready, oracle_lib, S):
+@pytest.mark.parametrize("S,per_sm", SP)
+def test_gemm_tiles(torch_ready, oracle_lib, S, per_sm):
     torch = torch_ready
     cases = []
     for i, t in enumerate([1, 2, 3, 5, 37, 100]):
@@ -96,7 +99,7 @@ def test_gemm_tiles(torch_ready, oracle_lib, S):
     B = synth.normal_f32(14, 77, 3 * 4096).reshape(3, 64, 64)
     cases.append((I, B, to_dev(I), to_dev(B), torch.zeros((3, 64, 64), device="cuda")))
     torch.cuda.current_stream().synchronize()
-    with lk.lk_init([S], idle_lease_ns=5_000_000_000) as c:
+    with lk.lk_init([S], idle_lease_ns=5_000_000_000, ctas_per_sm=per_sm) as c:
         hs = [lk.lk_submit(c, 0, lk.LK_OP_GEMM64_F32, A.shape[0], (dA, dB), dC) for A, B, dA, dB, dC in cases]
         for h in hs:
             assert lk.lk_wait(c, h) == lk.LK_OK

@@ -195,6 +195,37 @@ def test_status_words_follow_table1(torch_ready):
         assert lk.lk_status(c, 1) == lk.LK_ST_INIT
 
 
+def test_two_ctas_per_sm_share_every_sm(torch_ready, oracle_lib):
+    """ctas_per_sm = 2: both slots of every SM join clusters; slot-major order
+    puts cluster 0 (all first CTAs) and cluster 1 (all second CTAs) on the
+    same SMs, and every descriptor runs once on the CTAs it was pinned to."""
+    torch = torch_ready
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    with lk.lk_init([nsm, nsm], ctas_per_sm=2, exec_log_cap=64, idle_lease_ns=5_000_000_000) as c:
+        a, b = lk.lk_cluster_info(c, 0), lk.lk_cluster_info(c, 1)
+        assert a == b == sorted(a) and len(set(a)) == nsm
+        hs = [lk.lk_submit(c, i % 2, lk.LK_OP_NOP, 0) for i in range(40)]
+        assert all(lk.lk_wait(c, h) == lk.LK_OK for h in hs)
+        log, _ = lk.lk_exec_log(c)
+        verdict, _ = check_log(oracle_lib, c, log, [nsm, nsm], [20, 20], posted_op=[0] * 40)
+        assert verdict["violations"] == 0, verdict
+
+
+def test_two_ctas_per_sm_pinned_lists(torch_ready, oracle_lib):
+    lists = [[0, 1, 2], [2, 1], [0]]    # SM 0, 1, 2 each hold two CTAs of different clusters
+    with lk.lk_init([3, 2, 1], smids=sum(lists, []), ctas_per_sm=2, exec_log_cap=64,
+                    idle_lease_ns=5_000_000_000) as c:
+        for k in range(3):
+            assert lk.lk_cluster_info(c, k) == lists[k]
+        hs = [lk.lk_submit(c, i % 3, lk.LK_OP_NOP, 0) for i in range(30)]
+        assert all(lk.lk_wait(c, h) == lk.LK_OK for h in hs)
+        log, _ = lk.lk_exec_log(c)
+        verdict, _ = check_log(oracle_lib, c, log, [3, 2, 1], [10, 10, 10], posted_op=[0] * 30)
+        assert verdict["violations"] == 0, verdict
+        for r in log:
+            assert r["smid"] == lists[r["cluster"]][r["rank"]]
+
+
 def test_mailbox_status_words_follow_table1(torch_ready):
     """One-deep mailbox: INIT, WORKING/FINISHED around a descriptor, then the
     master's NOP acknowledgement of the host's re-arm (Table 1)."""

@@ -481,3 +481,42 @@ def test_mailbox_lost_completion_and_lease(fake_env):
     assert lk.lk_device_error(c) == lk.LK_DERR_LEASE
     assert lk.lk_poll(c, h1) == lk.LK_OK
     assert c.dispose() == lk.LK_OK
+
+
+# ---- two persistent CTAs per SM (ctas_per_sm = 2) ---------------------------------
+def test_two_ctas_per_sm_slot_major_clusters(fake_env):
+    """16 fake SMs x 2: every SM's first CTA (by SM id) before any second CTA,
+    so clusters 0 and 1 below sit on the same eight SMs."""
+    with ctx_(sizes=(8, 8, 8, 8), ctas_per_sm=2) as c:
+        info = [lk.lk_cluster_info(c, k) for k in range(4)]
+        assert info[0] == list(range(8)) and info[1] == list(range(8, 16))
+        assert info[2] == list(range(8)) and info[3] == list(range(8, 16))
+        hs = [lk.lk_submit(c, i % 4, lk.LK_OP_NOP, 0) for i in range(40)]
+        assert all(lk.lk_wait(c, h) == lk.LK_OK for h in hs)
+
+
+def test_two_ctas_per_sm_pinned_lists(fake_env, oracle_lib):
+    import oracle
+
+    # SM 3 appears twice: its first CTA joins cluster 0, its second cluster 1
+    lists = [[3, 5], [3, 9, 5]]
+    with ctx_(sizes=(2, 3), smids=lists[0] + lists[1], ctas_per_sm=2, exec_log_cap=64) as c:
+        assert lk.lk_cluster_info(c, 0) == lists[0] and lk.lk_cluster_info(c, 1) == lists[1]
+        hs = [lk.lk_submit(c, i % 2, lk.LK_OP_NOP, 0) for i in range(10)]
+        assert all(lk.lk_wait(c, h) == lk.LK_OK for h in hs)
+        log, _ = lk.lk_exec_log(c)
+        res = oracle.check_exec_log(log["seq"], log["cluster"], log["rank"], log["smid"], log["op"], log["order"],
+                                    [2, 3], [5, 5], pinned_smid=lists[0] + lists[1], posted_op=[0] * 10)
+        assert res["violations"] == 0, res
+
+
+@pytest.mark.parametrize("kw", [dict(sizes=(8,), ctas_per_sm=3),                      # one or two only
+                                dict(sizes=(17, 16), ctas_per_sm=2),                  # > 2 x 16 CTAs
+                                dict(sizes=(2,), ctas_per_sm=2, threads_per_cta=512),  # registers
+                                dict(sizes=(3,), smids=[4, 4, 4], ctas_per_sm=2),     # an SM thrice
+                                dict(sizes=(2,), smids=[4, 4])])                      # twice, one per SM
+def test_two_ctas_per_sm_rejects(fake_env, kw):
+    sizes = kw.pop("sizes")
+    with pytest.raises(lk.LkError) as e:
+        ctx_(sizes=sizes, **kw)
+    assert e.value.code == lk.LK_EINVAL
