@@ -553,15 +553,17 @@ def main():
     torch.cuda.synchronize()
     periods = args.iso_periods
 
-    def iso_run(init_kw):
-        """Critical periods alone, then under best-effort load, on one layout."""
+    def iso_run(init_kw, be_rate=0, alone=True):
+        """Critical periods alone, then under best-effort load, on one layout;
+        be_rate caps the best-effort cluster's loads (bytes/us, 0 = none)."""
         out = {}
-        for loaded in (False, True):
+        for loaded in ((False, True) if alone else (True,)):
             be_items = 0
             if loaded:
                 # enough best-effort work to outlast the critical run: time one pair first
                 with lk.lk_init(init_kw["sizes"], device=dev, idle_lease_ns=5_000_000_000,
                                 **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
+                    lk.lk_set_rate(ctx, 1, be_rate)
                     probe_tr = wl.isolation_traces(1, 4, pools.f32, crit_out, copy_src, copy_dst, hist_in, hist_out)
                     rc, rp = lk.lk_run_trace(ctx, probe_tr[1:], n_threads=1, closed_loop=True)
                 pair_ns = float(rp["t_complete_ns"][-1]) / 2.0
@@ -570,6 +572,7 @@ def main():
                                      loaded=loaded)
             with lk.lk_init(init_kw["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000,
                             **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
+                lk.lk_set_rate(ctx, 1, be_rate)
                 rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000)
             if rc != lk.LK_OK:
                 raise RuntimeError(f"isolation trace failed: {lk.lk_strerror(rc)}")
@@ -601,10 +604,19 @@ def main():
     co["inflation_p999"] = co["loaded_us"]["p999"] / co["alone_us"]["p999"]
     co["layout"] = (f"ctas_per_sm = 2; critical: one CTA on each of the {nc} lowest SM ids; best effort: "
                     f"one CTA on every one of the {n_sms} SMs (the other CTA of the critical SMs)")
+    # best-effort load-rate caps (token-bucket pacing of its TMA loads): the
+    # critical tail against the throughput given up, on the disjoint layout
+    paced = {}
+    for cap_gbs in (1000, 2000, 3000, 4000):
+        pr = iso_run({"sizes": iso["sizes"]}, be_rate=cap_gbs * 1000, alone=False)
+        paced[str(cap_gbs)] = {"loaded_us": pr["loaded_us"], "best_effort_gbs": pr["best_effort_gbs"],
+                               "inflation_p999": pr["loaded_us"]["p999"] / iso_res["alone_us"]["p999"],
+                               "load_covered_critical_run": pr["load_covered_critical_run"]}
     iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
     iso_res["inflation_max"] = iso_res["loaded_us"]["max"] / iso_res["alone_us"]["max"]
     iso_res["periods"] = periods
     iso_res["coresident"] = co
+    iso_res["best_effort_rate_cap_gbs"] = paced
     iso_sum_ok = abs(float(crit_out[0].cpu()) - oracle.sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())) <= \
         1e-4 * oracle.abs_sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())
     iso_copy_ok = bool(torch.equal(copy_dst[-(1 << 20):], copy_src[-(1 << 20):]))

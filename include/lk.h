@@ -36,7 +36,9 @@
  *
  * While a context runs, its CTAs occupy their SMs: a device-wide synchronise
  * (cudaDeviceSynchronize, torch.cuda.synchronize) blocks until the context is
- * disposed or its idle lease runs out.  Wait on other streams only.
+ * disposed or its idle lease runs out, and so may a device allocation or free
+ * (cudaMalloc / cudaFree, e.g. a caching allocator that grows).  Allocate
+ * buffers before lk_init; wait on other streams only.
  */
 #ifndef LK_H
 #define LK_H
@@ -161,8 +163,15 @@ typedef struct {
   uint32_t op;      /* LK_OP_*                                            */
   uint32_t flags;   /* reserved, 0                                        */
   uint64_t n;       /* elements (ADD/COPY: int32, SUM: float32, HIST: bytes, GEMM: tiles) */
-  uint64_t aux;     /* reserved, 0                                        */
+  uint64_t aux;     /* load-rate cap of this descriptor in bytes per      */
+                    /* microsecond (= MB/s) over the whole cluster, at     */
+                    /* least LK_RATE_MIN; 0 = the cluster's default       */
+                    /* (lk_set_rate).  Paces ADD, COPY, SUM, HIST, GEMM    */
+                    /* and batches; other ops ignore it                   */
 } lk_desc;
+
+/* Smallest load-rate cap (bytes per microsecond = 1 GB/s). */
+#define LK_RATE_MIN 1000ull
 
 /* One execution-log record: one CTA's share of one descriptor. */
 typedef struct {
@@ -199,6 +208,16 @@ int lk_init(lk_ctx** out, const lk_init_params* p);
  * nothing was posted), LK_ESTATE (context not running). */
 int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in, int n_in,
               void* out, lk_handle* h);
+
+/* Not in the paper: cap the rate at which `cluster` loads its inputs, for
+ * isolation of the other clusters' memory traffic.  Each CTA paces its TMA
+ * loads with a token bucket as deep as its stage ring (the burst), so a
+ * cluster of S CTAs moves at most about bytes_per_us (MB/s) once past the
+ * burst; a paced body takes correspondingly longer.  Applies to
+ * descriptors posted after the call whose own lk_desc.aux is 0.
+ * bytes_per_us: 0 = unpaced, else >= LK_RATE_MIN and < 2^40.
+ * Errors: LK_EINVAL (ctx, cluster, rate). */
+int lk_set_rate(lk_ctx* ctx, int cluster, uint64_t bytes_per_us);
 
 /* Wait (Sec. III), non-blocking: LK_OK if h finished, LK_PENDING if not.
  * Errors: LK_EINVAL (bad handle), LK_EDEVICE (the cluster stopped on a device

@@ -73,6 +73,24 @@ struct SmemCfg {
   static_assert(gemm_stages <= LK_NUM_BARS, "one mbarrier per stage");
 };
 
+/* Time limits of one body.  Every staging wait ends by `deadline`.  A
+ * non-zero `rate` (bytes per microsecond for this CTA) paces the TMA loads:
+ * a token bucket as deep as the stage ring, so the first stages load at once
+ * and each later one no earlier than its bytes allow; the deadline then
+ * moves out by the paced duration of the CTA's share. */
+struct Pace {
+  uint64_t deadline;
+  uint64_t rate;
+};
+
+/* Thread 0: sleep until `due` (%globaltimer ns); bounded by `due` itself. */
+__device__ __forceinline__ void sleep_until(uint64_t due) {
+  for (uint64_t now = gtime(); now < due; now = gtime()) {
+    const uint64_t left = due - now;
+    __nanosleep(left > 2000u ? 2000u : (uint32_t)left);
+  }
+}
+
 /* Stream the 16-byte vectors [beg, end) of NIN inputs through the stages.
  * consume(v0, nv, s0, s1) runs on every thread for each chunk: vectors
  * v0 .. v0+nv-1 of the share sit at s0[0..nv) (and s1[0..nv) for a second
@@ -80,15 +98,18 @@ struct SmemCfg {
  * and a stage is refilled only after those stores have read it.  `phase`
  * holds one parity bit per mbarrier and persists across descriptors.
  * Returns false, on every thread alike, if a stage did not arrive before
- * `deadline`; this CTA's copies in flight are allowed to land first. */
+ * the deadline; this CTA's copies in flight are allowed to land first. */
 template <int NIN, bool STORE, int P, class F>
 __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint64_t beg, uint64_t end,
-                                       unsigned char* stage_mem, uint64_t* bars, uint32_t& phase, uint64_t deadline,
+                                       unsigned char* stage_mem, uint64_t* bars, uint32_t& phase, Pace pace,
                                        F&& consume) {
   constexpr uint32_t stage_vec = SmemCfg<P>::stream_bytes / LK_STAGES / NIN / 16u;   /* vectors per input per chunk */
   const uint64_t total = end > beg ? end - beg : 0;
   const uint64_t nch = (total + stage_vec - 1) / stage_vec;
   if (nch == 0) return true;
+  constexpr uint64_t chunk_bytes = (uint64_t)stage_vec * 16u * NIN;
+  const uint64_t deadline = pace.rate ? pace.deadline + total * 16u * NIN * 1000u / pace.rate : pace.deadline;
+  const uint64_t t_first = pace.rate && threadIdx.x == 0 ? gtime() : 0;
   auto sbuf = [&](uint32_t st, int which) {
     return reinterpret_cast<uint4*>(stage_mem + ((size_t)st * NIN + which) * stage_vec * 16u);
   };
@@ -122,6 +143,7 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
     phase ^= 1u << st;
     /* every thread has finished chunk ch-1: refill its stage */
     if (threadIdx.x == 0 && ch >= 1 && ch - 1 + LK_STAGES < nch) {
+      if (pace.rate) sleep_until(t_first + ch * chunk_bytes * 1000u / pace.rate);
       if (STORE) bulk_wait_read_all();
       fence_proxy_async_smem();
       issue(ch - 1 + LK_STAGES);
@@ -141,14 +163,14 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
 /* ---- int32 add / copy -------------------------------------------------- */
 template <int P>
 __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                         uint32_t& phase, uint64_t deadline) {
+                                         uint32_t& phase, Pace pace) {
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   int4* o = reinterpret_cast<int4*>(d.out);
   const uint32_t T = blockDim.x;
   const bool ok = stream<2, false, P>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
-                                   beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase, deadline,
+                                   beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase, pace,
                                    [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
                                      const int4* a = reinterpret_cast<const int4*>(s0);
                                      const int4* b = reinterpret_cast<const int4*>(s1);
@@ -165,13 +187,13 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
 
 template <int P>
 __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                          uint32_t& phase, uint64_t deadline) {
+                                          uint32_t& phase, Pace pace) {
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   uint4* o = reinterpret_cast<uint4*>(d.out);
   const bool ok = stream<1, true, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars,
-                                  phase, deadline, [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4*) {
+                                  phase, pace, [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4*) {
                                     if (threadIdx.x == 0) {
                                       bulk_s2g(o + v0, s0, cnt * 16u);
                                       bulk_commit();
@@ -188,14 +210,14 @@ __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsign
 /* ---- float32 sum: this CTA's partial (valid in thread 0) ---------------- */
 template <int P>
 __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                         uint32_t& phase, uint64_t deadline, float* red, float* partial_out) {
+                                         uint32_t& phase, Pace pace, float* red, float* partial_out) {
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
   const uint32_t T = blockDim.x;
   float acc0 = 0.f, acc1 = 0.f;
   const bool ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes,
-                                   bars, phase, deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                                   bars, phase, pace, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                                      const float4* x = reinterpret_cast<const float4*>(s0);
                                      uint32_t v = threadIdx.x;
                                      for (; v + T < cnt; v += 2 * T) {
@@ -289,7 +311,7 @@ __device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
 
 template <int P>
 __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                          uint32_t& phase, uint64_t deadline, uint32_t* acc) {
+                                          uint32_t& phase, Pace pace, uint32_t* acc) {
   const uint64_t nv = d.n >> 4;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
@@ -303,7 +325,7 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
     __syncthreads();
     uint32_t* bins = sh + (threadIdx.x >> 5) * 256;
     ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase,
-                          deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                          pace, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                             for (uint32_t v = threadIdx.x; v < cnt; v += T) {
                               const uint4 q = s0[v];
                               count4_warp(bins, q.x);
@@ -334,7 +356,7 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   hist_zero(sh, copies * 4096u);
   __syncthreads();
   ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase,
-                        deadline, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
+                        pace, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                           const uint32_t per = (cnt + T - 1) / T;
                           if (since + per > limit) {   /* same decision on every thread */
                             __syncthreads();
@@ -440,11 +462,12 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
 /* Shared memory: SmemCfg<P>::gemm_stages stages of (A rows 16 KB, B tile
  * 16 KB) over the whole dynamic shared memory; one mbarrier per stage. */
 
-/* Returns false if a staging copy did not complete before `deadline`.
- * `phase` holds one parity bit per stage and persists across descriptors. */
+/* Returns false if a staging copy did not complete before the deadline.
+ * `phase` holds one parity bit per stage and persists across descriptors;
+ * `pace` paces the tile loads as in stream(). */
 template <bool FULL_UNROLL, int P>
 __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float* sm, uint64_t* bars,
-                                          uint32_t& phase, uint64_t deadline) {
+                                          uint32_t& phase, Pace pace) {
   const uint64_t tiles = d.n;
   const uint32_t U = gemm_row_split(tiles, S);
   const uint32_t rows = 64 / U;
@@ -456,6 +479,9 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   float* C = reinterpret_cast<float*>(d.out);
   const uint32_t T = blockDim.x;
   constexpr uint32_t nstages = SmemCfg<P>::gemm_stages;
+  const uint64_t unit_bytes = rows * 256u + 16384u;
+  const uint64_t deadline = pace.rate ? pace.deadline + (end - beg) * unit_bytes * 1000u / pace.rate : pace.deadline;
+  const uint64_t t_first = pace.rate && threadIdx.x == 0 ? gtime() : 0;
   auto issue = [&](uint64_t u) {   /* thread 0 */
     const uint32_t st = (uint32_t)((u - beg) % nstages);
     const uint64_t tile = u / U;
@@ -492,7 +518,10 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
       break;
     }
     /* every thread finished unit u-1: refill its stage with unit u-1+STAGES */
-    if (threadIdx.x == 0 && u > beg && u - 1 + nstages < end) issue(u - 1 + nstages);
+    if (threadIdx.x == 0 && u > beg && u - 1 + nstages < end) {
+      if (pace.rate) sleep_until(t_first + (u - beg) * unit_bytes * 1000u / pace.rate);
+      issue(u - 1 + nstages);
+    }
     /* the phase is complete: this wait returns at once and makes the copied
      * bytes visible to this thread */
     mbar_wait(&bars[st], (phase >> st) & 1u, deadline + 1000000000ull);

@@ -303,16 +303,27 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
   }
 }
 
+/* Per-CTA pace of a descriptor whose `aux` caps the cluster's load rate
+ * (bytes per microsecond over its S CTAs; 0 = none). */
+__device__ __forceinline__ uint64_t cta_rate(uint64_t cluster_rate, int S) {
+  if (!cluster_rate) return 0;
+  const uint64_t r = cluster_rate / (uint64_t)S;
+  return r ? r : 1;
+}
+
 /* This CTA's share of descriptor d (rank r of S).  Returns an LK_DERR_* code
  * or 0.  `partial_out` receives the sum body's per-CTA partial.  MAXT (the
  * largest block size of the calling kernel) sets how far the GEMM's k loop is
  * unrolled: fully at up to 256 threads with one CTA per SM, where the
- * registers allow it.  P (CTAs per SM) sets the shared-memory budget. */
+ * registers allow it.  P (CTAs per SM) sets the shared-memory budget.
+ * `rate` (bytes per microsecond for this CTA, 0 = unpaced) paces the loads
+ * of the streaming and GEMM bodies. */
 template <int MAXT, int P>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                        uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc) {
+                                        uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc,
+                                        uint64_t rate) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  const uint64_t deadline = gtime() + 2000000000ull;
+  const Pace deadline{gtime() + 2000000000ull, rate};
   bool ok = true;
   switch (op) {
     case LK_OP_ADD_I32: ok = body_add<P>(d, r, S, dsm, bars, phase, deadline); break;
@@ -349,6 +360,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
   uint32_t* my_hist = a.cta_hist + (size_t)(a.cl_start[c] + r) * 256u;
   const lk_unit* units = reinterpret_cast<const lk_unit*>(d.in0);
   const uint64_t nunits = d.n;
+  const uint64_t rate = cta_rate(d.aux, a.cl_start[c + 1] - a.cl_start[c]);
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned long long u = atomicAdd(&bc->ticket, 1ull);
@@ -376,7 +388,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
     it.out = s_unit[2];
     it.aux = 0;
     it.t_pick = 0;
-    const uint64_t deadline = gtime() + 2000000000ull;
+    const Pace deadline{gtime() + 2000000000ull, rate};
     bool ok = true;
     if (op == LK_OP_SUM_F32) {
       float* pout = parts > 1 ? &bc->sums[comb - 1].partial[part] : &s_part;
@@ -414,7 +426,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
         if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
       }
     } else {
-      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr);
+      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate);
       ok = (e == 0);
     }
     __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
@@ -588,7 +600,8 @@ __global__ void __launch_bounds__(MAXT, P) lk_persistent(const lk_kargs a) {
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
     const int berr = op == LK_OP_BATCH ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
-                                       : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot]);
+                                       : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r],
+                                                           dc->hist[slot], cta_rate(d.aux, S));
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -680,7 +693,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist);
+  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist, 0);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -82,6 +82,8 @@ struct lk_ctx {
   lk_mbox* mbox_h = nullptr;     /* [C] host-mapped to_GPU mailboxes */
   Tail* rearmed = nullptr;       /* [C] descriptors whose FINISHED the host consumed */
 
+  Tail* rate = nullptr;          /* [C] default load-rate cap (bytes/us), 0 = none */
+
   /* batches: per cluster LK_BATCH_BUFFERS unit tables in host-mapped memory */
   uint32_t max_units = 0;
   lk_unit* units_h = nullptr;    /* [C][LK_BATCH_BUFFERS][max_units] */
@@ -131,7 +133,7 @@ static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in
   int need = op_inputs(d->op);
   if (need < 0 || n_in != need) return LK_EINVAL;
   if (d->flags != 0) return LK_EINVAL;
-  if (d->n > (1ull << 40) || d->aux > LK_LOW48) return LK_EINVAL;
+  if (d->n > (1ull << 40) || d->aux >= (1ull << 40) || (d->aux != 0 && d->aux < LK_RATE_MIN)) return LK_EINVAL;
   const void* ins[2] = {in0, in1};
   for (int i = 0; i < need; ++i) {
     if (!aligned16(ins[i]) || (uintptr_t)ins[i] > LK_LOW48) return LK_EINVAL;
@@ -243,9 +245,16 @@ static int post_mailbox(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, cons
   return LK_OK;
 }
 
-/* Ticket + publish.  Returns LK_OK / LK_EAGAIN. */
+/* Ticket + publish.  Returns LK_OK / LK_EAGAIN.  A descriptor without its
+ * own rate cap carries the cluster's default (lk_set_rate) in `aux`. */
 static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
                 void* out, uint64_t* seq_out) {
+  lk_desc paced;
+  if (d && !d->aux) {
+    paced = *d;
+    paced.aux = ctx->rate[c].t.load(std::memory_order_relaxed);
+    d = &paced;
+  }
   if (ctx->mailbox) return post_mailbox(ctx, c, cmd, d, in0, in1, out, seq_out);
   Tail& tl = ctx->tail[c];
   uint64_t t = tl.t.load(std::memory_order_relaxed);
@@ -389,8 +398,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
 
   ctx->tail = new (std::nothrow) Tail[ctx->C];
   ctx->rearmed = new (std::nothrow) Tail[ctx->C];
+  ctx->rate = new (std::nothrow) Tail[ctx->C];
   ctx->batch = new (std::nothrow) lk_ctx::BatchState[ctx->C];
-  if (!ctx->tail || !ctx->rearmed || !ctx->batch) return LK_ENOMEM;
+  if (!ctx->tail || !ctx->rearmed || !ctx->rate || !ctx->batch) return LK_ENOMEM;
   return LK_OK;
 }
 
@@ -400,6 +410,7 @@ static void teardown(lk_ctx* ctx) {
   if (ctx->mapped_h) lkb_free_mapped(ctx->mapped_h);
   delete[] ctx->tail;
   delete[] ctx->rearmed;
+  delete[] ctx->rate;
   delete[] ctx->batch;
   delete ctx;
 }
@@ -508,6 +519,13 @@ int lk_poll(lk_ctx* ctx, lk_handle h) {
   if (decode(ctx, h, &c, &s) != LK_OK) return LK_EINVAL;
   beat(ctx);
   return poll_seq(ctx, c, s);
+}
+
+int lk_set_rate(lk_ctx* ctx, int cluster, uint64_t bytes_per_us) {
+  if (!ctx || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
+  if (bytes_per_us >= (1ull << 40) || (bytes_per_us != 0 && bytes_per_us < LK_RATE_MIN)) return LK_EINVAL;
+  ctx->rate[cluster].t.store(bytes_per_us, std::memory_order_relaxed);
+  return LK_OK;
 }
 
 int lk_heartbeat(lk_ctx* ctx) {

@@ -27,6 +27,7 @@ LK_ST_INIT, LK_ST_FINISHED, LK_ST_WORKING, LK_ST_NOP, LK_ST_EXITED, LK_ST_ERROR 
 LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
 LK_INIT_DIRECT = 1
 LK_INIT_MAILBOX = 2
+LK_RATE_MIN = 1000
 LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
 LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7
 LK_OP_SPIN = 8
@@ -122,6 +123,7 @@ def load(fake: bool = False) -> ctypes.CDLL:
             "lk_wait": (I, [P, U64, U64]),
             "lk_sync": (I, [P, U64]),
             "lk_heartbeat": (I, [P]),
+            "lk_set_rate": (I, [P, I, U64]),
             "lk_dispose": (I, [P, U64]),
             "lk_dispose_timed": (I, [P, U64, ctypes.POINTER(ctypes.c_float)]),
             "lk_cluster_info": (I, [P, I, ctypes.POINTER(I), I]),
@@ -257,6 +259,13 @@ def lk_sync(ctx: Context, timeout_ns: int = 10_000_000_000) -> int:
 
 def lk_heartbeat(ctx: Context) -> int:
     return ctx.lib.lk_heartbeat(ctx.ptr)
+
+
+def lk_set_rate(ctx: Context, cluster: int, bytes_per_us: int) -> None:
+    """Default load-rate cap of `cluster` (bytes per microsecond; 0 = none)."""
+    rc = ctx.lib.lk_set_rate(ctx.ptr, cluster, bytes_per_us)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_set_rate")
 
 
 def lk_dispose(ctx: Context, timeout_ns: int = 20_000_000_000) -> int:

@@ -520,3 +520,22 @@ def test_two_ctas_per_sm_rejects(fake_env, kw):
     with pytest.raises(lk.LkError) as e:
         ctx_(sizes=sizes, **kw)
     assert e.value.code == lk.LK_EINVAL
+
+
+# ---- load-rate caps (lk_set_rate, lk_desc.aux) --------------------------------------
+def test_rate_caps_are_checked(fake_env):
+    with ctx_() as c:
+        lk.lk_set_rate(c, 0, 0)
+        lk.lk_set_rate(c, 1, lk.LK_RATE_MIN)
+        for bad in (1, lk.LK_RATE_MIN - 1, 1 << 40):
+            with pytest.raises(lk.LkError) as e:
+                lk.lk_set_rate(c, 0, bad)
+            assert e.value.code == lk.LK_EINVAL
+        with pytest.raises(lk.LkError) as e:
+            lk.lk_set_rate(c, 2, 5000)       # no such cluster
+        assert e.value.code == lk.LK_EINVAL
+        with pytest.raises(lk.LkError) as e:
+            lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 64, (A,), A, aux=999)
+        assert e.value.code == lk.LK_EINVAL
+        h = lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 64, (A,), A, aux=5000)
+        assert lk.lk_wait(c, h) == lk.LK_OK
