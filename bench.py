@@ -648,9 +648,9 @@ def main():
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM))
     add = bw["add_i32"]
-    traffic = profiled_traffic("lk_persistent_add_i32_2p28.txt")
-    roofline = {"kernel": f"lk_persistent<256> finite mode, add_i32 n=2^28 x{add['descriptors_per_launch']} "
-                          f"per launch, {n_sms} SMs as one cluster",
+    traffic = profiled_traffic("lk_finite_add_i32_2p28.txt")
+    roofline = {"kernel": f"lk_finite (the persistent kernel, 256 threads, in finite mode), add_i32 n=2^28 "
+                          f"x{add['descriptors_per_launch']} per launch, {n_sms} SMs as one cluster",
                 "bound": "hbm", "achieved": add["gbs"], "peak": hbm, "unit": "GB/s", "frac": add["gbs"] / hbm,
                 "peak_source": f"{peak_src} (hbm_gbs, burst copy)", "traffic": traffic,
                 "algorithmic_bytes_per_launch": add["bytes_per_launch"]}

@@ -59,7 +59,7 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 #define LK_SMEM_DYN (LK_SMEM_WORK + LK_SMEM_STREAM)
 #define LK_STAGES 4u
 #define LK_GEMM_STAGE_FLOATS 8192u     /* one GEMM stage: A rows 16 KB + B tile 16 KB */
-#define LK_HIST_COPIES 4u              /* lane-private counter copies (16 KB each), P = 1 */
+#define LK_HIST_COPIES 2u              /* lane-private counter copies (32 KB each), P = 1 */
 #define LK_NUM_BARS 6u                 /* mbarriers: one per stage                */
 
 template <int P>
@@ -275,33 +275,33 @@ __device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
   asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
 }
 
-/* Lane-private counters: word ((v & 127) << 5) | lane of a copy holds bin v
- * (low 16 bits if v < 128, high 16 bits otherwise) for this lane alone; lane
- * l only touches bank l. */
-__device__ __forceinline__ void count4_lane(uint32_t* lane_base, uint32_t w) {
+/* Lane-private counters: word (v << 5) | lane of a copy (8192 words, 32 KB)
+ * counts bin v for this lane alone, so lane l only touches bank l, and one
+ * byte costs an extract, an address and one shared reduction.  32-bit
+ * counters cannot overflow: a share holds fewer than 2^31 bytes. */
+__device__ __forceinline__ void count4_lane(uint32_t lane_addr, uint32_t w) {
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const uint32_t v = (w >> (8 * b)) & 0xffu;
-    red_add_shared(lane_base + ((v & 127u) << 5), 1u << ((v >> 7) << 4));
+    asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + (v << 7)) : "memory");
   }
 }
 
-/* Add the lane-private counters into tot_lo / tot_hi (rows owned by threads
- * < 128: bin `row` and bin `row + 128`).  A warp's loads start at
- * row-dependent columns so they spread over all banks. */
+/* Thread v (< 256) adds bin v over the 32 lanes of every copy.  The loads of
+ * a row start at thread-dependent columns, so each 8-thread phase of a
+ * 128-bit warp load touches all 32 banks once. */
 template <int P>
-__device__ __forceinline__ void hist_readout(const uint32_t* sh, uint32_t& tot_lo, uint32_t& tot_hi) {
-  for (uint32_t row = threadIdx.x; row < 128; row += blockDim.x) {
-    for (uint32_t c = 0; c < SmemCfg<P>::hist_copies; ++c) {
-      const uint4* rw = reinterpret_cast<const uint4*>(sh + c * 4096u + row * 32u);
+__device__ __forceinline__ uint32_t hist_readout(const uint32_t* sh, uint32_t v) {
+  uint32_t tot = 0;
+  for (uint32_t c = 0; c < SmemCfg<P>::hist_copies; ++c) {
+    const uint4* rw = reinterpret_cast<const uint4*>(sh + c * 8192u + v * 32u);
 #pragma unroll
-      for (uint32_t j = 0; j < 8; ++j) {
-        const uint4 q = rw[(j + row) & 7u];
-        tot_lo += (q.x & 0xffffu) + (q.y & 0xffffu) + (q.z & 0xffffu) + (q.w & 0xffffu);
-        tot_hi += (q.x >> 16) + (q.y >> 16) + (q.z >> 16) + (q.w >> 16);
-      }
+    for (uint32_t j = 0; j < 8; ++j) {
+      const uint4 q = rw[(j + v) & 7u];
+      tot += (q.x + q.y) + (q.z + q.w);
     }
   }
+  return tot;
 }
 
 __device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
@@ -344,47 +344,47 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
     }
     return ok;
   }
-  /* large share: lane-private packed 16-bit counters.  A counter takes at
-   * most 65535 increments between read-outs; each lane word is shared by the
-   * ceil(W / copies) warps that use the same copy. */
+  /* large share: lane-private 32-bit counters, one set per copy; the
+   * W / copies warps of a copy share its words (their reductions to a word
+   * are atomic) */
   constexpr uint32_t copies = SmemCfg<P>::hist_copies;
   const uint32_t copy = (threadIdx.x >> 5) % copies;
-  uint32_t* lane_base = sh + copy * 4096u + lane;
-  const uint32_t sharers = (W + copies - 1) / copies;
-  const uint32_t limit = 65535u / sharers / 16u;   /* vectors per thread between read-outs */
-  uint32_t since = 0, tot_lo = 0, tot_hi = 0;
-  hist_zero(sh, copies * 4096u);
+  const uint32_t lane_addr = smem_addr(sh + copy * 8192u + lane);
+  hist_zero(sh, copies * 8192u);
   __syncthreads();
   ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase,
                         pace, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
-                          const uint32_t per = (cnt + T - 1) / T;
-                          if (since + per > limit) {   /* same decision on every thread */
-                            __syncthreads();
-                            hist_readout<P>(sh, tot_lo, tot_hi);
-                            __syncthreads();
-                            hist_zero(sh, copies * 4096u);
-                            __syncthreads();
-                            since = 0;
+                          /* four vectors loaded before their 64 reductions: the
+                           * reductions are ordered asm, so loads placed after
+                           * them would wait for them */
+                          uint32_t v = threadIdx.x;
+                          for (; v + 3 * T < cnt; v += 4 * T) {
+                            uint4 q[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) q[i] = s0[v + i * T];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                              count4_lane(lane_addr, q[i].x);
+                              count4_lane(lane_addr, q[i].y);
+                              count4_lane(lane_addr, q[i].z);
+                              count4_lane(lane_addr, q[i].w);
+                            }
                           }
-                          for (uint32_t v = threadIdx.x; v < cnt; v += T) {
+                          for (; v < cnt; v += T) {
                             const uint4 q = s0[v];
-                            count4_lane(lane_base, q.x);
-                            count4_lane(lane_base, q.y);
-                            count4_lane(lane_base, q.z);
-                            count4_lane(lane_base, q.w);
+                            count4_lane(lane_addr, q.x);
+                            count4_lane(lane_addr, q.y);
+                            count4_lane(lane_addr, q.z);
+                            count4_lane(lane_addr, q.w);
                           }
-                          since += per;
                         });
   if (tail)
-    for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T) {
-      const uint32_t v = xb[j];
-      red_add_shared(lane_base + ((v & 127u) << 5), 1u << ((v >> 7) << 4));
-    }
+    for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T)
+      asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + ((uint32_t)xb[j] << 7)) : "memory");
   __syncthreads();
-  hist_readout<P>(sh, tot_lo, tot_hi);
-  for (uint32_t row = threadIdx.x; row < 128; row += T) {
-    if (tot_lo) atomicAdd(&acc[row], tot_lo);
-    if (tot_hi) atomicAdd(&acc[row + 128], tot_hi);
+  for (uint32_t v = threadIdx.x; v < 256; v += T) {
+    const uint32_t tot = hist_readout<P>(sh, v);
+    if (tot) atomicAdd(&acc[v], tot);
   }
   return ok;
 }

@@ -436,7 +436,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
 }
 
 template <int MAXT, int P>
-__global__ void __launch_bounds__(MAXT, P) lk_persistent(const lk_kargs a) {
+__device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(64) lk_slot s_desc;
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
@@ -670,6 +670,17 @@ __global__ void __launch_bounds__(MAXT, P) lk_persistent(const lk_kargs a) {
   }
 }
 
+/* The persistent kernel (live contexts: lk_init). */
+template <int MAXT, int P>
+__global__ void __launch_bounds__(MAXT, P) lk_persistent(const lk_kargs a) {
+  persistent_main<MAXT, P>(a);
+}
+
+/* The same kernel under another name for finite mode (lk_run_finite, 256
+ * threads, one CTA per SM), so that a profiler can select its launches
+ * apart from live contexts, which wait on the host and cannot be replayed. */
+__global__ void __launch_bounds__(256, 1) lk_finite(const lk_kargs a) { persistent_main<256, 1>(a); }
+
 /* ---- ordinary-launch baseline: the same bodies, one launch per item ------ */
 struct lk_scratch {
   uint32_t counter;
@@ -739,6 +750,7 @@ void preload_all() {
     cudaFuncAttributes fa;
     const void* fns[] = {(const void*)lk_persistent<256, 1>,  (const void*)lk_persistent<512, 1>,
                          (const void*)lk_persistent<1024, 1>, (const void*)lk_persistent<256, 2>,
+                         (const void*)lk_finite,
                          (const void*)lk_ordinary<256>,
                          (const void*)lk_ordinary<512>,    (const void*)lk_ordinary<1024>,
                          (const void*)lk_pingpong_kernel};
@@ -756,7 +768,8 @@ void preload_all() {
   });
 }
 
-const void* persistent_fn(int threads, int per_sm) {
+const void* persistent_fn(int threads, int per_sm, bool finite) {
+  if (finite && per_sm == 1 && threads <= 256) return (const void*)lk_finite;
   if (per_sm == 2) return threads <= 256 ? (const void*)lk_persistent<256, 2> : nullptr;
   if (threads <= 256) return (const void*)lk_persistent<256, 1>;
   if (threads <= 512) return (const void*)lk_persistent<512, 1>;
@@ -926,7 +939,7 @@ int lkb_launch_kernel(int device, const lk_kargs* a, int threads, lkb_launch** o
   cudaDeviceProp p;
   if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return LK_EDEVICE;
   const int want = a->ctas_per_sm == 2 ? 2 : 1;
-  const void* fn = persistent_fn(threads, want);
+  const void* fn = persistent_fn(threads, want, (a->flags & LK_KFLAG_FINITE) != 0);
   if (!fn) return LK_EINVAL;
   /* exactly `want` CTAs per SM: ask for more than 1/(want+1) of the SM's
    * shared memory (one CTA: more than half; two: more than a third) */

@@ -173,6 +173,7 @@ typedef struct __attribute__((aligned(LK_LINE))) {
 /* Everything the persistent kernel needs; passed by value at launch. */
 #define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
 #define LK_KFLAG_MAILBOX 2u      /* the master takes work from lk_mbox, not the ring   */
+#define LK_KFLAG_FINITE 4u       /* finite mode: ring pre-filled in device memory      */
 
 typedef struct {
   lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */

@@ -390,6 +390,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.log_cap = ctx->log_cap;
   a.flags = ((p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u) | (ctx->mailbox ? LK_KFLAG_MAILBOX : 0u);
   a.ctas_per_sm = ctx->per_sm;
+  if (!live) a.flags |= LK_KFLAG_FINITE;
   a.backoff_base_ns = p->backoff_base_ns;
   a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;
   a.lease_ns = p->idle_lease_ns ? p->idle_lease_ns : 10000000000ull;
