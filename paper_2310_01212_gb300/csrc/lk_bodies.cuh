@@ -60,7 +60,7 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 #define LK_STAGES 4u
 #define LK_GEMM_STAGE_FLOATS 8192u     /* one GEMM stage: A rows 16 KB + B tile 16 KB */
 #define LK_HIST_COPIES 2u              /* lane-private counter copies (32 KB each), P = 1 */
-#define LK_NUM_BARS 6u                 /* mbarriers: one per stage                */
+#define LK_NUM_BARS 8u                 /* mbarriers: one per stage; two for MMA completion */
 
 template <int P>
 struct SmemCfg {
@@ -462,14 +462,273 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
 /* Shared memory: SmemCfg<P>::gemm_stages stages of (A rows 16 KB, B tile
  * 16 KB) over the whole dynamic shared memory; one mbarrier per stage. */
 
+/* ---- the GEMM tile on the 5th-generation tensor cores ------------------- */
+/* C = A B for whole 64x64x64 float32 tiles, with tcgen05.mma kind::tf32
+ * (tensor-core products of 19-bit floats, float32 accumulation in TMEM).
+ * One TF32 product per element pair would miss the 1e-4 sum|a b| bound, so
+ * every operand is split: x = x_hi + x_lo with x_hi = x truncated to TF32 and
+ * x_lo = x - x_hi (exact).  The A operand stacks A_hi (rows 0-63) on A_lo
+ * (rows 64-127) and the B operand B_hi (columns 0-63) on B_lo (64-127), so
+ * one chain of eight MMAs over K (M = 128, N = 128; TMEM rows are lanes
+ * 0-127, one to one) yields all four products in a 128 x 128 block D, and
+ * C[r][n] = D[r][n] + D[r][n+64] + D[r+64][n] + D[r+64][n+64] (the TF32
+ * truncation of x_lo inside the MMA leaves errors of order 2^-21 |a||b| per
+ * product).
+ * Two pipelines, one per half of the CTA (warps 0-3 and 4-7, each with its
+ * own operand buffer, TMEM block and named barrier), take alternate tiles:
+ * while one half waits for its MMAs and stores its tile, the other splits
+ * the next one.  The TMA stage ring is shared: tile u sits in stage
+ * (u - first) mod 3, and the half that split tile u refills that stage with
+ * tile u+3.
+ * Shared memory (224 KB): three 32 KB TMA stages of raw tiles (A rows, B) at
+ * 0; two 64 KB operand buffers at 96 KB (A_hi, A_lo, B_hi, B_lo, 16 KB each,
+ * in the K-major core-matrix layout the descriptors name).  TMEM: two blocks
+ * of 128 columns, allocated for the body and freed on every path out of it. */
+#define LK_TC_SMEM (224u * 1024u)
+#define LK_TC_STAGES 3u
+#define LK_TC_MMA_BAR 6u             /* bars 6 and 7: MMA completion of halves 0 and 1 */
+#define LK_TC_OPS (96u * 1024u)
+/* instruction descriptor: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9,
+ * 10-12 = 2), both K-major, N = 128 (bits 17-22 = N/8), M = 128 (bits 24-28 = M/16) */
+#define LK_TC_IDESC ((1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
+
+__device__ __forceinline__ float4 tf32_hi(float4 x) {
+  return make_float4(__uint_as_float(__float_as_uint(x.x) & 0xffffe000u), __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
+                     __uint_as_float(__float_as_uint(x.z) & 0xffffe000u), __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+/* Column e of the 4x4 block q[0..3] (rows k..k+3): the K-chunk of output column n = 4 n4 + e. */
+__device__ __forceinline__ float4 column_of(const float4* q, uint32_t e) {
+  float4 v;
+  v.x = e == 0 ? q[0].x : e == 1 ? q[0].y : e == 2 ? q[0].z : q[0].w;
+  v.y = e == 0 ? q[1].x : e == 1 ? q[1].y : e == 2 ? q[1].z : q[1].w;
+  v.z = e == 0 ? q[2].x : e == 1 ? q[2].y : e == 2 ? q[2].z : q[2].w;
+  v.w = e == 0 ? q[3].x : e == 1 ? q[3].y : e == 2 ? q[3].z : q[3].w;
+  return v;
+}
+
+/* The 128 threads of one half (local index t): split the staged raw tile
+ * (A rows at `raw`, B at raw + 16 KB) into an operand buffer.  The
+ * core-matrix offset of (row i, K-chunk k4) is (i/8) 2048 + k4 128 + (i%8) 16
+ * bytes.  The thread-to-chunk maps make each 8-thread phase of a 128-bit
+ * access touch eight distinct 16-byte bank groups, on the raw side and on
+ * the operand side. */
+__device__ __forceinline__ void tc_split(const unsigned char* raw, unsigned char* ops, uint32_t t) {
+#pragma unroll
+  for (uint32_t q = 0; q < 8; ++q) {                 /* A: 1024 chunks of 4 floats */
+    const uint32_t c = t + 128u * q;
+    const uint32_t j = c & 7u, s = (c >> 3) & 7u, h = (c >> 6) & 1u, ig = c >> 7;
+    const uint32_t i = ig * 8u + j, k4 = ((j + s) & 7u) + 8u * h;
+    const float4 x = *reinterpret_cast<const float4*>(raw + i * 256u + k4 * 16u);
+    const float4 hi = tf32_hi(x);
+    const uint32_t off = ig * 2048u + k4 * 128u + j * 16u;
+    *reinterpret_cast<float4*>(ops + off) = hi;                        /* A_hi */
+    *reinterpret_cast<float4*>(ops + 16384u + off) = sub4(x, hi);      /* A_lo */
+  }
+#pragma unroll
+  for (uint32_t q = 0; q < 2; ++q) {                 /* B: 256 blocks of 4 k x 4 n, transposed */
+    const uint32_t blk = t + 128u * q, n4 = blk & 15u, kb = blk >> 4;
+    const unsigned char* rb = raw + 16384u;
+    float4 v[4];
+#pragma unroll
+    for (uint32_t m = 0; m < 4; ++m) v[m] = *reinterpret_cast<const float4*>(rb + (4u * kb + m) * 256u + n4 * 16u);
+#pragma unroll
+    for (uint32_t te = 0; te < 4; ++te) {
+      const uint32_t e = (te + (n4 >> 1)) & 3u;      /* rotated: distinct bank groups per phase */
+      const uint32_t n = 4u * n4 + e;
+      const float4 x = column_of(v, e);
+      const float4 hi = tf32_hi(x);
+      const uint32_t off = (n >> 3) * 2048u + kb * 128u + (n & 7u) * 16u;
+      *reinterpret_cast<float4*>(ops + 32768u + off) = hi;               /* B_hi */
+      *reinterpret_cast<float4*>(ops + 49152u + off) = sub4(x, hi);      /* B_lo */
+    }
+  }
+}
+
+/* Barrier of one half (named barrier 1 or 2, 128 threads); the _and form
+ * also returns the AND of every participant's `v`, so that all 128 threads
+ * take the same branch afterwards. */
+__device__ __forceinline__ void half_sync(uint32_t h) { asm volatile("bar.sync %0, 128;" ::"r"(1u + h) : "memory"); }
+__device__ __forceinline__ bool half_sync_and(uint32_t h, bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, %2, 128, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(out)
+      : "r"((uint32_t)v), "r"(1u + h)
+      : "memory");
+  return out != 0;
+}
+
+__device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
+                                             uint32_t& phase, Pace pace) {
+  uint64_t beg, end;
+  share(d.n, r, S, beg, end);
+  if (beg >= end) return true;
+  const float* A = reinterpret_cast<const float*>(d.in0);
+  const float* B = reinterpret_cast<const float*>(d.in1);
+  float* C = reinterpret_cast<float*>(d.out);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t h = warp >> 2, lt = threadIdx.x & 127u;   /* half, index within it */
+  const bool leader = lt == 0;
+  const uint64_t tiles = end - beg;
+  constexpr uint64_t unit_bytes = 32768u;
+  const uint64_t deadline = pace.rate ? pace.deadline + tiles * unit_bytes * 1000u / pace.rate : pace.deadline;
+  const uint64_t t_first = pace.rate ? gtime() : 0;
+  auto issue = [&](uint64_t u) {   /* a half's leader, or thread 0 at the start */
+    const uint32_t st = (uint32_t)((u - beg) % LK_TC_STAGES);
+    unsigned char* sa = dsm + st * 32768u;
+    fence_proxy_async_smem();
+    mbar_expect_tx(&bars[st], 32768u);
+    bulk_g2s(sa, A + u * 4096, 16384u, &bars[st]);
+    bulk_g2s(sa + 16384u, B + u * 4096, 16384u, &bars[st]);
+  };
+  /* parity of a barrier's k-th completion in this body, from its bit at entry */
+  const uint32_t phase0 = phase;
+  auto parity = [&](uint32_t bar, uint64_t k) { return ((phase0 >> bar) & 1u) ^ (uint32_t)(k & 1u); };
+  __shared__ uint32_t s_tmem;
+  /* loads issued into each stage so far: a parity wait is only sound one
+   * phase ahead, so a half waits for a stage's next load to be issued (by
+   * the other half, once it consumed the stage's previous tile) before it
+   * waits for that load's phase */
+  __shared__ uint32_t s_issued[LK_TC_STAGES];
+  __syncthreads();          /* every stage is free: the previous use ended with a barrier */
+  if (warp == 0) tmem_alloc(&s_tmem, 256);
+  if (threadIdx.x == 0) {
+    for (uint32_t sb = 0; sb < LK_TC_STAGES; ++sb) s_issued[sb] = 0;
+    for (uint64_t u = beg; u < end && u < beg + LK_TC_STAGES; ++u) {
+      issue(u);
+      s_issued[u - beg] = 1;
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t dt = s_tmem + 128u * h;
+  unsigned char* ops = dsm + LK_TC_OPS + h * 65536u;
+  const uint32_t ah = smem_addr(ops), bh = ah + 32768u;
+  /* epilogue: warp quarter q holds D rows 32q..32q+31 (rows 64-127 are the
+   * A_lo products of output rows 0-63) */
+  const uint32_t quarter = warp & 3u;
+  const uint32_t drow = 32u * quarter + lane;
+  bool ok = true;
+  uint64_t k = 0;                  /* tiles this half has finished */
+  for (uint64_t u = beg + h; u < end; u += 2, ++k) {
+    const uint32_t st = (uint32_t)((u - beg) % LK_TC_STAGES);
+    const uint64_t use = (u - beg) / LK_TC_STAGES;   /* completions of stage st before this one */
+    bool go = true;
+    if (leader) {
+      const volatile uint32_t* iss = s_issued;
+      for (uint32_t it = 0; iss[st] < use + 1; ++it)
+        if ((it & 15) == 15 && gtime() > deadline) {
+          go = false;
+          break;
+        }
+      __threadfence_block();
+      if (go) {
+        go = mbar_wait(&bars[st], parity(st, use), deadline);
+        if (!go) mbar_wait(&bars[st], parity(st, use), deadline + 1000000000ull);   /* let it land */
+      }
+    }
+    if (!half_sync_and(h, go)) {
+      ok = false;
+      break;
+    }
+    mbar_wait(&bars[st], parity(st, use), deadline + 1000000000ull);   /* complete: visibility */
+    tc_split(dsm + st * 32768u, ops, lt);
+    fence_proxy_async_smem();       /* the operands, written by threads, are read by the tensor core */
+    tc_fence_before_sync();
+    half_sync(h);
+    if (leader) {
+      /* this half has split tile u: its stage takes tile u+3 */
+      if (u + LK_TC_STAGES < end) {
+        if (pace.rate) sleep_until(t_first + (u + 1 - beg) * unit_bytes * 1000u / pace.rate);
+        issue(u + LK_TC_STAGES);
+        __threadfence_block();
+        atomicAdd(&s_issued[st], 1u);
+      }
+      tc_fence_after_sync();
+#pragma unroll
+      for (uint32_t j = 0; j < 8; ++j)
+        umma_tf32(dt, umma_desc(ah + 256u * j, 128u, 2048u), umma_desc(bh + 256u * j, 128u, 2048u), LK_TC_IDESC, j > 0);
+      umma_commit(&bars[LK_TC_MMA_BAR + h]);
+    }
+    /* epilogue: every warp folds its rows' column halves (B_hi and B_lo
+     * products) and parks them in the operand buffer, free once the MMAs
+     * completed: rows 0-63 at `part`, rows 64-127 at part + 64 x 68 (rows
+     * padded to 68 floats: no bank conflicts); then the 128 threads add the
+     * two parts and store the tile in coalesced 128-bit stores */
+    float* part = reinterpret_cast<float*>(ops);
+    bool done = mbar_wait(&bars[LK_TC_MMA_BAR + h], parity(LK_TC_MMA_BAR + h, k), deadline + 1000000000ull);
+    if (done) {
+      tc_fence_after_sync();
+      float* prow = part + drow * 68u;
+#pragma unroll
+      for (uint32_t c0 = 0; c0 < 64; c0 += 32) {
+        float v[32], w[32];
+        tmem_ld32(dt + ((32u * quarter) << 16) + c0, v);
+        tmem_ld32(dt + ((32u * quarter) << 16) + c0 + 64u, w);
+#pragma unroll
+        for (uint32_t c = 0; c < 32; c += 4)
+          *reinterpret_cast<float4*>(prow + c0 + c) = make_float4(v[c] + w[c], v[c + 1] + w[c + 1], v[c + 2] + w[c + 2], v[c + 3] + w[c + 3]);
+      }
+    }
+    tc_fence_before_sync();         /* these TMEM reads precede this half's next MMAs */
+    if (half_sync_and(h, done)) {
+      float* ct = C + u * 4096;
+#pragma unroll
+      for (uint32_t q = 0; q < 8; ++q) {
+        const uint32_t f = lt + 128u * q, i = f >> 4, c4 = f & 15u;
+        const float4 x = *reinterpret_cast<const float4*>(part + i * 68u + c4 * 4u);
+        const float4 y = *reinterpret_cast<const float4*>(part + (i + 64u) * 68u + c4 * 4u);
+        st_stream(reinterpret_cast<float4*>(ct + i * 64u + c4 * 4u), make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w));
+      }
+    } else {
+      done = false;
+    }
+    if (!half_sync_and(h, done)) {  /* the operand buffer and TMEM block are free again */
+      ok = false;
+      ++k;
+      break;
+    }
+  }
+  /* MMAs of a failed tile may still be in flight: let them finish (bounded)
+   * before TMEM is freed */
+  if (!ok && leader && k > 0)
+    mbar_wait(&bars[LK_TC_MMA_BAR + h], parity(LK_TC_MMA_BAR + h, k - 1), deadline + 2000000000ull);
+  tc_fence_before_sync();
+  __syncthreads();          /* both halves done: stages and operand buffers are free */
+  tc_fence_after_sync();
+  if (warp == 0) tmem_dealloc(s_tmem, 256);
+  /* every thread advances every barrier's phase bit by its completions here */
+  if (ok) {
+    for (uint32_t sb = 0; sb < LK_TC_STAGES; ++sb) {
+      const uint64_t uses = tiles > sb ? (tiles - sb + LK_TC_STAGES - 1) / LK_TC_STAGES : 0;
+      phase ^= (uint32_t)(uses & 1u) << sb;
+    }
+    for (uint32_t hh = 0; hh < 2; ++hh) {
+      const uint64_t mine = tiles > hh ? (tiles - hh + 1) / 2 : 0;
+      phase ^= (uint32_t)(mine & 1u) << (LK_TC_MMA_BAR + hh);
+    }
+  }
+  return ok;
+}
+
 /* Returns false if a staging copy did not complete before the deadline.
  * `phase` holds one parity bit per stage and persists across descriptors;
- * `pace` paces the tile loads as in stream(). */
+ * `pace` paces the tile loads as in stream().  Whole tiles at 256 threads
+ * with one CTA per SM run on the tensor cores (body_gemm_tc); row blocks of
+ * split tiles and other shapes take the FFMA path below. */
 template <bool FULL_UNROLL, int P>
 __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float* sm, uint64_t* bars,
                                           uint32_t& phase, Pace pace) {
   const uint64_t tiles = d.n;
   const uint32_t U = gemm_row_split(tiles, S);
+  if (P == 1 && U == 1 && blockDim.x == 256)
+    return body_gemm_tc(d, r, S, reinterpret_cast<unsigned char*>(sm), bars, phase, pace);
   const uint32_t rows = 64 / U;
   uint64_t beg, end;
   share(tiles * U, r, S, beg, end);
@@ -569,7 +828,7 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
 }
 
 /* Dynamic shared memory a CTA asks for when P CTAs share an SM. */
-__host__ __device__ constexpr uint32_t body_smem_bytes(int P) { return P == 2 ? SmemCfg<2>::dyn_bytes : SmemCfg<1>::dyn_bytes; }
+__host__ __device__ constexpr uint32_t body_smem_bytes(int P) { return P == 2 ? SmemCfg<2>::dyn_bytes : LK_TC_SMEM; }
 
 }  // namespace lk
 #endif

@@ -1011,7 +1011,7 @@ void pin_cpu(int cpu) {
 }
 cudaError_t launch_ordinary(const lk_slot& d, int grid, int threads, lk_scratch* sc, cudaStream_t s) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  const size_t smem = (op == LK_OP_NOP || op == LK_OP_SPIN) ? 0 : lk::body_smem_bytes(threads);
+  const size_t smem = (op == LK_OP_NOP || op == LK_OP_SPIN) ? 0 : lk::body_smem_bytes(1);
   if (threads <= 256) lk_ordinary<256><<<grid, threads, smem, s>>>(d, sc);
   else if (threads <= 512) lk_ordinary<512><<<grid, threads, smem, s>>>(d, sc);
   else lk_ordinary<1024><<<grid, threads, smem, s>>>(d, sc);

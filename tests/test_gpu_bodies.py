@@ -105,8 +105,14 @@ def test_gemm_tiles(torch_ready, oracle_lib, S, per_sm):
             assert lk.lk_wait(c, h) == lk.LK_OK
     for A, B, dA, dB, dC in cases:
         assert gemm_ok(host(dC), A, B, oracle_lib), A.shape
-    # identity tile: exact
-    assert np.array_equal(host(cases[-1][4]), B)
+    # identity tile: exact on the FFMA path (row blocks of split tiles, or two
+    # CTAs per SM); whole tiles with one CTA per SM run on the tensor cores,
+    # where B = B_hi + B_lo comes back with B_lo truncated to TF32 (|err| <= 2^-20 |b|)
+    got = host(cases[-1][4])
+    if per_sm == 1 and S <= 3:
+        assert np.all(np.abs(got - B) <= 2.0 ** -20 * np.abs(B)), np.max(np.abs(got - B) / np.abs(B))
+    else:
+        assert np.array_equal(got, B)
 
 
 def test_misaligned_pointers_rejected_on_host(torch_ready):
