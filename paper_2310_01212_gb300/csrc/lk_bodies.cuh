@@ -50,10 +50,12 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 }
 
 /* ---- shared-memory layout of a CTA ------------------------------------- */
-/* With one CTA per SM (P = 1) a CTA owns 192 KB: a 64 KB work region
- * (histogram counters) and a 128 KB ring of LK_STAGES streaming stages; the
- * GEMM stages span all of it.  With two CTAs per SM (P = 2) each CTA owns
- * half of every region, so the bytes in flight per SM stay the same. */
+/* With one CTA per SM (P = 1) the streaming bodies use 192 KB of the CTA's
+ * 224 KB: a 64 KB work region (histogram counters) and a 128 KB ring of
+ * LK_STAGES streaming stages; the FFMA GEMM's stages span those 192 KB and
+ * the tensor-core GEMM uses all 224 KB (LK_TC_SMEM).  With two CTAs per SM
+ * (P = 2) each CTA owns half of every region, so the bytes in flight per SM
+ * stay the same. */
 #define LK_SMEM_WORK (64u * 1024u)     /* histogram counters or GEMM stages   */
 #define LK_SMEM_STREAM (128u * 1024u)  /* streaming stages                    */
 #define LK_SMEM_DYN (LK_SMEM_WORK + LK_SMEM_STREAM)

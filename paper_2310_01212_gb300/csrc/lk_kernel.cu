@@ -10,13 +10,15 @@
  * given as explicit SM lists).  The paper's check that a block sits on the SM
  * it expects becomes a table built from the SM ids actually observed.
  *
- * Mailboxes (Sec. II.D, Table 1): each CTA's thread 0 polls its cluster's
- * host-mapped ring (or, with LK_INIT_RELAY, only rank 0 -- the paper's master
- * thread -- polls it and relays each descriptor through a device ring), and
- * every CTA runs its share.  Each CTA then release-stores its own finished
- * count; rank 0 gathers the counts, combines partial results and publishes
- * the descriptor's sequence number in the host-mapped `done` word
- * (from_GPU = THREAD_FINISHED).
+ * Mailboxes (Sec. II.D, Table 1): rank 0's thread 0 -- the paper's master
+ * thread -- polls its cluster's host-mapped ring and relays each descriptor
+ * through a device ring (with LK_INIT_DIRECT every CTA's thread 0 polls the
+ * ring itself; with LK_INIT_MAILBOX the master runs the paper's one-deep
+ * to_GPU / from_GPU handshake instead of the ring), and every CTA runs its
+ * share.  Each CTA then release-stores its own finished count; rank 0 gathers
+ * the counts, combines partial results and publishes the descriptor's
+ * sequence number in the host-mapped `done` word (from_GPU =
+ * THREAD_FINISHED; the status word itself in mailbox mode).
  *
  * Every device-side wait is bounded: by an idle lease (refreshed by the
  * host's heartbeat), by the host's abort word, and by a stall deadline.  On
@@ -168,7 +170,7 @@ __device__ __noinline__ int take_from_mailbox(const lk_kargs& a, int c, uint64_t
   return 0;
 }
 
-/* Relay (LK_INIT_RELAY): the master copies descriptor k into relay slot
+/* Relay (the default delivery): the master copies descriptor k into relay slot
  * k mod D as six lap-tagged words (the host ring's format, tag = relay lap),
  * after the acquire-release fence that followed its ring probe, so members
  * need no separate generation word: they probe the slot in L2 (one round
