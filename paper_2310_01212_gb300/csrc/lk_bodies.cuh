@@ -263,8 +263,10 @@ __device__ __forceinline__ void combine_sum(const lk_slot& d, const float* parti
 
 /* ---- uint8 histogram ---------------------------------------------------- */
 /* Shares below this many bytes per CTA use per-warp bins, whose set-up and
- * read-out are cheap; larger shares use the conflict-free lane-private path. */
-#define LK_HIST_SMALL_BYTES (64u * 1024u)
+ * read-out are cheap; larger shares use the conflict-free lane-private path
+ * (measured crossover on GB300: a 28 KB share counts in 2.5 us lane-private
+ * against 2.9 us in per-warp bins; a 7 KB share in 1.9 against 1.7 us). */
+#define LK_HIST_SMALL_BYTES (16u * 1024u)
 
 __device__ __forceinline__ void count4_warp(uint32_t* bins, uint32_t w) {
   atomicAdd(&bins[w & 0xffu], 1u);
