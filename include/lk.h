@@ -157,6 +157,12 @@ typedef struct {
  * the previous one has finished and its re-arm was acknowledged.  Cannot be
  * combined with LK_INIT_DIRECT (LK_EINVAL). */
 #define LK_INIT_MAILBOX 2u
+/* LK_INIT_GEMM_FFMA: GEMM tiles always take the float32 FFMA path (k-order
+ * fused multiply-adds, bit-reproducible).  Default: whole tiles at 256
+ * threads with one CTA per SM run on the tensor cores with split-TF32
+ * operands (each product's error of order 2^-21 |a||b|, inside the GEMM
+ * bound 1e-4 sum_k |a b|); tiles split across CTAs always take FFMA. */
+#define LK_INIT_GEMM_FFMA 4u
 
 /* A work descriptor.  The in/out pointers travel beside it. */
 typedef struct {

@@ -724,14 +724,15 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
 /* Returns false if a staging copy did not complete before the deadline.
  * `phase` holds one parity bit per stage and persists across descriptors;
  * `pace` paces the tile loads as in stream().  Whole tiles at 256 threads
- * with one CTA per SM run on the tensor cores (body_gemm_tc); row blocks of
- * split tiles and other shapes take the FFMA path below. */
+ * with one CTA per SM run on the tensor cores (body_gemm_tc) unless
+ * `tensor_cores` is false; row blocks of split tiles and other shapes take
+ * the FFMA path below. */
 template <bool FULL_UNROLL, int P>
 __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float* sm, uint64_t* bars,
-                                          uint32_t& phase, Pace pace) {
+                                          uint32_t& phase, Pace pace, bool tensor_cores) {
   const uint64_t tiles = d.n;
   const uint32_t U = gemm_row_split(tiles, S);
-  if (P == 1 && U == 1 && blockDim.x == 256)
+  if (P == 1 && tensor_cores && U == 1 && blockDim.x == 256)
     return body_gemm_tc(d, r, S, reinterpret_cast<unsigned char*>(sm), bars, phase, pace);
   const uint32_t rows = 64 / U;
   uint64_t beg, end;

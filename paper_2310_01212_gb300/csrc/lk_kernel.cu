@@ -319,11 +319,12 @@ __device__ __forceinline__ uint64_t cta_rate(uint64_t cluster_rate, int S) {
  * unrolled: fully at up to 256 threads with one CTA per SM, where the
  * registers allow it.  P (CTAs per SM) sets the shared-memory budget.
  * `rate` (bytes per microsecond for this CTA, 0 = unpaced) paces the loads
- * of the streaming and GEMM bodies. */
+ * of the streaming and GEMM bodies; `tc` lets whole GEMM tiles use the
+ * tensor cores. */
 template <int MAXT, int P>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                         uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc,
-                                        uint64_t rate) {
+                                        uint64_t rate, bool tc = true) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
   const Pace deadline{gtime() + 2000000000ull, rate};
   bool ok = true;
@@ -333,7 +334,7 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
     case LK_OP_SUM_F32: ok = body_sum<P>(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
     case LK_OP_HIST_U8: ok = body_hist<P>(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
     case LK_OP_GEMM64_F32:
-      ok = body_gemm<(MAXT <= 256 && P == 1), P>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline);
+      ok = body_gemm<(MAXT <= 256 && P == 1), P>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline, tc);
       break;
     case LK_OP_COMBINE_SUM: body_combine_sum(d, r); break;
     case LK_OP_COMBINE_HIST: body_combine_hist(d, r); break;
@@ -428,7 +429,8 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
         if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
       }
     } else {
-      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate);
+      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate,
+                                      (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
       ok = (e == 0);
     }
     __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
@@ -603,7 +605,8 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     const uint32_t op = d.cmd - LK_CMD_WORK;
     const int berr = op == LK_OP_BATCH ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
                                        : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r],
-                                                           dc->hist[slot], cta_rate(d.aux, S));
+                                                           dc->hist[slot], cta_rate(d.aux, S),
+                                                           (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 

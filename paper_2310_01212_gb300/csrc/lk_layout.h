@@ -174,6 +174,7 @@ typedef struct __attribute__((aligned(LK_LINE))) {
 #define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
 #define LK_KFLAG_MAILBOX 2u      /* the master takes work from lk_mbox, not the ring   */
 #define LK_KFLAG_FINITE 4u       /* finite mode: ring pre-filled in device memory      */
+#define LK_KFLAG_GEMM_FFMA 8u    /* GEMM tiles on the FFMA path only                   */
 
 typedef struct {
   lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */

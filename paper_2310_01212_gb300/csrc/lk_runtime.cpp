@@ -310,7 +310,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   ctx->R_log2 = 0;
   while ((1u << ctx->R_log2) < R) ctx->R_log2++;
   ctx->log_cap = p->exec_log_cap;
-  if (p->flags & ~(uint32_t)(LK_INIT_DIRECT | LK_INIT_MAILBOX)) return LK_EINVAL;
+  if (p->flags & ~(uint32_t)(LK_INIT_DIRECT | LK_INIT_MAILBOX | LK_INIT_GEMM_FFMA)) return LK_EINVAL;
   if ((p->flags & LK_INIT_DIRECT) && (p->flags & LK_INIT_MAILBOX)) return LK_EINVAL;
   ctx->mailbox = live && (p->flags & LK_INIT_MAILBOX);
 
@@ -390,6 +390,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.log_cap = ctx->log_cap;
   a.flags = ((p->flags & LK_INIT_DIRECT) ? LK_KFLAG_DIRECT : 0u) | (ctx->mailbox ? LK_KFLAG_MAILBOX : 0u);
   a.ctas_per_sm = ctx->per_sm;
+  if (p->flags & LK_INIT_GEMM_FFMA) a.flags |= LK_KFLAG_GEMM_FFMA;
   if (!live) a.flags |= LK_KFLAG_FINITE;
   a.backoff_base_ns = p->backoff_base_ns;
   a.backoff_cap_ns = p->backoff_cap_ns ? p->backoff_cap_ns : 256;

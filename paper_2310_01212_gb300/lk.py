@@ -27,6 +27,7 @@ LK_ST_INIT, LK_ST_FINISHED, LK_ST_WORKING, LK_ST_NOP, LK_ST_EXITED, LK_ST_ERROR 
 LK_CMD_NOP, LK_CMD_EXIT, LK_CMD_WORK = 4, 8, 16
 LK_INIT_DIRECT = 1
 LK_INIT_MAILBOX = 2
+LK_INIT_GEMM_FFMA = 4
 LK_RATE_MIN = 1000
 LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_COPY_I32 = 0, 1, 2, 3, 4, 5
 LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7

@@ -115,6 +115,34 @@ def test_gemm_tiles(torch_ready, oracle_lib, S, per_sm):
         assert np.array_equal(got, B)
 
 
+@pytest.mark.parametrize("S", [1, 5])
+def test_gemm_ffma_flag(torch_ready, oracle_lib, S):
+    """LK_INIT_GEMM_FFMA keeps whole tiles on the FFMA path: the identity tile
+    is exact there, and both paths stay within the per-element bound."""
+    torch = torch_ready
+    t = 40
+    A = synth.normal_f32(15, 1, t * 4096).reshape(t, 64, 64)
+    B = synth.normal_f32(15, 2, t * 4096).reshape(t, 64, 64)
+    I = np.broadcast_to(np.eye(64, dtype=np.float32), (t, 64, 64)).copy()
+    dA, dB, dI = to_dev(A), to_dev(B), to_dev(I)
+    outs = {f: (torch.zeros((t, 64, 64), device="cuda"), torch.zeros((t, 64, 64), device="cuda"))
+            for f in (0, lk.LK_INIT_GEMM_FFMA)}
+    torch.cuda.current_stream().synchronize()
+    for f, (o_ab, o_ib) in outs.items():
+        with lk.lk_init([S], idle_lease_ns=5_000_000_000, flags=f) as c:
+            hs = [lk.lk_submit(c, 0, lk.LK_OP_GEMM64_F32, t, (dA, dB), o_ab),
+                  lk.lk_submit(c, 0, lk.LK_OP_GEMM64_F32, t, (dI, dB), o_ib)]
+            for h in hs:
+                assert lk.lk_wait(c, h) == lk.LK_OK
+    for f, (o_ab, o_ib) in outs.items():
+        assert gemm_ok(host(o_ab), A, B, oracle_lib)
+        if f:
+            assert np.array_equal(host(o_ib), B)
+        else:
+            got = host(o_ib)
+            assert np.all(np.abs(got - B) <= 2.0 ** -20 * np.abs(B))
+
+
 def test_misaligned_pointers_rejected_on_host(torch_ready):
     torch = torch_ready
     x = torch.zeros(1024, dtype=torch.int32, device="cuda")

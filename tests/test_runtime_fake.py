@@ -180,7 +180,7 @@ def test_init_rejects_bad_partitions(fake_env, sizes, bad):
 
 
 @pytest.mark.parametrize("kw", [dict(threads_per_cta=48), dict(ring_depth=3), dict(smids=[1, 1, 2, 3, 4]),
-                                dict(smids=[1, 2, 3, 4, 99])])
+                                dict(smids=[1, 2, 3, 4, 99]), dict(flags=8)])
 def test_init_rejects_bad_params(fake_env, kw):
     with pytest.raises(lk.LkError) as e:
         ctx_(**kw)
@@ -539,3 +539,8 @@ def test_rate_caps_are_checked(fake_env):
         assert e.value.code == lk.LK_EINVAL
         h = lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 64, (A,), A, aux=5000)
         assert lk.lk_wait(c, h) == lk.LK_OK
+
+
+def test_gemm_ffma_flag_accepted(fake_env):
+    with ctx_(flags=lk.LK_INIT_GEMM_FFMA | lk.LK_INIT_MAILBOX) as c:
+        assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)) == lk.LK_OK
