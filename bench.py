@@ -413,6 +413,15 @@ def main():
             raise RuntimeError(f"baseline failed: {lk.lk_strerror(rc)}")
         base.append((res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0)
     base = np.concatenate(base)
+    # the occupancy-chosen grid: what an ordinary launch of the body picks on
+    # its own (one CTA per SM at this shared-memory size, so every SM), for the
+    # last timed step's trace
+    occ_grid = n_sms
+    rc, res = lk.lk_baseline_run_trace(traces[-1][0], [occ_grid] * len(sizes), threads=cfg["threads"],
+                                       n_threads=len(sizes), device=dev)
+    if rc != lk.LK_OK:
+        raise RuntimeError(f"occupancy-grid baseline failed: {lk.lk_strerror(rc)}")
+    base_occ = (res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0
 
     # ---- dispatch alone: closed-loop NOPs, persistent kernel vs launch+sync ---------
     nop = np.zeros(2 * items_per_step, dtype=lk.TRACE_ITEM_DTYPE)
@@ -688,6 +697,8 @@ def main():
         "arrival_to_complete_us": lat_summary(lat_arr),
         "max_us": mx,
         "baseline_launch_sync_us": lat_summary(base),
+        "baseline_occupancy_grid_us": dict(lat_summary(base_occ), grid=occ_grid,
+                                           note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),
         "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
                             "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base)},
         "paper_mailbox_vs_ring": mbox,
