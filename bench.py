@@ -533,23 +533,33 @@ def main():
     serving = {"budget_bytes": scfg["budget_bytes"], "arena_bytes": scfg["arena_bytes"],
                "chunk_bytes": scfg["chunk_bytes"], "window": scfg["window"], "producers": scfg["producers"],
                "seconds_per_rate": args.serve_seconds, "partition": "4 clusters x 37 SMs", "rates": {}}
+    # the same rates with small requests coalesced many to a batch post
+    # (throughput mode: one dispatch serves many small requests)
+    serving["coalesced"] = {"coalesce_bytes": scfg["coalesce_bytes"], "coalesce_part_bytes": scfg["coalesce_part_bytes"],
+                            "rates": {}}
     with lk.lk_init(scfg["sizes"], device=dev, threads_per_cta=scfg["threads"], idle_lease_ns=30_000_000_000) as ctx:
-        for rate in scfg["rates"]:
-            reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
-            rc, res = lk.lk_serve(ctx, reqs, n_producers=scfg["producers"], budget_bytes=scfg["budget_bytes"],
-                                  arena=arena, arena_bytes=scfg["arena_bytes"], window=scfg["window"],
-                                  chunk_bytes=scfg["chunk_bytes"], timeout_ns=300_000_000_000)
-            if rc != lk.LK_OK:
-                raise RuntimeError(f"serving at {rate}/s failed: {lk.lk_strerror(rc)}")
-            lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
-            wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
-            span = float(res["t_complete_ns"].max()) / 1e9
-            serving["rates"][str(rate)] = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
-                                           "admission_wait_us": lat_summary(wait_s),
-                                           "throughput_req_per_s": reqs.size / span,
-                                           "throughput_gbs": float(inb.sum()) / span / 1e9,
-                                           "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
-                                           "chunks": int(res["chunks"].sum())}
+        for mode, rates, co in (("rates", scfg["rates"], 0), ("coalesced", scfg["rates"][-3:], scfg["coalesce_bytes"])):
+            for rate in rates:
+                reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
+                rc, res = lk.lk_serve(ctx, reqs, n_producers=scfg["producers"], budget_bytes=scfg["budget_bytes"],
+                                      arena=arena, arena_bytes=scfg["arena_bytes"], window=scfg["window"],
+                                      chunk_bytes=scfg["chunk_bytes"], timeout_ns=300_000_000_000,
+                                      coalesce_bytes=co, coalesce_part_bytes=scfg["coalesce_part_bytes"])
+                if rc != lk.LK_OK:
+                    raise RuntimeError(f"serving at {rate}/s failed: {lk.lk_strerror(rc)}")
+                lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
+                wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
+                span = float(res["t_complete_ns"].max()) / 1e9
+                entry = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
+                         "admission_wait_us": lat_summary(wait_s),
+                         "throughput_req_per_s": reqs.size / span,
+                         "throughput_gbs": float(inb.sum()) / span / 1e9,
+                         "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
+                         "chunks": int(res["chunks"].sum())}
+                if mode == "rates":
+                    serving["rates"][str(rate)] = entry
+                else:
+                    serving["coalesced"]["rates"][str(rate)] = entry
     del arena
 
     # ---- isolation: critical 16-SM cluster vs best-effort 132-SM cluster -----------

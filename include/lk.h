@@ -318,10 +318,21 @@ typedef struct {
                               /* partials of split sums and histograms             */
   uint64_t arena_bytes;
   uint64_t timeout_ns;        /* whole run; 0 -> 120 s                            */
+  uint64_t coalesce_bytes;    /* requests of at most this many input bytes run as  */
+                              /* items of batch posts (lk_submit_batch), many to a */
+                              /* post, so that one dispatch serves them all; 0 =   */
+                              /* off; at most chunk_bytes                          */
+  uint32_t coalesce_max;      /* requests per coalesced post; 0 -> 256, <= 256     */
+  uint32_t coalesce_part_bytes; /* input bytes per work unit of a coalesced item   */
+                              /* (its CTAs: at most 8); 0 -> 256 KiB              */
 } lk_serve_params;
 
 /* Run the requests through the context's clusters (all of one size) and
- * fill res[i] for each.  Outputs taken from the arena are released when the
+ * fill res[i] for each.  A request runs the same way whatever else is
+ * served, so its result does not depend on the mix: as chunks of at most
+ * chunk_bytes (one descriptor each, then one combine descriptor for split
+ * sums and histograms), or, when it is at most coalesce_bytes, as one item
+ * of a batch post split by coalesce_part_bytes.  Outputs taken from the arena are released when the
  * request completes (read them before the next call reuses the arena).
  * Returns LK_OK if every request finished, LK_EINVAL, LK_ENOMEM (a request
  * needs more arena or budget than exists), or the first error. */

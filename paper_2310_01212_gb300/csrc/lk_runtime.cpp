@@ -1034,6 +1034,7 @@ struct ServeReq {
   uint64_t elem_bytes = 4;    /* input bytes per element (per input) */
   uint32_t chunks = 1, done_chunks = 0;
   bool needs_combine = false, arena_out = false;
+  bool coalesced = false;     /* runs as one item of a batch post */
   uint64_t out_off = 0, scratch_off = 0;
   void* out = nullptr;
   void* scratch = nullptr;
@@ -1050,6 +1051,12 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
   const uint64_t chunk_bytes = p->chunk_bytes ? p->chunk_bytes : (16ull << 20);
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
   if (chunk_bytes < 65536 || ((uintptr_t)p->arena & 255u)) return LK_EINVAL;
+  const uint64_t coalesce_bytes = p->coalesce_bytes;
+  const uint32_t coalesce_max = p->coalesce_max ? p->coalesce_max : 256u;
+  lk_batch_tune ctune{8u, 0u, p->coalesce_part_bytes ? p->coalesce_part_bytes : (256u << 10)};
+  if (coalesce_bytes > chunk_bytes || coalesce_max > 256 || (coalesce_bytes && !ctx->max_units) ||
+      (coalesce_bytes && (uint64_t)coalesce_max * 8 > ctx->max_units))
+    return LK_EINVAL;
   std::vector<ServeReq> st(count);
   for (size_t i = 0; i < count; ++i) {
     const lk_request& r = reqs[i];
@@ -1070,7 +1077,9 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
     const uint64_t per_elem = r.op == LK_OP_ADD_I32 ? 8 : q.elem_bytes;
     uint64_t ce = std::max<uint64_t>(q.unit, chunk_bytes / per_elem / q.unit * q.unit);
     q.chunks = (uint32_t)std::max<uint64_t>(1, (r.n + ce - 1) / ce);
-    q.needs_combine = q.chunks > 1 && (r.op == LK_OP_SUM_F32 || r.op == LK_OP_HIST_U8);
+    q.coalesced = q.in_bytes <= coalesce_bytes;
+    if (q.coalesced) q.chunks = 1;
+    q.needs_combine = !q.coalesced && q.chunks > 1 && (r.op == LK_OP_SUM_F32 || r.op == LK_OP_HIST_U8);
     q.scratch_bytes = q.needs_combine ? (uint64_t)q.chunks * (r.op == LK_OP_SUM_F32 ? 16 : 1024) : 0;
     q.arena_out = r.out == nullptr;
     q.held = q.in_bytes + q.out_bytes + q.scratch_bytes;
@@ -1113,7 +1122,10 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
   std::deque<size_t> waiting;                      /* arrived, not admitted (FIFO) */
   std::deque<std::pair<size_t, uint32_t>> chunks;  /* admitted chunks to post     */
   std::deque<size_t> combines;                     /* requests whose combine is due */
-  struct Fly { uint64_t seq; size_t req; bool combine; };
+  std::deque<size_t> smalls;                       /* admitted coalesced requests  */
+  std::vector<std::vector<size_t>> posts;          /* members of each batch post   */
+  std::vector<lk_batch_item> bitems;
+  struct Fly { uint64_t seq; size_t req; int kind; };   /* kind 0 chunk, 1 combine, 2 batch (req = post) */
   std::vector<std::deque<Fly>> fly(ctx->C);
   size_t finished = 0;
   int first_err = LK_OK;
@@ -1187,13 +1199,16 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
       q.scratch = q.scratch_bytes ? (char*)p->arena + so : nullptr;
       held += q.held;
       res[i].t_admit_ns = now_ns() - t0;
-      for (uint32_t j = 0; j < q.chunks; ++j) chunks.emplace_back(i, j);
+      if (q.coalesced) smalls.push_back(i);
+      else for (uint32_t j = 0; j < q.chunks; ++j) chunks.emplace_back(i, j);
       waiting.pop_front();
     }
-    /* clusters pull: each takes work while its window has room */
+    /* clusters pull: each takes work while its window has room; coalesced
+     * requests go out many to a batch post, in arrival order against the
+     * chunks of larger requests */
     for (int k = 0; k < ctx->C; ++k) {
       const int c = (rr + k) % ctx->C;
-      while ((int)fly[c].size() < window && (!combines.empty() || !chunks.empty())) {
+      while ((int)fly[c].size() < window && (!combines.empty() || !chunks.empty() || !smalls.empty())) {
         uint64_t seq = 0;
         if (!combines.empty()) {
           const size_t i = combines.front();
@@ -1201,13 +1216,29 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
           lk_desc d{reqs[i].op == LK_OP_SUM_F32 ? (uint32_t)LK_OP_COMBINE_SUM : (uint32_t)LK_OP_COMBINE_HIST, 0,
                     q.chunks, 0};
           if (post(ctx, c, LK_CMD_WORK + d.op, &d, q.scratch, nullptr, q.out, &seq) != LK_OK) break;
-          fly[c].push_back({seq, i, true});
+          fly[c].push_back({seq, i, 1});
           combines.pop_front();
-        } else {
+        } else if (!smalls.empty() &&
+                   (chunks.empty() || reqs[smalls.front()].t_arrival_ns <= reqs[chunks.front().first].t_arrival_ns)) {
+          const size_t take = std::min<size_t>(smalls.size(), coalesce_max);
+          bitems.clear();
+          for (size_t m = 0; m < take; ++m) {
+            const size_t i = smalls[m];
+            const lk_request& r = reqs[i];
+            bitems.push_back(lk_batch_item{r.in0, r.in1, st[i].out, r.op, 0u, r.n});
+          }
+          lk_handle h = 0;
+          if (lk_submit_batch(ctx, c, bitems.data(), (uint32_t)take, &ctune, &h) != LK_OK) break;
+          posts.emplace_back(smalls.begin(), smalls.begin() + (long)take);
+          smalls.erase(smalls.begin(), smalls.begin() + (long)take);
+          fly[c].push_back({h & kSeqMask, posts.size() - 1, 2});
+        } else if (!chunks.empty()) {
           const auto cj = chunks.front();
           if (post_chunk(c, cj.first, cj.second, &seq) != LK_OK) break;
-          fly[c].push_back({seq, cj.first, false});
+          fly[c].push_back({seq, cj.first, 0});
           chunks.pop_front();
+        } else {
+          break;
         }
       }
     }
@@ -1219,8 +1250,14 @@ extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const
       while (!fly[c].empty() && fly[c].front().seq <= done) {
         const Fly f = fly[c].front();
         fly[c].pop_front();
+        if (f.kind == 2) {
+          for (size_t i : posts[f.req]) complete(i, LK_OK);
+          posts[f.req].clear();
+          posts[f.req].shrink_to_fit();
+          continue;
+        }
         ServeReq& q = st[f.req];
-        if (f.combine) {
+        if (f.kind == 1) {
           complete(f.req, LK_OK);
         } else if (++q.done_chunks == q.chunks) {
           if (q.needs_combine) combines.push_back(f.req);

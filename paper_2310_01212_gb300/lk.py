@@ -86,7 +86,8 @@ assert REQUEST_DTYPE.itemsize == 48 and REQUEST_RES_DTYPE.itemsize == 32
 class lk_serve_params(ctypes.Structure):
     _fields_ = [("n_producers", ctypes.c_int), ("window", ctypes.c_int), ("chunk_bytes", ctypes.c_uint64),
                 ("budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
-                ("timeout_ns", ctypes.c_uint64)]
+                ("timeout_ns", ctypes.c_uint64), ("coalesce_bytes", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32),
+                ("coalesce_part_bytes", ctypes.c_uint32)]
 
 
 TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op", "<u4"), ("n", "<u8"),
@@ -427,11 +428,13 @@ def lk_baseline_graph(items: np.ndarray, max_ctas: int, threads: int = 256, reps
 
 
 def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int, arena=None, arena_bytes: int = 0,
-             window: int = 0, chunk_bytes: int = 0, timeout_ns: int = 0):
+             window: int = 0, chunk_bytes: int = 0, timeout_ns: int = 0, coalesce_bytes: int = 0,
+             coalesce_max: int = 0, coalesce_part_bytes: int = 0):
     """Serve REQUEST_DTYPE requests; returns (rc, REQUEST_RES_DTYPE results)."""
     reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
     res = np.zeros(reqs.size, dtype=REQUEST_RES_DTYPE)
-    prm = lk_serve_params(n_producers, window, chunk_bytes, budget_bytes, _ptr(arena) or None, arena_bytes, timeout_ns)
+    prm = lk_serve_params(n_producers, window, chunk_bytes, budget_bytes, _ptr(arena) or None, arena_bytes, timeout_ns,
+                          coalesce_bytes, coalesce_max, coalesce_part_bytes)
     rc = ctx.lib.lk_serve(ctx.ptr, reqs.ctypes.data if reqs.size else None, reqs.size, ctypes.byref(prm),
                           res.ctypes.data if reqs.size else None)
     return rc, res

@@ -1,7 +1,8 @@
 """GPU parity of the serving loop (lk_serve): requests of uneven size arriving
 from 8 producers are admitted, split into chunks that interleave across the
-clusters, combined, and every output matches the oracle; each result is
-bit-identical when the request is served alone."""
+clusters (or, when small, coalesced many to a batch post), combined, and
+every output matches the oracle; each result is bit-identical when the
+request is served alone."""
 import numpy as np
 import pytest
 
@@ -11,8 +12,9 @@ from paper_2310_01212_gb300 import lk, workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def served(native_built, oracle_lib):
+@pytest.fixture(scope="module", params=[0, 256 << 10], ids=["chunks", "coalesced"])
+def served(request, native_built, oracle_lib):
+    coalesce = request.param
     torch = need_gpu()
     pools = wl.Pools.create(5, i32_bytes=256 << 20, u8_bytes=256 << 20, f32_bytes=256 << 20, slots=4, n_add=16)
     reqs, _ = wl.serving_requests(pools, 5, 40_000.0, 0.006, s_hi=24 << 20)
@@ -32,8 +34,8 @@ def served(native_built, oracle_lib):
     torch.cuda.synchronize()
     with lk.lk_init([8, 8, 8, 8], idle_lease_ns=10_000_000_000) as c:
         rc, res = lk.lk_serve(c, reqs, n_producers=8, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
-                              window=2, chunk_bytes=1 << 20)
-    return torch, pools, reqs, outs, rc, res, arena
+                              window=2, chunk_bytes=1 << 20, coalesce_bytes=coalesce)
+    return torch, pools, reqs, outs, rc, res, arena, coalesce
 
 
 def _inputs(pools, r):
@@ -51,9 +53,11 @@ def _inputs(pools, r):
 
 
 def test_served_outputs_match_oracle(served, oracle_lib):
-    torch, pools, reqs, outs, rc, res, arena = served
+    torch, pools, reqs, outs, rc, res, arena, coalesce = served
     assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
     assert reqs.size >= 100 and res["chunks"].max() > 1
+    if coalesce:
+        assert np.sum(res["chunks"] == 1) > 10
     for r, o in zip(reqs, outs):
         op = int(r["op"])
         ins = _inputs(pools, r)
@@ -69,18 +73,21 @@ def test_served_outputs_match_oracle(served, oracle_lib):
 
 
 def test_each_result_same_alone_and_in_the_mix(served):
-    torch, pools, reqs, outs, rc, res, arena = served
+    torch, pools, reqs, outs, rc, res, arena, coalesce = served
     pick = [i for i in range(reqs.size) if int(reqs[i]["op"]) in (lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8)][:12]
-    pick += [i for i in range(reqs.size) if int(reqs[i]["op"]) == lk.LK_OP_ADD_I32][:4]
+    pick += [i for i in range(reqs.size) if int(reqs[i]["op"]) in (lk.LK_OP_ADD_I32, lk.LK_OP_GEMM64_F32)][:8]
+    # outputs exist before the context starts (an allocation while it runs may wait for the device)
+    alone = {i: torch.empty_like(outs[i]) for i in pick}
+    torch.cuda.synchronize()
     with lk.lk_init([8, 8, 8, 8], idle_lease_ns=10_000_000_000) as c:
         for i in pick:
-            alone_out = torch.empty_like(outs[i])
+            alone_out = alone[i]
             one = reqs[i:i + 1].copy()
             one["t_arrival_ns"] = 0
             one["producer"] = 0
             one["out"] = alone_out.data_ptr()
             rc1, r1 = lk.lk_serve(c, one, n_producers=1, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
-                                  window=2, chunk_bytes=1 << 20)
+                                  window=2, chunk_bytes=1 << 20, coalesce_bytes=coalesce)
             assert rc1 == lk.LK_OK and r1["chunks"][0] == res["chunks"][i]
             a, m = host(alone_out), host(outs[i])
             if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32:

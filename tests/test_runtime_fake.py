@@ -357,6 +357,37 @@ def test_serve_admits_chunks_and_combines(fake_env):
         assert np.all(res["out"] % 256 == 0)
 
 
+def test_serve_coalesces_small_requests(fake_env):
+    """Requests of at most coalesce_bytes go out many to a batch post: fewer
+    posts than requests, every request finished, larger ones still chunked."""
+    fake_env["LK_FAKE_STALL_US"] = "200"
+    with ctx_(sizes=(2, 2), exec_log_cap=4096) as c:
+        reqs = _reqs(200, [lk.LK_OP_ADD_I32, lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8], [1 << 10, 1 << 12, 1 << 14],
+                     gap_ns=0)
+        big = _reqs(4, [lk.LK_OP_SUM_F32], [5 << 20], gap_ns=0)
+        allr = np.concatenate([reqs, big])
+        rc, res = lk.lk_serve(c, allr, n_producers=4, budget_bytes=1 << 34, arena=1 << 20, arena_bytes=1 << 34,
+                              chunk_bytes=1 << 20, coalesce_bytes=1 << 16, coalesce_max=64)
+        assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+        assert np.all(res["chunks"][:200] == 1) and np.all(res["chunks"][200:] == 20)
+        log, _ = lk.lk_exec_log(c, cap=1 << 16)
+        batches = int(np.sum(log["op"] == lk.LK_OP_BATCH)) // 2       # two ranks log each post
+        assert 4 <= batches < 200
+        assert np.sum(log["op"] == lk.LK_OP_COMBINE_SUM) == 2 * 4
+
+
+@pytest.mark.parametrize("units,kw", [(8192, dict(coalesce_bytes=2 << 20, chunk_bytes=1 << 20)),   # > chunk
+                                      (8192, dict(coalesce_max=300)),                            # > 256
+                                      (1024, dict())])                     # 256 items x 8 parts > table
+def test_serve_coalesce_checks(fake_env, units, kw):
+    with ctx_(sizes=(1,), max_batch_units=units) as c:
+        kw.setdefault("coalesce_bytes", 1 << 16)
+        kw.setdefault("chunk_bytes", 1 << 20)
+        rc, _ = lk.lk_serve(c, _reqs(1, [lk.LK_OP_COPY_I32], [16]), n_producers=4, budget_bytes=1 << 30,
+                            arena=1 << 20, arena_bytes=1 << 30, **kw)
+        assert rc == lk.LK_EINVAL
+
+
 def test_serve_budget_limits_admission(fake_env):
     fake_env["LK_FAKE_STALL_US"] = "2000"
     with ctx_(sizes=(1, 1)) as c:
