@@ -80,7 +80,9 @@ extern "C" {
 #define LK_OP_ADD_I32    1 /* out[i] = in0[i] + in1[i], int32, wraps mod 2^32; n elements */
 #define LK_OP_HIST_U8    2 /* out[v] = #{i : in0[i] == v}; n bytes in, 256 int32 bins out (overwritten) */
 #define LK_OP_SUM_F32    3 /* out[0] = sum of n float32 (fixed order for a given n and cluster size) */
-#define LK_OP_GEMM64_F32 4 /* n tiles: out[t] = in0[t] x in1[t], 64x64 row-major float32 tiles, FFMA */
+#define LK_OP_GEMM64_F32 4 /* n tiles: out[t] = in0[t] x in1[t], 64x64 row-major float32 tiles;     */
+                           /* float32 FFMA, or split-TF32 tensor-core MMAs for whole tiles (see   */
+                           /* LK_INIT_GEMM_FFMA); per element within 1e-4 sum_k |a b|              */
 #define LK_OP_COPY_I32   5 /* out[i] = in0[i], int32; n elements             */
 #define LK_OP_COMBINE_SUM  6 /* out[0] = binary64 sum of n float32 partials, one at the start of each */
                              /* 16-byte slot of in0 (fixed order)            */
