@@ -275,10 +275,6 @@ __device__ __forceinline__ void count4_warp(uint32_t* bins, uint32_t w) {
   atomicAdd(&bins[w >> 24], 1u);
 }
 
-__device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
-  asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
-}
-
 /* Lane-private counters: word (v << 5) | lane of a copy (8192 words, 32 KB)
  * counts bin v for this lane alone, so lane l only touches bank l, and one
  * byte costs an extract, an address and one shared reduction.  32-bit
