@@ -162,8 +162,33 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
   return true;
 }
 
+/* Shares of at most K vectors per thread skip the stage ring: every thread
+ * issues all of its 128-bit loads at once and then consumes them -- one
+ * global round trip, with no TMA issue, mbarrier wait or CTA barrier, which
+ * on a share of a few tens of KB cost more than they hide.  f(i, v, x) gets
+ * the thread's i-th vector, index v of the input.  Used by the add and sum
+ * bodies of kernels with registers to spare (DIRECT: at most 256 threads,
+ * one CTA per SM); elsewhere the extra live registers would spill. */
+template <int K, class F>
+__device__ __forceinline__ void direct(const uint4* in, uint64_t beg, uint64_t total, F&& f) {
+  const uint32_t T = blockDim.x;
+  uint4 q[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const uint64_t v = threadIdx.x + (uint64_t)i * T;
+    if (v < total) q[i] = ld_stream(in + beg + v);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const uint64_t v = threadIdx.x + (uint64_t)i * T;
+    if (v < total) f(i, beg + v, q[i]);
+  }
+}
+#define LK_DIRECT_ADD 4u     /* vectors per thread per input: add  */
+#define LK_DIRECT_ONE 8u     /* vectors per thread: sum, histogram */
+
 /* ---- int32 add / copy -------------------------------------------------- */
-template <int P>
+template <int P, bool DIRECT = false>
 __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                          uint32_t& phase, Pace pace) {
   const uint64_t n = d.n, nv = n >> 2;
@@ -171,13 +196,33 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
   share(nv, r, S, beg, end);
   int4* o = reinterpret_cast<int4*>(d.out);
   const uint32_t T = blockDim.x;
-  const bool ok = stream<2, false, P>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
-                                   beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase, pace,
-                                   [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
-                                     const int4* a = reinterpret_cast<const int4*>(s0);
-                                     const int4* b = reinterpret_cast<const int4*>(s1);
-                                     for (uint32_t v = threadIdx.x; v < cnt; v += T) st_stream(o + v0 + v, add4(a[v], b[v]));
-                                   });
+  bool ok = true;
+  if (DIRECT && end - beg <= (uint64_t)LK_DIRECT_ADD * T) {
+    const int4* a = reinterpret_cast<const int4*>(d.in0);
+    const int4* b = reinterpret_cast<const int4*>(d.in1);
+    int4 x[LK_DIRECT_ADD], y[LK_DIRECT_ADD];
+#pragma unroll
+    for (uint32_t i = 0; i < LK_DIRECT_ADD; ++i) {
+      const uint64_t v = beg + threadIdx.x + (uint64_t)i * T;
+      if (v < end) {
+        x[i] = ld_stream(a + v);
+        y[i] = ld_stream(b + v);
+      }
+    }
+#pragma unroll
+    for (uint32_t i = 0; i < LK_DIRECT_ADD; ++i) {
+      const uint64_t v = beg + threadIdx.x + (uint64_t)i * T;
+      if (v < end) st_stream(o + v, add4(x[i], y[i]));
+    }
+  } else {
+    ok = stream<2, false, P>(reinterpret_cast<const uint4*>(d.in0), reinterpret_cast<const uint4*>(d.in1),
+                             beg, end, dsm + SmemCfg<P>::work_bytes, bars, phase, pace,
+                             [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
+                               const int4* a = reinterpret_cast<const int4*>(s0);
+                               const int4* b = reinterpret_cast<const int4*>(s1);
+                               for (uint32_t v = threadIdx.x; v < cnt; v += T) st_stream(o + v0 + v, add4(a[v], b[v]));
+                             });
+  }
   if (r == S - 1) {
     const int32_t* as = reinterpret_cast<const int32_t*>(d.in0);
     const int32_t* bs = reinterpret_cast<const int32_t*>(d.in1);
@@ -210,7 +255,7 @@ __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsign
 }
 
 /* ---- float32 sum: this CTA's partial (valid in thread 0) ---------------- */
-template <int P>
+template <int P, bool DIRECT = false>
 __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                          uint32_t& phase, Pace pace, float* red, float* partial_out) {
   const uint64_t n = d.n, nv = n >> 2;
@@ -218,7 +263,16 @@ __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigne
   share(nv, r, S, beg, end);
   const uint32_t T = blockDim.x;
   float acc0 = 0.f, acc1 = 0.f;
-  const bool ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes,
+  bool ok = true;
+  if (DIRECT && end - beg <= (uint64_t)LK_DIRECT_ONE * T) {
+    /* the thread's vectors alternate between the two accumulators, as in
+     * the staged loop below over a single chunk */
+    direct<LK_DIRECT_ONE>(reinterpret_cast<const uint4*>(d.in0), beg, end - beg, [&](int i, uint64_t, uint4 q) {
+      const float4 p = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), __uint_as_float(q.w));
+      if (i & 1) acc1 += (p.x + p.y) + (p.z + p.w);
+      else acc0 += (p.x + p.y) + (p.z + p.w);
+    });
+  } else ok = stream<1, false, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes,
                                    bars, phase, pace, [&](uint64_t, uint32_t cnt, const uint4* s0, const uint4*) {
                                      const float4* x = reinterpret_cast<const float4*>(s0);
                                      uint32_t v = threadIdx.x;
@@ -319,8 +373,9 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   const uint32_t T = blockDim.x, W = T / 32, lane = threadIdx.x & 31;
   uint32_t* sh = reinterpret_cast<uint32_t*>(dsm);
   const uint8_t* xb = reinterpret_cast<const uint8_t*>(d.in0);
-  bool ok;
-  if ((end - beg) * 16 < LK_HIST_SMALL_BYTES) {
+  bool ok = true;
+  const uint64_t total = end - beg;
+  if (total * 16 < LK_HIST_SMALL_BYTES) {
     hist_zero(sh, W * 256);
     __syncthreads();
     uint32_t* bins = sh + (threadIdx.x >> 5) * 256;

@@ -329,9 +329,11 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
   const Pace deadline{gtime() + 2000000000ull, rate};
   bool ok = true;
   switch (op) {
-    case LK_OP_ADD_I32: ok = body_add<P>(d, r, S, dsm, bars, phase, deadline); break;
+    case LK_OP_ADD_I32: ok = body_add<P, (MAXT <= 256 && P == 1)>(d, r, S, dsm, bars, phase, deadline); break;
     case LK_OP_COPY_I32: ok = body_copy<P>(d, r, S, dsm, bars, phase, deadline); break;
-    case LK_OP_SUM_F32: ok = body_sum<P>(d, r, S, dsm, bars, phase, deadline, red, partial_out); break;
+    case LK_OP_SUM_F32:
+      ok = body_sum<P, (MAXT <= 256 && P == 1)>(d, r, S, dsm, bars, phase, deadline, red, partial_out);
+      break;
     case LK_OP_HIST_U8: ok = body_hist<P>(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
     case LK_OP_GEMM64_F32:
       ok = body_gemm<(MAXT <= 256 && P == 1), P>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline, tc);
@@ -395,7 +397,7 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
     bool ok = true;
     if (op == LK_OP_SUM_F32) {
       float* pout = parts > 1 ? &bc->sums[comb - 1].partial[part] : &s_part;
-      ok = body_sum<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
+      ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
       if (threadIdx.x == 0) {
         if (parts == 1) {
           *reinterpret_cast<float*>(it.out) = s_part;
