@@ -567,9 +567,14 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       } else {
         err = take_from_relay(a, dc, &dc->relay[slot], k, dsc);
       }
+      /* A relayed member needs no check below: the master completes
+       * descriptor k-1 (every rank finished it) before it relays k, so every
+       * earlier descriptor has finished by the time a member sees k.  Members
+       * that read the ring themselves (LK_INIT_DIRECT) can run ahead. */
+      const bool gated = relay && !master;
       /* relay-ring slot k mod D (relay copy, partials, histogram accumulator)
        * is free once descriptor k+1-D has finished */
-      if (!err && k + 1 > LK_BCAST_DEPTH && known_done < k + 1 - LK_BCAST_DEPTH &&
+      if (!err && !gated && k + 1 > LK_BCAST_DEPTH && known_done < k + 1 - LK_BCAST_DEPTH &&
           (master ? relay : dsc.cmd != LK_CMD_EXIT)) {
         const int ww = wait_word(a, &dc->dev_done, k + 1 - LK_BCAST_DEPTH, false, &known_done);
         err = ww < 0 ? LK_DERR_STALL : ww;
@@ -580,7 +585,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       }
       /* a batch starts once every earlier descriptor of the cluster finished
        * (its ticket and combine state are then at rest) */
-      if (!err && dsc.cmd == LK_CMD_WORK + LK_OP_BATCH && k > 0 && known_done < k) {
+      if (!err && !gated && dsc.cmd == LK_CMD_WORK + LK_OP_BATCH && k > 0 && known_done < k) {
         const int ww = wait_word(a, &dc->dev_done, k, false, &known_done);
         err = ww < 0 ? LK_DERR_STALL : ww;
       }
