@@ -253,11 +253,14 @@ __device__ __noinline__ int wait_word(const lk_kargs& a, const uint64_t* word, u
   }
 }
 
-/* Warp 0 of rank 0: wait until every rank of the cluster has finished
+/* Every warp of rank 0: wait until every rank of the cluster has finished
  * descriptor `want` (flag[q] >= want).  Lanes poll disjoint ranks in
- * parallel, so the wait costs about one L2 round trip once the last rank is
- * done.  Returns 0 or an LK_DERR_* reason (same bounds as wait_word). */
-__device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag, int S, uint64_t want) {
+ * parallel; the warps poll independently, each one round trip per pass, and
+ * the first to see every flag raised tells the others through *found --
+ * with their passes out of step, a raised flag is seen sooner than by one
+ * warp alone.  Returns 0 or an LK_DERR_* reason (same bounds as wait_word). */
+__device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag, int S, uint64_t want,
+                                         volatile int* found) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t pending = 0;   /* bit j: rank lane + 32 j not seen yet */
   for (int j = 0; j < 32 && (int)lane + 32 * j < S; ++j) pending |= 1u << j;
@@ -268,6 +271,10 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
   }
   const uint64_t limit = a.lease_ns + 1000000000ull;
   for (uint32_t it = 1;; ++it) {
+    if (__any_sync(0xffffffffu, *found != 0)) {   /* warp-uniform */
+      fence_acq_rel_gpu();
+      return 0;
+    }
     /* relaxed loads can all be in flight at once (acquire loads would each
      * wait for the one before); one acquire fence follows success */
     for (int g = 0; g < 32 && (pending >> g); g += 8) {
@@ -282,6 +289,7 @@ __device__ __noinline__ int gather_flags(const lk_kargs& a, const uint64_t* flag
     }
     if (__all_sync(0xffffffffu, pending == 0)) {
       fence_acq_rel_gpu();
+      if (lane == 0) *found = 1;
       return 0;
     }
     if ((it & 255) == 0) {
@@ -446,6 +454,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(64) lk_slot s_desc;
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
+  __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag */
   __shared__ float s_red[32];
   __shared__ __align__(8) uint64_t s_bars[LK_NUM_BARS];
   __shared__ uint64_t s_tstart;
@@ -602,6 +611,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
         s_exit = (dsc.cmd == LK_CMD_EXIT);
       }
       s_err = 0;
+      s_found = 0;
       s_tstart = gtime();
     }
     __syncthreads();
@@ -624,9 +634,9 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       if (S > 1) st_release_gpu(&dc->flag[r], k + 1);   /* orders this CTA's writes (after the barrier) */
     }
     if (master) {
-      if (S > 1 && tid < 32) {
-        const int gerr = gather_flags(a, dc->flag, S, k + 1);
-        if (gerr && tid == 0) s_err = gerr;
+      if (S > 1) {
+        const int gerr = gather_flags(a, dc->flag, S, k + 1, &s_found);
+        if (gerr && (tid & 31) == 0) s_err = gerr;
       }
       __syncthreads();
       if (!s_err) {
