@@ -6,7 +6,9 @@ or CPU fallback: if the library is missing, loading fails with an error.
 
 Functions keep the C names (lk_init, lk_submit, lk_poll, lk_wait, lk_sync,
 lk_dispose, ...).  Device pointers may be given as ints or as objects with a
-``data_ptr()`` method (torch tensors).  Failures raise ``LkError`` carrying the
+``data_ptr()`` method (torch tensors); a tensor must be a contiguous CUDA
+tensor holding at least the bytes the operation touches (``op_bytes``), which
+is checked here before the call.  Failures raise ``LkError`` carrying the
 C return code, except where a code is an expected answer (lk_poll's
 LK_PENDING, lk_wait's LK_ETIMEDOUT, lk_submit's LK_EAGAIN), which are returned.
 """
@@ -171,6 +173,56 @@ def _ptr(x) -> int:
     return int(x.data_ptr())
 
 
+def op_bytes(op: int, n: int, ctas: int = 0) -> tuple:
+    """Bytes of (in0, in1, out) that one descriptor of `op` over `n` reads or
+    writes, from the operation definitions in include/lk.h; `ctas` = the CTAs
+    that run it (LK_OP_SPIN writes one uint32 per CTA)."""
+    n = int(n)
+    if op == LK_OP_ADD_I32:
+        return 4 * n, 4 * n, 4 * n
+    if op == LK_OP_HIST_U8:
+        return n, 0, 1024
+    if op == LK_OP_SUM_F32:
+        return 4 * n, 0, 4
+    if op == LK_OP_GEMM64_F32:
+        return 16384 * n, 16384 * n, 16384 * n
+    if op == LK_OP_COPY_I32:
+        return 4 * n, 0, 4 * n
+    if op == LK_OP_COMBINE_SUM:
+        return (16 * (n - 1) + 4 if n else 0), 0, 4
+    if op == LK_OP_COMBINE_HIST:
+        return 1024 * n, 0, 1024
+    if op == LK_OP_SPIN:
+        return 0, 0, 4 * int(ctas)
+    return 0, 0, 0
+
+
+def _checked(x, need: int, what: str) -> int:
+    """Device address of x.  A tensor (an object with is_cuda / numel /
+    element_size) must live on a CUDA device, be contiguous and hold at least
+    `need` bytes, else LkError(LK_EINVAL) before anything reaches the library.
+    Plain ints are the caller's responsibility (the library checks alignment)."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if hasattr(x, "is_cuda") and hasattr(x, "numel"):
+        if not x.is_cuda:
+            raise LkError(LK_EINVAL, f"{what}: not a CUDA tensor")
+        if not x.is_contiguous():
+            raise LkError(LK_EINVAL, f"{what}: not contiguous")
+        have = int(x.numel()) * int(x.element_size())
+        if have < need:
+            raise LkError(LK_EINVAL, f"{what}: holds {have} bytes, the operation touches {need}")
+    return int(x.data_ptr())
+
+
+def _operands(op: int, n: int, ins, out, ctas: int = 0) -> tuple:
+    """(in0, in1, out) addresses, each tensor checked against op_bytes."""
+    need = op_bytes(op, n, ctas)
+    ins = tuple(ins or ())
+    a = [_checked(ins[i], need[i] if i < 2 else 0, f"in{i}") for i in range(len(ins))]
+    return a, _checked(out, need[2], "out")
+
+
 def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
                 backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
                 boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0,
@@ -228,9 +280,11 @@ def lk_init(sizes, fake: bool = False, **kw) -> Context:
 def lk_submit(ctx: Context, cluster: int, op: int, n: int, ins=(), out=None, aux: int = 0) -> int | None:
     """Returns the handle, or None if the cluster's ring is full (LK_EAGAIN)."""
     d = lk_desc(op, 0, n, aux)
-    arr = (ctypes.c_void_p * max(1, len(ins)))(*[_ptr(i) for i in ins]) if ins else None
+    ctas = ctx.sizes[cluster] if 0 <= cluster < len(ctx.sizes) else 0
+    a, o = _operands(op, n, ins, out, ctas)
+    arr = (ctypes.c_void_p * max(1, len(a)))(*a) if a else None
     h = ctypes.c_uint64()
-    rc = ctx.lib.lk_submit(ctx.ptr, cluster, ctypes.byref(d), arr, len(ins), _ptr(out), ctypes.byref(h))
+    rc = ctx.lib.lk_submit(ctx.ptr, cluster, ctypes.byref(d), arr, len(a), o, ctypes.byref(h))
     if rc == LK_EAGAIN:
         return None
     if rc != LK_OK:
@@ -329,15 +383,21 @@ def lk_run_finite(sizes, descs, cluster_of, in0=None, in1=None, out=None, log_ca
     D = (lk_desc * max(1, cnt))(*[lk_desc(op, 0, n, 0) for op, n in descs])
     C = (ctypes.c_int * max(1, cnt))(*cluster_of)
 
-    def arr(xs):
+    def ctas_of(i):
+        c = int(cluster_of[i])
+        return sizes[c] if 0 <= c < len(sizes) else 0
+
+    def arr(xs, k):
         if xs is None:
             return None
-        return (ctypes.c_void_p * max(1, cnt))(*[_ptr(x) for x in xs])
+        return (ctypes.c_void_p * max(1, cnt))(
+            *[_checked(x, op_bytes(descs[i][0], descs[i][1], ctas_of(i))[k] if i < cnt else 0, f"descriptor {i}")
+              for i, x in enumerate(xs)])
 
     ms = ctypes.c_float(-1.0)
     logbuf = np.zeros(max(1, log_cap), dtype=EXEC_REC_DTYPE)
     ln = ctypes.c_size_t()
-    rc = lib.lk_run_finite(ctypes.byref(p), D, C, arr(in0), arr(in1), arr(out), cnt, ctypes.byref(ms),
+    rc = lib.lk_run_finite(ctypes.byref(p), D, C, arr(in0, 0), arr(in1, 1), arr(out, 2), cnt, ctypes.byref(ms),
                            logbuf.ctypes.data if log_cap else None, log_cap, ctypes.byref(ln))
     if rc != LK_OK:
         raise LkError(rc, "lk_run_finite")
@@ -382,8 +442,9 @@ def lk_launch_noalloc(op: int, n: int, ins=(), out=None, ctas: int = 37, threads
     ``torch.cuda.current_stream().cuda_stream``) or None."""
     lib = load()
     d = lk_desc(op, 0, n, 0)
-    arr = (ctypes.c_void_p * max(1, len(ins)))(*[_ptr(i) for i in ins]) if ins else None
-    return lib.lk_launch_noalloc(device, ctypes.byref(d), arr, len(ins), _ptr(out), ctas, threads, stream or 0)
+    a, o = _operands(op, n, ins, out, ctas)
+    arr = (ctypes.c_void_p * max(1, len(a)))(*a) if a else None
+    return lib.lk_launch_noalloc(device, ctypes.byref(d), arr, len(a), o, ctas, threads, stream or 0)
 
 
 def batch_items(rows) -> np.ndarray:
@@ -393,9 +454,10 @@ def batch_items(rows) -> np.ndarray:
     for i, r in enumerate(rows):
         op, n, ins, out = r[:4]
         a[i]["op"], a[i]["n"] = op, n
-        a[i]["in0"] = _ptr(ins[0]) if len(ins) > 0 else 0
-        a[i]["in1"] = _ptr(ins[1]) if len(ins) > 1 else 0
-        a[i]["out"] = _ptr(out)
+        p, o = _operands(op, n, ins, out)
+        a[i]["in0"] = p[0] if len(p) > 0 else 0
+        a[i]["in1"] = p[1] if len(p) > 1 else 0
+        a[i]["out"] = o
         a[i]["parts"] = r[4] if len(r) > 4 else 0
     return a
 

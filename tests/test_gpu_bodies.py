@@ -154,6 +154,26 @@ def test_misaligned_pointers_rejected_on_host(torch_ready):
         assert lk.lk_wait(c, h) == lk.LK_OK
 
 
+def test_short_or_host_tensors_rejected_before_the_call(torch_ready):
+    """The binding compares each tensor's numel * element_size with the bytes
+    the operation touches; nothing reaches the GPU when one is short."""
+    torch = torch_ready
+    x = torch.arange(1000, dtype=torch.int32, device="cuda")
+    xh = x.cpu()
+    out = torch.full((1000,), -1, dtype=torch.int32, device="cuda")
+    untouched = torch.full((1000,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([2], idle_lease_ns=5_000_000_000) as c:
+        for args in [(1001, (x,), untouched), (1000, (x,), untouched[:996]), (1000, (xh,), untouched),
+                     (500, (x[::2],), untouched)]:
+            with pytest.raises(lk.LkError) as e:
+                lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, *args)
+            assert e.value.code == lk.LK_EINVAL
+        assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 1000, (x,), out)) == lk.LK_OK
+    assert np.array_equal(host(out), host(x))
+    assert np.all(host(untouched) == -1)        # none of the rejected calls ran
+
+
 def test_sum_is_identical_alone_and_in_the_mix(torch_ready, oracle_lib):
     """The split depends only on (n, cluster size): a result does not depend on
     what else ran before or beside it."""

@@ -8,7 +8,7 @@ import time
 import numpy as np
 import pytest
 
-from gpu_util import host, need_gpu, sum_ok, to_dev
+from gpu_util import check_log, host, need_gpu, sum_ok, to_dev
 from paper_2310_01212_gb300 import lk, synth
 
 pytestmark = pytest.mark.gpu
@@ -17,23 +17,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def torch_ready(native_built):
     return need_gpu()
-
-
-def check_log(oracle, ctx, log, sizes, n_posted, posted_op=None):
-    pinned = sum((lk.lk_cluster_info(ctx, c) for c in range(len(sizes))), [])
-    # completion time of each descriptor = t_done of its last arriver
-    C = len(sizes)
-    off = np.concatenate([[0], np.cumsum(n_posted)])
-    t_complete = np.zeros(int(off[-1]), dtype=np.uint64)
-    last = log[log["t_done_ns"] > 0]
-    idx = off[last["cluster"].astype(np.int64)] + last["seq"].astype(np.int64) - 1
-    t_complete[idx] = last["t_done_ns"]
-    res = oracle.check_exec_log(log["seq"], log["cluster"], log["rank"], log["smid"], log["op"], log["order"],
-                                sizes, n_posted, pinned_smid=pinned, posted_op=posted_op,
-                                t_end=log["t_end_ns"], t_complete=t_complete)
-    # exactly one last arriver per descriptor
-    assert len(last) == int(off[-1])
-    return res, pinned
 
 
 @pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX])

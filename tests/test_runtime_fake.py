@@ -223,6 +223,91 @@ def test_multi_producer_exec_log_passes_checker(fake_env, oracle_lib):
     assert c.dispose() == lk.LK_OK
 
 
+def test_stress_trace_full_chip_passes_checker(fake_env, oracle_lib):
+    """100,000 NOPs from four native producer threads over eight clusters of
+    very different sizes covering 152 fake SMs; the whole log is checked."""
+    import oracle
+
+    fake_env["LK_FAKE_SMS"] = "152"
+    sizes = [1, 3, 4, 8, 16, 24, 32, 64]
+    total, C = 100_000, 8
+    items = np.zeros(total, dtype=lk.TRACE_ITEM_DTYPE)
+    items["cluster"] = np.arange(total) % C
+    n_posted = [total // C] * C
+    with ctx_(sizes=sizes, exec_log_cap=total // C) as c:
+        rc, res = lk.lk_run_trace(c, items, n_threads=4, timeout_ns=60_000_000_000)
+        assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+        log, dropped = lk.lk_exec_log(c)
+        assert dropped == 0 and len(log) == sum(sizes) * total // C
+        pinned = sum((lk.lk_cluster_info(c, k) for k in range(C)), [])
+        assert sorted(pinned) == list(range(152))
+        res = oracle.check_exec_log(log["seq"], log["cluster"], log["rank"], log["smid"], log["op"], log["order"],
+                                    sizes, n_posted, pinned_smid=pinned, posted_op=np.zeros(total, np.int32))
+        assert res["violations"] == 0, res
+
+
+class _DevBuf:
+    """Stands in for a CUDA tensor: what the binding's size check reads."""
+
+    def __init__(self, nbytes, addr=A, is_cuda=True, contiguous=True):
+        self.nbytes, self.addr, self.is_cuda, self.contiguous = nbytes, addr, is_cuda, contiguous
+
+    def numel(self):
+        return self.nbytes
+
+    def element_size(self):
+        return 1
+
+    def is_contiguous(self):
+        return self.contiguous
+
+    def data_ptr(self):
+        return self.addr
+
+
+def test_op_bytes_follow_the_operation_definitions():
+    n = 1000
+    assert lk.op_bytes(lk.LK_OP_NOP, n) == (0, 0, 0)
+    assert lk.op_bytes(lk.LK_OP_ADD_I32, n) == (4000, 4000, 4000)
+    assert lk.op_bytes(lk.LK_OP_HIST_U8, n) == (1000, 0, 1024)
+    assert lk.op_bytes(lk.LK_OP_SUM_F32, n) == (4000, 0, 4)
+    assert lk.op_bytes(lk.LK_OP_GEMM64_F32, 3) == (3 * 64 * 64 * 4,) * 3
+    assert lk.op_bytes(lk.LK_OP_COPY_I32, n) == (4000, 0, 4000)
+    assert lk.op_bytes(lk.LK_OP_COMBINE_SUM, 5) == (16 * 4 + 4, 0, 4)
+    assert lk.op_bytes(lk.LK_OP_COMBINE_SUM, 0) == (0, 0, 4)
+    assert lk.op_bytes(lk.LK_OP_COMBINE_HIST, 3) == (3 * 1024, 0, 1024)
+    assert lk.op_bytes(lk.LK_OP_SPIN, 20000, ctas=7) == (0, 0, 28)
+
+
+def test_binding_checks_tensor_sizes_before_the_call(fake_env):
+    torch = pytest.importorskip("torch")
+    with ctx_(sizes=(3,)) as c:
+        n = 256
+        ok = _DevBuf(4 * n)
+        h = lk.lk_submit(c, 0, lk.LK_OP_ADD_I32, n, (ok, ok), ok)
+        assert lk.lk_wait(c, h) == lk.LK_OK
+        for bad in [(_DevBuf(4 * n - 1), ok, ok), (ok, _DevBuf(4 * n - 4), ok), (ok, ok, _DevBuf(16)),
+                    (ok, ok, _DevBuf(4 * n, contiguous=False)), (ok, _DevBuf(4 * n, is_cuda=False), ok)]:
+            with pytest.raises(lk.LkError) as e:
+                lk.lk_submit(c, 0, lk.LK_OP_ADD_I32, n, bad[:2], bad[2])
+            assert e.value.code == lk.LK_EINVAL
+        # a host tensor is never a device operand
+        with pytest.raises(lk.LkError, match="not a CUDA tensor"):
+            lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, 4, (torch.zeros(4, dtype=torch.int32),), ok)
+        # spin writes one uint32 per CTA of the cluster
+        assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_SPIN, 10, (), _DevBuf(12))) == lk.LK_OK
+        with pytest.raises(lk.LkError):
+            lk.lk_submit(c, 0, lk.LK_OP_SPIN, 10, (), _DevBuf(8))
+        # histogram bins and batch items are checked the same way
+        with pytest.raises(lk.LkError):
+            lk.lk_submit(c, 0, lk.LK_OP_HIST_U8, 64, (_DevBuf(64),), _DevBuf(1020))
+        with pytest.raises(lk.LkError):
+            lk.batch_items([(lk.LK_OP_COPY_I32, n, (ok,), _DevBuf(4 * n - 16))])
+        # plain ints pass through unchecked (the library checks alignment)
+        assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_COPY_I32, n, (A,), A)) == lk.LK_OK
+        assert lk.lk_sync(c) == lk.LK_OK
+
+
 def test_exec_log_ring_keeps_latest(fake_env):
     with ctx_(sizes=(1,), exec_log_cap=4) as c:
         for _ in range(10):
