@@ -289,17 +289,21 @@ def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, th
         "gemm64_f32": (lk.LK_OP_GEMM64_F32, tiles, f32[:half], f32[half:2 * half],
                        pools.out_add.view(torch.float32).view(-1)[:half], 3 * half * 4),
     }
+    # the block size is a context parameter: the histogram, bound by shared-
+    # memory reductions, is also timed at 512 threads per CTA
+    runs = [(name, case, threads) for name, case in cases.items()]
+    runs.append(("hist_u8_512_threads", cases["hist_u8"], 512))
     res = {}
-    for name, (op, cnt, a, b, o, nbytes) in cases.items():
+    for name, (op, cnt, a, b, o, nbytes), t_cta in runs:
         ms = []
         for _ in range(reps):
             t, _log = lk.lk_run_finite([n_sms], [(op, cnt)] * per_launch, [0] * per_launch,
                                        in0=[a] * per_launch, in1=[b] * per_launch if b is not None else None,
-                                       out=[o] * per_launch, threads_per_cta=threads, exec_log_cap=per_launch + 1)
+                                       out=[o] * per_launch, threads_per_cta=t_cta, exec_log_cap=per_launch + 1)
             ms.append(t)
         avg = float(np.mean(ms))
         res[name] = {"gbs": nbytes * per_launch / (avg * 1e-3) / 1e9, "launch_ms": avg, "bytes_per_launch":
-                     nbytes * per_launch, "descriptors_per_launch": per_launch}
+                     nbytes * per_launch, "descriptors_per_launch": per_launch, "threads_per_cta": t_cta}
         if op == lk.LK_OP_GEMM64_F32:
             res[name]["tflops"] = 524288.0 * cnt * per_launch / (avg * 1e-3) / 1e12
     return res

@@ -20,15 +20,17 @@
  *             stage (no registers touched)
  *   hist_u8   per-CTA counts -> cluster accumulator (global atomics) -> copied
  *             out by rank 0.  Small shares count into per-warp bins with
- *             shared atomics; large shares count into lane-private packed
- *             16-bit counters, which no two lanes of a warp ever share, so
- *             random bytes cause no shared-memory bank conflicts.
+ *             shared atomics; large shares count into lane-private 32-bit
+ *             counters, which no two lanes of a warp ever share, so random
+ *             bytes cause no shared-memory bank conflicts; with one CTA per
+ *             SM every warp streams its part through a ring of its own.
  *   sum_f32   per-thread float accumulators, warp shuffles, per-CTA partial;
  *             rank 0 adds the partials in rank order in binary64
  *   gemm64    64x64x64 float32 tiles staged into shared memory by TMA bulk
- *             copies (six 32 KB stages, three with two CTAs per SM, so later
- *             tiles load while this one computes), 4x4 register micro-tiles,
- *             FFMA in k order
+ *             copies.  Whole tiles (one CTA per SM, 256 threads): tcgen05
+ *             tensor cores on split-TF32 operands.  Row blocks and other
+ *             shapes: six 32 KB stages (three with two CTAs per SM), 4x4
+ *             register micro-tiles, FFMA in k order
  * Used by the persistent kernel and by the ordinary-launch baseline kernels.
  */
 #ifndef LK_BODIES_CUH
@@ -63,6 +65,8 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 #define LK_GEMM_STAGE_FLOATS 8192u     /* one GEMM stage: A rows 16 KB + B tile 16 KB */
 #define LK_HIST_COPIES 2u              /* lane-private counter copies (32 KB each), P = 1 */
 #define LK_NUM_BARS 8u                 /* mbarriers: one per stage; two for MMA completion */
+#define LK_WARP_BARS (32u * LK_STAGES)  /* then one per stage of each warp's own ring (histogram) */
+#define LK_ALL_BARS (LK_NUM_BARS + LK_WARP_BARS)
 
 template <int P>
 struct SmemCfg {
@@ -321,6 +325,11 @@ __device__ __forceinline__ void combine_sum(const lk_slot& d, const float* parti
  * (measured crossover on GB300: a 28 KB share counts in 2.5 us lane-private
  * against 2.9 us in per-warp bins; a 7 KB share in 1.9 against 1.7 us). */
 #define LK_HIST_SMALL_BYTES (16u * 1024u)
+/* With one CTA per SM, shares from this many bytes per CTA stream through
+ * one ring per warp (measured on GB300 over 152 CTAs: from 0.4 MB per CTA
+ * 3-4 % faster at 256 threads and 14 % at 512; below 0.2 MB 1-4 % slower,
+ * where the CTA's single ring needs fewer copies and waits). */
+#define LK_HIST_WARP_BYTES (256u * 1024u)
 
 __device__ __forceinline__ void count4_warp(uint32_t* bins, uint32_t w) {
   atomicAdd(&bins[w & 0xffu], 1u);
@@ -363,6 +372,132 @@ __device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
   for (uint32_t i = threadIdx.x; i < words / 4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
 }
 
+/* ---- histogram of a large share, one CTA per SM ------------------------- */
+/* Counters: word 64 v + 32 c + lane counts bin v for one lane of copy c
+ * (two copies, 64 KB).  A bin's row is 256 bytes, so the byte offset of
+ * bin v is v << 8: one byte permute moves byte b of a loaded word into
+ * bits 8..15, and an add of the lane's base makes the address.  Lane l
+ * still touches only bank l. */
+__device__ __forceinline__ void count4_row(uint32_t lane_addr, uint32_t w) {
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const uint32_t off = __byte_perm(w, 0u, 0x4404u | ((uint32_t)b << 4));
+    asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + off) : "memory");
+  }
+}
+
+/* Thread v (< 256) adds row v (both copies, 32 lanes each); each 8-thread
+ * phase of the 128-bit loads starts at thread-dependent columns and so
+ * touches all 32 banks once. */
+__device__ __forceinline__ uint32_t hist_row_readout(const uint32_t* sh, uint32_t v) {
+  const uint4* rw = reinterpret_cast<const uint4*>(sh + v * 64u);
+  uint32_t tot = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 16; ++j) {
+    const uint4 q = rw[(j + v) & 15u];
+    tot += (q.x + q.y) + (q.z + q.w);
+  }
+  return tot;
+}
+
+/* Every warp streams its own contiguous part of the CTA's share [beg, end)
+ * (16-byte vectors) through a private ring of LK_STAGES stages -- its slice
+ * of the streaming region -- which its lane 0 fills with TMA bulk copies and
+ * all its lanes await on the warp's own mbarriers (bars[LK_NUM_BARS + 4 w
+ * + s], phase bits LK_NUM_BARS + s of `phase`, which every lane of the warp
+ * keeps alike).  A warp never waits for another between chunks (with one
+ * ring per CTA, warps stalled about a fifth of their cycles at the per-chunk
+ * barrier: random bytes make their counting times uneven).  Returns false,
+ * on every thread alike, if a stage did not arrive before the deadline. */
+template <int P>
+__device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg, uint64_t end, unsigned char* dsm,
+                                                  uint64_t* bars, uint32_t& phase, uint32_t lane_addr, Pace pace) {
+  static_assert(P == 1, "the counter rows take the whole 64 KB work region of one CTA per SM");
+  const uint32_t W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t stage_vec = SmemCfg<P>::stream_bytes / W / LK_STAGES / 16u;
+  uint4* ring = reinterpret_cast<uint4*>(dsm + SmemCfg<P>::work_bytes) + (size_t)warp * LK_STAGES * stage_vec;
+  uint64_t* wb = bars + LK_NUM_BARS + warp * LK_STAGES;
+  uint64_t wbeg, wend;
+  share(end - beg, (int)warp, (int)W, wbeg, wend);
+  wbeg += beg;
+  wend += beg;
+  const uint64_t total = wend - wbeg;
+  const uint64_t nch = (total + stage_vec - 1) / stage_vec;
+  /* the warp's rate: the CTA's, split evenly over its warps */
+  const uint64_t rate = pace.rate ? (pace.rate / W ? pace.rate / W : 1) : 0;
+  const uint64_t deadline = rate ? pace.deadline + total * 16u * 1000u / rate : pace.deadline;
+  const uint64_t t_first = rate && lane == 0 ? gtime() : 0;
+  auto parity = [&](uint64_t ch) {
+    return ((phase >> (LK_NUM_BARS + (uint32_t)(ch % LK_STAGES))) & 1u) ^ ((uint32_t)(ch / LK_STAGES) & 1u);
+  };
+  auto issue = [&](uint64_t ch) {   /* lane 0 only */
+    const uint32_t st = (uint32_t)(ch % LK_STAGES);
+    const uint64_t v0 = wbeg + ch * stage_vec;
+    const uint32_t nv = (uint32_t)((wend - v0) < stage_vec ? (wend - v0) : stage_vec);
+    mbar_expect_tx(&wb[st], nv * 16u);
+    bulk_g2s(ring + (size_t)st * stage_vec, in + v0, nv * 16u, &wb[st]);
+  };
+  if (lane == 0 && nch) {
+    fence_proxy_async_global();   /* earlier generic writes before these async reads */
+    fence_proxy_async_smem();     /* earlier generic shared accesses before async writes */
+    for (uint64_t ch = 0; ch < nch && ch < LK_STAGES; ++ch) issue(ch);
+  }
+  bool failed = false;
+  uint64_t ch = 0;
+  for (; ch < nch; ++ch) {
+    const uint32_t st = (uint32_t)(ch % LK_STAGES);
+    const bool ok = mbar_wait(&wb[st], parity(ch), deadline);
+    if (!__all_sync(0xffffffffu, ok)) {
+      failed = true;
+      break;
+    }
+    const uint64_t v0 = wbeg + ch * stage_vec;
+    const uint32_t cnt = (uint32_t)((wend - v0) < stage_vec ? (wend - v0) : stage_vec);
+    const uint4* s0 = ring + (size_t)st * stage_vec;
+    /* four vectors loaded before their 64 reductions: the reductions are
+     * ordered asm, so loads placed after them would wait for them */
+    uint32_t v = lane;
+    for (; v + 96 < cnt; v += 128) {
+      uint4 q[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = s0[v + 32 * i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        count4_row(lane_addr, q[i].x);
+        count4_row(lane_addr, q[i].y);
+        count4_row(lane_addr, q[i].z);
+        count4_row(lane_addr, q[i].w);
+      }
+    }
+    for (; v < cnt; v += 32) {
+      const uint4 q = s0[v];
+      count4_row(lane_addr, q.x);
+      count4_row(lane_addr, q.y);
+      count4_row(lane_addr, q.z);
+      count4_row(lane_addr, q.w);
+    }
+    __syncwarp();   /* every lane has read the stage before it is refilled */
+    if (lane == 0 && ch + LK_STAGES < nch) {
+      /* token bucket as deep as the ring: chunk k >= LK_STAGES no earlier
+       * than t_first + (k - LK_STAGES + 1) chunks' worth of time */
+      if (rate) sleep_until(t_first + (ch + 1) * (uint64_t)stage_vec * 16u * 1000u / rate);
+      fence_proxy_async_smem();
+      issue(ch + LK_STAGES);
+    }
+  }
+  /* a failed wait leaves the copies issued after it in flight: let them land */
+  const uint64_t issued = failed ? (ch + LK_STAGES < nch ? ch + LK_STAGES : nch) : nch;
+  if (lane == 0)
+    for (uint64_t c2 = ch; failed && c2 < issued; ++c2)
+      mbar_wait(&wb[c2 % LK_STAGES], parity(c2), deadline + 1000000000ull);
+  /* each issued chunk completed one phase of its stage's barrier */
+  for (uint32_t st = 0; st < LK_STAGES; ++st) {
+    const uint64_t uses = issued > st ? (issued - st + LK_STAGES - 1) / LK_STAGES : 0;
+    phase ^= (uint32_t)(uses & 1u) << (LK_NUM_BARS + st);
+  }
+  return !__syncthreads_or(failed);
+}
+
 template <int P>
 __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                           uint32_t& phase, Pace pace, uint32_t* acc) {
@@ -399,9 +534,29 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
     }
     return ok;
   }
-  /* large share: lane-private 32-bit counters, one set per copy; the
-   * W / copies warps of a copy share its words (their reductions to a word
-   * are atomic) */
+  if constexpr (P == 1) {
+    if (total * 16 >= LK_HIST_WARP_BYTES) {
+      /* large share, one CTA per SM: rows of 2 x 32 lane-private counters,
+       * warps w and w + 2 share copy w % 2 (their reductions are atomic) */
+      const uint32_t lane_addr = smem_addr(sh) + ((threadIdx.x >> 5) & 1u) * 128u + lane * 4u;
+      hist_zero(sh, 256u * 64u);
+      __syncthreads();
+      ok = hist_warp_streams<P>(reinterpret_cast<const uint4*>(d.in0), beg, end, dsm, bars, phase, lane_addr, pace);
+      if (tail)
+        for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T)
+          asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + ((uint32_t)xb[j] << 8))
+                       : "memory");
+      __syncthreads();
+      for (uint32_t v = threadIdx.x; v < 256; v += T) {
+        const uint32_t tot = hist_row_readout(sh, v);
+        if (tot) atomicAdd(&acc[v], tot);
+      }
+      return ok;
+    }
+  }
+  /* medium share, or two CTAs per SM: one ring for the CTA; lane-private
+   * 32-bit counters, one set per copy; the W / copies warps of a copy share
+   * its words (their reductions to a word are atomic) */
   constexpr uint32_t copies = SmemCfg<P>::hist_copies;
   const uint32_t copy = (threadIdx.x >> 5) % copies;
   const uint32_t lane_addr = smem_addr(sh + copy * 8192u + lane);

@@ -456,7 +456,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
   __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag */
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bars[LK_NUM_BARS];
+  __shared__ __align__(8) uint64_t s_bars[LK_ALL_BARS];
   __shared__ uint64_t s_tstart;
   const uint32_t tid = threadIdx.x;
 
@@ -542,7 +542,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     } else if (rk == 0) {
       st_relaxed_sys(&a.cword[c].status, LK_ST_INIT);
     }
-    for (uint32_t i = 0; i < LK_NUM_BARS; ++i) mbar_init(&s_bars[i], 1);
+    for (uint32_t i = 0; i < LK_ALL_BARS; ++i) mbar_init(&s_bars[i], 1);
     fence_barrier_init();
     red_release_sys_add(&a.ctrl->booted, 1u);
   }
@@ -715,13 +715,14 @@ template <int MAXT>
 __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch* sc) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ float s_red[32];
-  __shared__ __align__(8) uint64_t s_bars[LK_NUM_BARS];
+  __shared__ __align__(8) uint64_t s_bars[LK_ALL_BARS];
   __shared__ int32_t s_last;
   const int r = blockIdx.x, S = gridDim.x;
   const uint32_t op = d.cmd - LK_CMD_WORK;
   if (op == LK_OP_NOP) return;
-  if (threadIdx.x == 0) {
-    for (uint32_t i = 0; i < LK_NUM_BARS; ++i) mbar_init(&s_bars[i], 1);
+  /* the shared stage barriers and those of this block's warps, one per thread */
+  if (threadIdx.x < LK_NUM_BARS + (blockDim.x >> 5) * LK_STAGES) {
+    mbar_init(&s_bars[threadIdx.x], 1);
     fence_barrier_init();
   }
   __syncthreads();

@@ -63,6 +63,31 @@ def test_hist_bit_exact(torch_ready, oracle_lib, S, per_sm):
         assert np.array_equal(host(out).astype(np.int64), oracle_lib.hist_u8(x)), x.size
 
 
+@pytest.mark.parametrize("threads", [128, 256, 512, 1024])
+def test_hist_block_sizes_and_skew(torch_ready, oracle_lib, threads):
+    """Large shares stream through one ring per warp (its size depends on the
+    block size): many laps of every warp's ring, ragged warp parts, and skewed
+    inputs where the warps sharing a counter copy hit the same words."""
+    torch = torch_ready
+    n_big = (1 << 24) + 4099
+    xs = [synth.bytes_uniform(14, 0, n_big),
+          np.full(300_017, 201, np.uint8),                           # one bin only
+          (synth.bytes_uniform(14, 1, 1_000_003) & 3).astype(np.uint8),   # four bins
+          synth.bytes_uniform(14, 2, 16 * 1024 * 37 + 16)]          # just above the small-share cut
+    cases = [(x, to_dev(x), torch.full((256,), -1, dtype=torch.int32, device="cuda")) for x in xs]
+    torch.cuda.current_stream().synchronize()
+    for sizes in ([1], [37]):
+        for _, _, out in cases:
+            out.fill_(-1)
+        torch.cuda.current_stream().synchronize()
+        with lk.lk_init(sizes, idle_lease_ns=5_000_000_000, threads_per_cta=threads) as c:
+            hs = [lk.lk_submit(c, 0, lk.LK_OP_HIST_U8, x.size, (dx,), out) for x, dx, out in cases]
+            for h in hs:
+                assert lk.lk_wait(c, h) == lk.LK_OK
+        for x, _, out in cases:
+            assert np.array_equal(host(out).astype(np.int64), oracle_lib.hist_u8(x)), (sizes, x.size)
+
+
 @pytest.mark.parametrize("S,per_sm", SP)
 def test_sum_within_tolerance_and_exact_closed_form(torch_ready, oracle_lib, S, per_sm):
     torch = torch_ready

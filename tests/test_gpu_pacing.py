@@ -59,6 +59,28 @@ def test_paced_copy_takes_the_paced_time(torch_ready, oracle_lib):
     assert fast < want / 4
 
 
+def test_paced_histogram_takes_the_paced_time(torch_ready, oracle_lib):
+    """Large histogram shares stream through one ring per warp; the cap is
+    split evenly over the warps and still bounds the whole CTA's loads."""
+    torch = torch_ready
+    n = 1 << 26                                    # 64 MiB of bytes: 4 MiB per CTA
+    hb = synth.bytes_uniform(33, 0, n)
+    dh = to_dev(hb)
+    outs = [torch.zeros(256, dtype=torch.int32, device="cuda") for _ in range(2)]
+    torch.cuda.current_stream().synchronize()
+    rate = 20_000                                  # bytes/us over the cluster = 20 GB/s
+    with lk.lk_init([16], idle_lease_ns=5_000_000_000) as c:
+        fast = timed_wait(c, submit(c, 0, lk.LK_OP_HIST_U8, n, (dh,), outs[0]))
+        paced = timed_wait(c, submit(c, 0, lk.LK_OP_HIST_U8, n, (dh,), outs[1], aux=rate))
+    want = n / (rate * 1e6)
+    burst = 16 * 4 * 32768 / (rate * 1e6)          # the buckets: each warp's four stages
+    print(f"\nhistogram 64 MiB: unpaced {fast * 1e3:.2f} ms, paced {paced * 1e3:.2f} ms (cap {want * 1e3:.2f} ms)")
+    for o in outs:
+        assert np.array_equal(host(o).astype(np.int64), oracle_lib.hist_u8(hb))
+    assert paced >= want - burst - 1e-4 and paced < 2.0 * want
+    assert fast < want / 4
+
+
 def test_paced_bodies_match_oracle(torch_ready, oracle_lib):
     torch = torch_ready
     n = (1 << 20) + 13
