@@ -699,7 +699,7 @@ def main():
     line = {
         "metric": METRIC, "value": p99, "unit": "us", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": kms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32 / uint8->int32 / fp32 (GEMM tiles: split-TF32 on tcgen05, fp32 accumulate)",
+        "vs_baseline": None, "dtype": "int32 / uint8->int32 / fp32 (GEMM tiles: fp32 split into two bf16 parts on tcgen05, fp32 accumulate)",
         "data": "synthetic (seeded device pools)",
         "config": {"workload": WORKLOAD, "partition": "4 clusters x 37 SMs", "threads_per_cta": cfg["threads"],
                    "items_per_step": items_per_step, "rate_per_s": cfg["rate_per_s"],

@@ -81,7 +81,7 @@ extern "C" {
 #define LK_OP_HIST_U8    2 /* out[v] = #{i : in0[i] == v}; n bytes in, 256 int32 bins out (overwritten) */
 #define LK_OP_SUM_F32    3 /* out[0] = sum of n float32 (fixed order for a given n and cluster size) */
 #define LK_OP_GEMM64_F32 4 /* n tiles: out[t] = in0[t] x in1[t], 64x64 row-major float32 tiles;     */
-                           /* float32 FFMA, or split-TF32 tensor-core MMAs for whole tiles (see   */
+                           /* float32 FFMA, or split-bf16 tensor-core MMAs for whole tiles (see   */
                            /* LK_INIT_GEMM_FFMA); per element within 1e-4 sum_k |a b|              */
 #define LK_OP_COPY_I32   5 /* out[i] = in0[i], int32; n elements             */
 #define LK_OP_COMBINE_SUM  6 /* out[0] = binary64 sum of n float32 partials, one at the start of each */
@@ -161,9 +161,9 @@ typedef struct {
 #define LK_INIT_MAILBOX 2u
 /* LK_INIT_GEMM_FFMA: GEMM tiles always take the float32 FFMA path (k-order
  * fused multiply-adds, bit-reproducible).  Default: whole tiles at 256
- * threads with one CTA per SM run on the tensor cores with split-TF32
- * operands (each product's error of order 2^-21 |a||b|, inside the GEMM
- * bound 1e-4 sum_k |a b|); tiles split across CTAs always take FFMA. */
+ * threads with one CTA per SM run on the tensor cores with operands split
+ * into two bf16 parts (each product formed to within 2^-15 |a||b|, inside
+ * the GEMM bound 1e-4 sum_k |a b|); tiles split across CTAs always take FFMA. */
 #define LK_INIT_GEMM_FFMA 4u
 
 /* A work descriptor.  The in/out pointers travel beside it. */

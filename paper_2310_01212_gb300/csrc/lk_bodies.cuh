@@ -28,7 +28,7 @@
  *             rank 0 adds the partials in rank order in binary64
  *   gemm64    64x64x64 float32 tiles staged into shared memory by TMA bulk
  *             copies.  Whole tiles (one CTA per SM, 256 threads): tcgen05
- *             tensor cores on split-TF32 operands.  Row blocks and other
+ *             tensor cores on split-bf16 operands.  Row blocks and other
  *             shapes: six 32 KB stages (three with two CTAs per SM), 4x4
  *             register micro-tiles, FFMA in k order
  * Used by the persistent kernel and by the ordinary-launch baseline kernels.
@@ -673,17 +673,19 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
  * 16 KB) over the whole dynamic shared memory; one mbarrier per stage. */
 
 /* ---- the GEMM tile on the 5th-generation tensor cores ------------------- */
-/* C = A B for whole 64x64x64 float32 tiles, with tcgen05.mma kind::tf32
- * (tensor-core products of 19-bit floats, float32 accumulation in TMEM).
- * One TF32 product per element pair would miss the 1e-4 sum|a b| bound, so
- * every operand is split: x = x_hi + x_lo with x_hi = x truncated to TF32 and
- * x_lo = x - x_hi (exact).  The A operand stacks A_hi (rows 0-63) on A_lo
- * (rows 64-127) and the B operand B_hi (columns 0-63) on B_lo (64-127), so
- * one chain of eight MMAs over K (M = 128, N = 128; TMEM rows are lanes
- * 0-127, one to one) yields all four products in a 128 x 128 block D, and
- * C[r][n] = D[r][n] + D[r][n+64] + D[r+64][n] + D[r+64][n+64] (the TF32
- * truncation of x_lo inside the MMA leaves errors of order 2^-21 |a||b| per
- * product).
+/* C = A B for whole 64x64x64 float32 tiles, with tcgen05.mma kind::f16 on
+ * bf16 operands (exact products, float32 accumulation in TMEM).  One bf16
+ * (or TF32) product per element pair would miss the 1e-4 sum|a b| bound, so
+ * every operand is split in two: x_hi = bf16(x) and x_lo = bf16(x - x_hi),
+ * both rounded to nearest; x - x_hi is exact in float32, and x_hi + x_lo
+ * differs from x by at most 2^-16 |x|, so each product a b is formed to
+ * within about 2^-15 |a b| (3.1e-5, against the 1e-4 bound; accumulation
+ * adds at most 64 float32 roundings).  The A operand stacks A_hi (rows 0-63)
+ * on A_lo (rows 64-127) and the B operand B_hi (columns 0-63) on B_lo
+ * (64-127), so one chain of four MMAs over K (M = 128, N = 128, K = 16;
+ * TMEM rows are lanes 0-127, one to one) yields all four products in a
+ * 128 x 128 block D, and
+ * C[r][n] = D[r][n] + D[r][n+64] + D[r+64][n] + D[r+64][n+64].
  * Two pipelines, one per half of the CTA (warps 0-3 and 4-7, each with its
  * own operand buffer, TMEM block and named barrier), take alternate tiles:
  * while one half waits for its MMAs and stores its tile, the other splits
@@ -691,22 +693,34 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
  * (u - first) mod 3, and the half that split tile u refills that stage with
  * tile u+3.
  * Shared memory (224 KB): three 32 KB TMA stages of raw tiles (A rows, B) at
- * 0; two 64 KB operand buffers at 96 KB (A_hi, A_lo, B_hi, B_lo, 16 KB each,
- * in the K-major core-matrix layout the descriptors name).  TMEM: two blocks
- * of 128 columns, allocated for the body and freed on every path out of it. */
+ * 0; two 64 KB buffers at 96 KB, one per half: the operands (A' then B',
+ * 16 KB each, in the K-major core-matrix layout the descriptors name), and
+ * the epilogue's row exchange once the MMAs have read them.  TMEM: two
+ * blocks of 128 columns, allocated for the body and freed on every path out
+ * of it. */
 #define LK_TC_SMEM (224u * 1024u)
 #define LK_TC_STAGES 3u
 #define LK_TC_MMA_BAR 6u             /* bars 6 and 7: MMA completion of halves 0 and 1 */
 #define LK_TC_OPS (96u * 1024u)
-/* instruction descriptor: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9,
- * 10-12 = 2), both K-major, N = 128 (bits 17-22 = N/8), M = 128 (bits 24-28 = M/16) */
-#define LK_TC_IDESC ((1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
+/* instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16 (bits 7-9,
+ * 10-12 = 1), both K-major, N = 128 (bits 17-22 = N/8), M = 128 (bits 24-28 = M/16) */
+#define LK_TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
 
-__device__ __forceinline__ float4 tf32_hi(float4 x) {
-  return make_float4(__uint_as_float(__float_as_uint(x.x) & 0xffffe000u), __uint_as_float(__float_as_uint(x.y) & 0xffffe000u),
-                     __uint_as_float(__float_as_uint(x.z) & 0xffffe000u), __uint_as_float(__float_as_uint(x.w) & 0xffffe000u));
+/* (x0, x1) -> bf16 pairs hi = bf16(x), lo = bf16(x - hi), x0 in the low half */
+__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(x1), "f"(x0));
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(x1 - h1), "f"(x0 - h0));
 }
-__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+/* Eight consecutive k of one operand row (x0: k..k+3, x1: k+4..k+7) -> one
+ * 16-byte core-matrix row of hi parts and one of lo parts. */
+__device__ __forceinline__ void bf16_split8(float4 x0, float4 x1, uint4& hi, uint4& lo) {
+  bf16_split2(x0.x, x0.y, hi.x, lo.x);
+  bf16_split2(x0.z, x0.w, hi.y, lo.y);
+  bf16_split2(x1.x, x1.y, hi.z, lo.z);
+  bf16_split2(x1.z, x1.w, hi.w, lo.w);
+}
 
 /* Column e of the 4x4 block q[0..3] (rows k..k+3): the K-chunk of output column n = 4 n4 + e. */
 __device__ __forceinline__ float4 column_of(const float4* q, uint32_t e) {
@@ -719,39 +733,42 @@ __device__ __forceinline__ float4 column_of(const float4* q, uint32_t e) {
 }
 
 /* The 128 threads of one half (local index t): split the staged raw tile
- * (A rows at `raw`, B at raw + 16 KB) into an operand buffer.  The
- * core-matrix offset of (row i, K-chunk k4) is (i/8) 2048 + k4 128 + (i%8) 16
- * bytes.  The thread-to-chunk maps make each 8-thread phase of a 128-bit
- * access touch eight distinct 16-byte bank groups, on the raw side and on
- * the operand side. */
+ * (A rows at `raw`, B at raw + 16 KB) into an operand buffer.  A core matrix
+ * is 8 rows of 8 bf16 (16 bytes); the offset of (row i, K-chunk kc = k/8) is
+ * (i/8) 1024 + kc 128 + (i%8) 16 bytes.  The thread-to-chunk maps make each
+ * 8-thread phase of a 128-bit access touch eight distinct 16-byte bank
+ * groups, on the raw side and on the operand side. */
 __device__ __forceinline__ void tc_split(const unsigned char* raw, unsigned char* ops, uint32_t t) {
 #pragma unroll
-  for (uint32_t q = 0; q < 8; ++q) {                 /* A: 1024 chunks of 4 floats */
+  for (uint32_t q = 0; q < 4; ++q) {                 /* A: 512 chunks of 8 k */
     const uint32_t c = t + 128u * q;
-    const uint32_t j = c & 7u, s = (c >> 3) & 7u, h = (c >> 6) & 1u, ig = c >> 7;
-    const uint32_t i = ig * 8u + j, k4 = ((j + s) & 7u) + 8u * h;
-    const float4 x = *reinterpret_cast<const float4*>(raw + i * 256u + k4 * 16u);
-    const float4 hi = tf32_hi(x);
-    const uint32_t off = ig * 2048u + k4 * 128u + j * 16u;
-    *reinterpret_cast<float4*>(ops + off) = hi;                        /* A_hi */
-    *reinterpret_cast<float4*>(ops + 16384u + off) = sub4(x, hi);      /* A_lo */
+    const uint32_t j = c & 7u, s = (c >> 3) & 7u, ig = c >> 6;
+    const uint32_t i = ig * 8u + j, kc = (j + s) & 7u, h = (kc >> 2) & 1u;
+    const unsigned char* src = raw + i * 256u + kc * 32u;
+    /* the half at 16 h first: distinct bank groups across the phase */
+    const float4 xa = *reinterpret_cast<const float4*>(src + h * 16u);
+    const float4 xb = *reinterpret_cast<const float4*>(src + (h ^ 1u) * 16u);
+    uint4 hi, lo;
+    bf16_split8(h ? xb : xa, h ? xa : xb, hi, lo);
+    const uint32_t off = ig * 1024u + kc * 128u + j * 16u;
+    *reinterpret_cast<uint4*>(ops + off) = hi;                         /* A_hi: rows 0-63 */
+    *reinterpret_cast<uint4*>(ops + 8192u + off) = lo;                 /* A_lo: rows 64-127 */
   }
-#pragma unroll
-  for (uint32_t q = 0; q < 2; ++q) {                 /* B: 256 blocks of 4 k x 4 n, transposed */
-    const uint32_t blk = t + 128u * q, n4 = blk & 15u, kb = blk >> 4;
+  {                                                  /* B: 128 blocks of 8 k x 4 n, transposed */
+    const uint32_t n4 = t & 15u, kb = t >> 4;
     const unsigned char* rb = raw + 16384u;
-    float4 v[4];
+    float4 v[8];
 #pragma unroll
-    for (uint32_t m = 0; m < 4; ++m) v[m] = *reinterpret_cast<const float4*>(rb + (4u * kb + m) * 256u + n4 * 16u);
+    for (uint32_t m = 0; m < 8; ++m) v[m] = *reinterpret_cast<const float4*>(rb + (8u * kb + m) * 256u + n4 * 16u);
 #pragma unroll
     for (uint32_t te = 0; te < 4; ++te) {
       const uint32_t e = (te + (n4 >> 1)) & 3u;      /* rotated: distinct bank groups per phase */
       const uint32_t n = 4u * n4 + e;
-      const float4 x = column_of(v, e);
-      const float4 hi = tf32_hi(x);
-      const uint32_t off = (n >> 3) * 2048u + kb * 128u + (n & 7u) * 16u;
-      *reinterpret_cast<float4*>(ops + 32768u + off) = hi;               /* B_hi */
-      *reinterpret_cast<float4*>(ops + 49152u + off) = sub4(x, hi);      /* B_lo */
+      uint4 hi, lo;
+      bf16_split8(column_of(v, e), column_of(v + 4, e), hi, lo);
+      const uint32_t off = (n >> 3) * 1024u + kb * 128u + (n & 7u) * 16u;
+      *reinterpret_cast<uint4*>(ops + 16384u + off) = hi;              /* B_hi: rows 0-63 */
+      *reinterpret_cast<uint4*>(ops + 24576u + off) = lo;              /* B_lo: rows 64-127 */
     }
   }
 }
@@ -819,7 +836,7 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
   tc_fence_after_sync();
   const uint32_t dt = s_tmem + 128u * h;
   unsigned char* ops = dsm + LK_TC_OPS + h * 65536u;
-  const uint32_t ah = smem_addr(ops), bh = ah + 32768u;
+  const uint32_t ah = smem_addr(ops), bh = ah + 16384u;
   /* epilogue: warp quarter q holds D rows 32q..32q+31 (rows 64-127 are the
    * A_lo products of output rows 0-63) */
   const uint32_t quarter = warp & 3u;
@@ -862,8 +879,8 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
       }
       tc_fence_after_sync();
 #pragma unroll
-      for (uint32_t j = 0; j < 8; ++j)
-        umma_tf32(dt, umma_desc(ah + 256u * j, 128u, 2048u), umma_desc(bh + 256u * j, 128u, 2048u), LK_TC_IDESC, j > 0);
+      for (uint32_t j = 0; j < 4; ++j)
+        umma_f16(dt, umma_desc(ah + 256u * j, 128u, 1024u), umma_desc(bh + 256u * j, 128u, 1024u), LK_TC_IDESC, j > 0);
       umma_commit(&bars[LK_TC_MMA_BAR + h]);
     }
     /* epilogue: every warp folds its rows' column halves (B_hi and B_lo

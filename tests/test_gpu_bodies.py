@@ -132,10 +132,11 @@ def test_gemm_tiles(torch_ready, oracle_lib, S, per_sm):
         assert gemm_ok(host(dC), A, B, oracle_lib), A.shape
     # identity tile: exact on the FFMA path (row blocks of split tiles, or two
     # CTAs per SM); whole tiles with one CTA per SM run on the tensor cores,
-    # where B = B_hi + B_lo comes back with B_lo truncated to TF32 (|err| <= 2^-20 |b|)
+    # where B comes back as B_hi + B_lo, two bf16 parts rounded to nearest
+    # (|err| <= 2^-17 |b| for the pair, plus the float32 rounding of the sum)
     got = host(cases[-1][4])
     if per_sm == 1 and S <= 3:
-        assert np.all(np.abs(got - B) <= 2.0 ** -20 * np.abs(B)), np.max(np.abs(got - B) / np.abs(B))
+        assert np.all(np.abs(got - B) <= 2.0 ** -16 * np.abs(B)), np.max(np.abs(got - B) / np.abs(B))
     else:
         assert np.array_equal(got, B)
 
@@ -165,7 +166,7 @@ def test_gemm_ffma_flag(torch_ready, oracle_lib, S):
             assert np.array_equal(host(o_ib), B)
         else:
             got = host(o_ib)
-            assert np.all(np.abs(got - B) <= 2.0 ** -20 * np.abs(B))
+            assert np.all(np.abs(got - B) <= 2.0 ** -16 * np.abs(B))
 
 
 def test_misaligned_pointers_rejected_on_host(torch_ready):
