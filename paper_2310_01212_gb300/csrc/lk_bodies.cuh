@@ -687,20 +687,23 @@ __device__ __forceinline__ uint32_t gemm_row_split(uint64_t tiles, int S) {
  * 128 x 128 block D, and
  * C[r][n] = D[r][n] + D[r][n+64] + D[r+64][n] + D[r+64][n+64].
  * Two pipelines, one per half of the CTA (warps 0-3 and 4-7, each with its
- * own operand buffer, TMEM block and named barrier), take alternate tiles:
- * while one half waits for its MMAs and stores its tile, the other splits
- * the next one.  The TMA stage ring is shared: tile u sits in stage
- * (u - first) mod 3, and the half that split tile u refills that stage with
- * tile u+3.
+ * own named barrier), take alternate tiles.  Each half has two buffers
+ * (operands in shared memory, a 128 x 128 block in TMEM, an MMA-completion
+ * mbarrier) and alternates between them: it splits tile k into buffer
+ * k mod 2, hands it to the tensor core, and finishes tile k-1 (TMEM read-out,
+ * row exchange, stores) while those MMAs run, so the tensor core's latency
+ * hides behind the epilogue.  The TMA stage ring is shared: tile u sits in
+ * stage (u - first) mod 3, and the half that split tile u refills that stage
+ * with tile u+3.
  * Shared memory (224 KB): three 32 KB TMA stages of raw tiles (A rows, B) at
- * 0; two 64 KB buffers at 96 KB, one per half: the operands (A' then B',
- * 16 KB each, in the K-major core-matrix layout the descriptors name), and
- * the epilogue's row exchange once the MMAs have read them.  TMEM: two
- * blocks of 128 columns, allocated for the body and freed on every path out
- * of it. */
+ * 0; four 32 KB buffers at 96 KB, two per half: the operands (A' then B',
+ * 16 KB each, in the K-major core-matrix layout the descriptors name), then
+ * the epilogue's row exchange once the MMAs have read them.  TMEM: all 512
+ * columns (four blocks of 128), allocated for the body and freed on every
+ * path out of it. */
 #define LK_TC_SMEM (224u * 1024u)
 #define LK_TC_STAGES 3u
-#define LK_TC_MMA_BAR 6u             /* bars 6 and 7: MMA completion of halves 0 and 1 */
+#define LK_TC_MMA_BAR 4u             /* bars 4-7: MMA completion of (half, buffer) 2 h + b */
 #define LK_TC_OPS (96u * 1024u)
 /* instruction descriptor: D float32 (bits 4-5 = 1), A and B bf16 (bits 7-9,
  * 10-12 = 1), both K-major, N = 128 (bits 17-22 = N/8), M = 128 (bits 24-28 = M/16) */
@@ -823,7 +826,7 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
    * waits for that load's phase */
   __shared__ uint32_t s_issued[LK_TC_STAGES];
   __syncthreads();          /* every stage is free: the previous use ended with a barrier */
-  if (warp == 0) tmem_alloc(&s_tmem, 256);
+  if (warp == 0) tmem_alloc(&s_tmem, 512);
   if (threadIdx.x == 0) {
     for (uint32_t sb = 0; sb < LK_TC_STAGES; ++sb) s_issued[sb] = 0;
     for (uint64_t u = beg; u < end && u < beg + LK_TC_STAGES; ++u) {
@@ -834,18 +837,61 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
-  const uint32_t dt = s_tmem + 128u * h;
-  unsigned char* ops = dsm + LK_TC_OPS + h * 65536u;
-  const uint32_t ah = smem_addr(ops), bh = ah + 16384u;
+  /* this half's two buffers b: TMEM block dt0 + 128 b, shared memory
+   * ops0 + 32 KB b (operands, then the epilogue's row exchange) */
+  const uint32_t dt0 = s_tmem + 256u * h;
+  unsigned char* ops0 = dsm + LK_TC_OPS + h * 65536u;
   /* epilogue: warp quarter q holds D rows 32q..32q+31 (rows 64-127 are the
    * A_lo products of output rows 0-63) */
   const uint32_t quarter = warp & 3u;
   const uint32_t drow = 32u * quarter + lane;
+  /* Tile u, the kk-th of this half, in buffer b = kk & 1: wait for its MMAs,
+   * fold each row's column halves (B_hi and B_lo products) into the buffer,
+   * rows 0-63 at `part`, rows 64-127 at part + 64 x 64 (16-byte chunk c of
+   * row i at position c ^ (i & 7): no bank conflicts on either side), then
+   * add the two parts and store the tile in coalesced 128-bit stores.
+   * Returns false, on all 128 threads alike, if the MMAs did not complete
+   * in time; on return the buffer and its TMEM block are free again. */
+  auto epilogue = [&](uint64_t u, uint64_t kk) -> bool {
+    const uint32_t b = (uint32_t)(kk & 1u), bar = LK_TC_MMA_BAR + 2u * h + b;
+    float* part = reinterpret_cast<float*>(ops0 + 32768u * b);
+    bool done = mbar_wait(&bars[bar], parity(bar, kk >> 1), deadline + 1000000000ull);
+    if (done) {
+      tc_fence_after_sync();
+      float* prow = part + drow * 64u;
+      const uint32_t sw = drow & 7u;
+#pragma unroll
+      for (uint32_t c0 = 0; c0 < 64; c0 += 32) {
+        float v[32], w[32];
+        tmem_ld32(dt0 + 128u * b + ((32u * quarter) << 16) + c0, v);
+        tmem_ld32(dt0 + 128u * b + ((32u * quarter) << 16) + c0 + 64u, w);
+#pragma unroll
+        for (uint32_t c = 0; c < 32; c += 4)
+          *reinterpret_cast<float4*>(prow + ((((c0 + c) >> 2) ^ sw) << 2)) =
+              make_float4(v[c] + w[c], v[c + 1] + w[c + 1], v[c + 2] + w[c + 2], v[c + 3] + w[c + 3]);
+      }
+    }
+    tc_fence_before_sync();         /* these TMEM reads precede this block's next MMAs */
+    if (half_sync_and(h, done)) {
+      float* ct = C + u * 4096;
+#pragma unroll
+      for (uint32_t q = 0; q < 8; ++q) {
+        const uint32_t f = lt + 128u * q, i = f >> 4, c4 = f & 15u, pos = (c4 ^ (i & 7u)) << 2;
+        const float4 x = *reinterpret_cast<const float4*>(part + i * 64u + pos);
+        const float4 y = *reinterpret_cast<const float4*>(part + (i + 64u) * 64u + pos);
+        st_stream(reinterpret_cast<float4*>(ct + i * 64u + c4 * 4u), make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w));
+      }
+    } else {
+      done = false;
+    }
+    return half_sync_and(h, done);
+  };
   bool ok = true;
-  uint64_t k = 0;                  /* tiles this half has finished */
+  uint64_t k = 0;                  /* tiles this half has split and handed to the tensor core */
   for (uint64_t u = beg + h; u < end; u += 2, ++k) {
     const uint32_t st = (uint32_t)((u - beg) % LK_TC_STAGES);
     const uint64_t use = (u - beg) / LK_TC_STAGES;   /* completions of stage st before this one */
+    const uint32_t b = (uint32_t)(k & 1u);
     bool go = true;
     if (leader) {
       const volatile uint32_t* iss = s_issued;
@@ -865,6 +911,7 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
       break;
     }
     mbar_wait(&bars[st], parity(st, use), deadline + 1000000000ull);   /* complete: visibility */
+    unsigned char* ops = ops0 + 32768u * b;
     tc_split(dsm + st * 32768u, ops, lt);
     fence_proxy_async_smem();       /* the operands, written by threads, are read by the tensor core */
     tc_fence_before_sync();
@@ -878,58 +925,32 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
         atomicAdd(&s_issued[st], 1u);
       }
       tc_fence_after_sync();
+      const uint32_t ah = smem_addr(ops), bh = ah + 16384u;
 #pragma unroll
       for (uint32_t j = 0; j < 4; ++j)
-        umma_f16(dt, umma_desc(ah + 256u * j, 128u, 1024u), umma_desc(bh + 256u * j, 128u, 1024u), LK_TC_IDESC, j > 0);
-      umma_commit(&bars[LK_TC_MMA_BAR + h]);
+        umma_f16(dt0 + 128u * b, umma_desc(ah + 256u * j, 128u, 1024u), umma_desc(bh + 256u * j, 128u, 1024u),
+                 LK_TC_IDESC, j > 0);
+      umma_commit(&bars[LK_TC_MMA_BAR + 2u * h + b]);
     }
-    /* epilogue: every warp folds its rows' column halves (B_hi and B_lo
-     * products) and parks them in the operand buffer, free once the MMAs
-     * completed: rows 0-63 at `part`, rows 64-127 at part + 64 x 68 (rows
-     * padded to 68 floats: no bank conflicts); then the 128 threads add the
-     * two parts and store the tile in coalesced 128-bit stores */
-    float* part = reinterpret_cast<float*>(ops);
-    bool done = mbar_wait(&bars[LK_TC_MMA_BAR + h], parity(LK_TC_MMA_BAR + h, k), deadline + 1000000000ull);
-    if (done) {
-      tc_fence_after_sync();
-      float* prow = part + drow * 68u;
-#pragma unroll
-      for (uint32_t c0 = 0; c0 < 64; c0 += 32) {
-        float v[32], w[32];
-        tmem_ld32(dt + ((32u * quarter) << 16) + c0, v);
-        tmem_ld32(dt + ((32u * quarter) << 16) + c0 + 64u, w);
-#pragma unroll
-        for (uint32_t c = 0; c < 32; c += 4)
-          *reinterpret_cast<float4*>(prow + c0 + c) = make_float4(v[c] + w[c], v[c + 1] + w[c + 1], v[c + 2] + w[c + 2], v[c + 3] + w[c + 3]);
-      }
-    }
-    tc_fence_before_sync();         /* these TMEM reads precede this half's next MMAs */
-    if (half_sync_and(h, done)) {
-      float* ct = C + u * 4096;
-#pragma unroll
-      for (uint32_t q = 0; q < 8; ++q) {
-        const uint32_t f = lt + 128u * q, i = f >> 4, c4 = f & 15u;
-        const float4 x = *reinterpret_cast<const float4*>(part + i * 68u + c4 * 4u);
-        const float4 y = *reinterpret_cast<const float4*>(part + (i + 64u) * 68u + c4 * 4u);
-        st_stream(reinterpret_cast<float4*>(ct + i * 64u + c4 * 4u), make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w));
-      }
-    } else {
-      done = false;
-    }
-    if (!half_sync_and(h, done)) {  /* the operand buffer and TMEM block are free again */
+    /* while the tensor core works on tile u, finish the previous tile */
+    if (k > 0 && !epilogue(u - 2, k - 1)) {
       ok = false;
       ++k;
       break;
     }
   }
-  /* MMAs of a failed tile may still be in flight: let them finish (bounded)
-   * before TMEM is freed */
-  if (!ok && leader && k > 0)
-    mbar_wait(&bars[LK_TC_MMA_BAR + h], parity(LK_TC_MMA_BAR + h, k - 1), deadline + 2000000000ull);
+  if (ok && k > 0 && !epilogue(beg + h + 2 * (k - 1), k - 1)) ok = false;
+  /* MMAs of an unfinished tile may still be in flight: the last commit
+   * covers every earlier MMA, so let it complete (bounded) before TMEM is
+   * freed */
+  if (!ok && leader && k > 0) {
+    const uint32_t bar = LK_TC_MMA_BAR + 2u * h + (uint32_t)((k - 1) & 1u);
+    mbar_wait(&bars[bar], parity(bar, (k - 1) >> 1), deadline + 2000000000ull);
+  }
   tc_fence_before_sync();
   __syncthreads();          /* both halves done: stages and operand buffers are free */
   tc_fence_after_sync();
-  if (warp == 0) tmem_dealloc(s_tmem, 256);
+  if (warp == 0) tmem_dealloc(s_tmem, 512);
   /* every thread advances every barrier's phase bit by its completions here */
   if (ok) {
     for (uint32_t sb = 0; sb < LK_TC_STAGES; ++sb) {
@@ -938,7 +959,10 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
     }
     for (uint32_t hh = 0; hh < 2; ++hh) {
       const uint64_t mine = tiles > hh ? (tiles - hh + 1) / 2 : 0;
-      phase ^= (uint32_t)(mine & 1u) << (LK_TC_MMA_BAR + hh);
+      for (uint32_t bb = 0; bb < 2; ++bb) {
+        const uint64_t commits = mine > bb ? (mine - bb + 1) / 2 : 0;
+        phase ^= (uint32_t)(commits & 1u) << (LK_TC_MMA_BAR + 2u * hh + bb);
+      }
     }
   }
   return ok;
