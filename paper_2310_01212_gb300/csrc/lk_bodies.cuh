@@ -386,6 +386,19 @@ __device__ __forceinline__ void count4_row(uint32_t lane_addr, uint32_t w) {
   }
 }
 
+/* The 16 bytes of one vector: every address is formed before the first
+ * reduction, so the reductions issue back to back. */
+__device__ __forceinline__ void count16_row(uint32_t lane_addr, uint4 q) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t a[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) a[4 * i + b] = lane_addr + __byte_perm(w[i], 0u, 0x4404u | ((uint32_t)b << 4));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(a[j]) : "memory");
+}
+
 /* Thread v (< 256) adds row v (both copies, 32 lanes each); each 8-thread
  * phase of the 128-bit loads starts at thread-dependent columns and so
  * touches all 32 banks once. */
@@ -462,20 +475,9 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
 #pragma unroll
       for (int i = 0; i < 4; ++i) q[i] = s0[v + 32 * i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        count4_row(lane_addr, q[i].x);
-        count4_row(lane_addr, q[i].y);
-        count4_row(lane_addr, q[i].z);
-        count4_row(lane_addr, q[i].w);
-      }
+      for (int i = 0; i < 4; ++i) count16_row(lane_addr, q[i]);
     }
-    for (; v < cnt; v += 32) {
-      const uint4 q = s0[v];
-      count4_row(lane_addr, q.x);
-      count4_row(lane_addr, q.y);
-      count4_row(lane_addr, q.z);
-      count4_row(lane_addr, q.w);
-    }
+    for (; v < cnt; v += 32) count16_row(lane_addr, s0[v]);
     __syncwarp();   /* every lane has read the stage before it is refilled */
     if (lane == 0 && ch + LK_STAGES < nch) {
       /* token bucket as deep as the ring: chunk k >= LK_STAGES no earlier
