@@ -61,3 +61,15 @@ def test_reference_arm_under_torchrun(oracle_lib):
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
     assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_submitter_cores_are_disjoint_per_rank(monkeypatch):
+    """Each local rank pins its four submitting threads to its own cores, and
+    leaves them unpinned when those cores are not in the process's set."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setattr(os, "sched_getaffinity", lambda pid: set(range(16)))
+    assert [bench.submitter_cpus(r) for r in range(4)] == [2, 6, 10, -1]
+    monkeypatch.setattr(os, "sched_getaffinity", lambda pid: {0, 1, 2, 3})
+    assert bench.submitter_cpus(0) == -1
