@@ -215,6 +215,22 @@ def time_oracle(items, budget_s: float):
     return np.array(out)
 
 
+def time_oracle_pool(items, workers: int) -> float:
+    """Items per second of the oracle over `items` on `workers` host threads
+    (its C routines run without the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2310_01212_gb300 import lk
+
+    fns = {lk.LK_OP_ADD_I32: oracle.add_i32, lk.LK_OP_HIST_U8: oracle.hist_u8, lk.LK_OP_SUM_F32: oracle.sum_f32,
+           lk.LK_OP_GEMM64_F32: oracle.gemm64_f32}
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        n = sum(1 for _ in ex.map(lambda it: fns[it[0]](*it[1:]), items))
+    return n / (time.perf_counter() - t0)
+
+
 def run_reference(args, dist: Dist):
     """The oracle, as it stands, on the host cores: same metric and workload."""
     import oracle
@@ -700,10 +716,16 @@ def main():
         import oracle as _o
 
         _o.build()
-        us = time_oracle(oracle_sample(424242, 400), budget_s=15.0)
+        sample = oracle_sample(424242, 400)
+        us = time_oracle(sample, budget_s=15.0)
+        names = ["add_i32", "hist_u8", "sum_f32", "gemm64_f32"]   # the sample cycles through the bodies
+        workers = host_info()["cores"]
         cpu = {"value": pct(us, 0.99), "unit": "us", "cores": 1, "kind": "oracle",
                "sample": f"{us.size} items of the workload's body mix (equal shares), per-item time, one host thread",
-               "p50": pct(us, 0.5)}
+               "p50": pct(us, 0.5),
+               "per_body_p50_us": {nm: pct(us[j::4], 0.5) for j, nm in enumerate(names) if us[j::4].size},
+               "all_cores": {"items_per_s": time_oracle_pool(sample, workers), "threads": workers,
+                             "sample": f"the same {len(sample)} items on a thread pool"}}
 
     p99 = dist.max(pct(lat, 0.99))
     mx = dist.max(pct(lat, 1.0))
