@@ -102,6 +102,9 @@ extern "C" {
 #define LK_DERR_STALL    4 /* a CTA waited too long for its cluster master   */
 #define LK_DERR_BADDESC  5 /* descriptor failed the device-side check        */
 #define LK_DERR_STAGING  6 /* a shared-memory staging copy did not complete in time */
+#define LK_DERR_BOUNDS   7 /* bounds-checking build (liblk_bounds.so) only: a body's index or   */
+                           /* address fell outside its operand, share or shared-memory region; */
+                           /* the access was skipped (see lk_bounds_violations)                 */
 
 typedef struct lk_ctx lk_ctx;   /* opaque; owned by the library */
 
@@ -500,6 +503,24 @@ int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms);
  * Returns LK_OK (launched), LK_EINVAL, LK_EDEVICE (CUDA error). */
 int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
                       int ctas, int threads, void* stream);
+
+/* ---- the bounds-checking build ---------------------------------------- */
+/* liblk_bounds.so is this library compiled with -DLK_DEBUG_BOUNDS: every
+ * body checks, before each global-memory access path and shared-memory or
+ * TMEM region it uses, that the index or address lies inside the operand
+ * (as the descriptor's n sizes it), the CTA's or warp's share, and the
+ * region, and that vector and TMA addresses are 16-byte aligned.  A failed
+ * check skips the access (a skipped TMA copy completes its barrier phase
+ * with no bytes), counts a violation, records the first site (LK_OOB_*
+ * values of lk_device.cuh: 1 share, 2 staged load, 3 stage region, 4 store,
+ * 5 histogram counter, 6 GEMM load, 7 GEMM store, 8 GEMM shared memory or
+ * TMEM) and makes that descriptor end with LK_DERR_BOUNDS (lk_wait returns
+ * LK_EDEVICE).  It stands in for a device memory checker.
+ *   device: CUDA ordinal.  count, first_site: out.  Read it with no context
+ *   running on the device (the read is an ordinary synchronous copy).
+ * Returns LK_OK; LK_EINVAL in the product build (liblk.so) or for NULL
+ * outputs; LK_EDEVICE (CUDA error). */
+int lk_bounds_violations(int device, uint64_t* count, uint32_t* first_site);
 
 /* Host-mapped round-trip floor: one host thread release-stores a counter, one
  * GPU thread acquire-spins on it and release-stores an echo, the host

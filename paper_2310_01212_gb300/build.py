@@ -3,6 +3,9 @@
 * liblk.so       the product: persistent kernel + host runtime, sm_103a only.
 * liblk_fake.so  test build of the same host runtime over a host-thread
                  stand-in for the GPU (no CUDA needed to run it).
+* liblk_bounds.so  test build of liblk.so with -DLK_DEBUG_BOUNDS: every body
+                 checks its indexes and addresses and skips an access that
+                 would leave its operand or region (lk_bounds_violations).
 
 nvcc compiles the CUDA translation unit while g++ compiles the host runtime,
 in parallel; nothing here uses cmake.
@@ -18,6 +21,7 @@ OUT = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(OUT, "liblk.so")
+BOUNDS = os.path.join(OUT, "liblk_bounds.so")
 FAKE = os.path.join(OUT, "liblk_fake.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
@@ -52,20 +56,26 @@ def _run_all(cmds):
         raise RuntimeError("native build failed:\n" + "\n".join(errs))
 
 
-def build(force: bool = False, fake: bool = True, cuda: bool = True) -> None:
+def build(force: bool = False, fake: bool = True, cuda: bool = True, bounds: bool = True) -> None:
     os.makedirs(OUT, exist_ok=True)
     pid = os.getpid()
     cmds, moves = [], []
     need_cuda = cuda and (force or _stale(LIB))
     need_fake = fake and (force or _stale(FAKE))
+    need_bounds = cuda and bounds and (force or _stale(BOUNDS))
     common = ["-O3", "-std=c++17", f"-I{INCLUDE}", f"-I{CSRC}"]
-    if need_cuda:
-        ko = os.path.join(OUT, f"lk_kernel.{pid}.o")
-        ro = os.path.join(OUT, f"lk_runtime.{pid}.o")
-        cmds.append([_nvcc(), "-gencode", GENCODE, "-lineinfo", *common, "-Xcompiler", "-fPIC",
-                     "-c", os.path.join(CSRC, "lk_kernel.cu"), "-o", ko])
+    ro = os.path.join(OUT, f"lk_runtime.{pid}.o")
+    if need_cuda or need_bounds:
         cmds.append(["g++", *common, "-fPIC", "-Wall", "-c", os.path.join(CSRC, "lk_runtime.cpp"),
                      "-I/usr/local/cuda/include", "-o", ro])
+    if need_cuda:
+        ko = os.path.join(OUT, f"lk_kernel.{pid}.o")
+        cmds.append([_nvcc(), "-gencode", GENCODE, "-lineinfo", *common, "-Xcompiler", "-fPIC",
+                     "-c", os.path.join(CSRC, "lk_kernel.cu"), "-o", ko])
+    if need_bounds:
+        kbo = os.path.join(OUT, f"lk_kernel_bounds.{pid}.o")
+        cmds.append([_nvcc(), "-gencode", GENCODE, "-lineinfo", "-DLK_DEBUG_BOUNDS", *common, "-Xcompiler",
+                     "-fPIC", "-c", os.path.join(CSRC, "lk_kernel.cu"), "-o", kbo])
     if need_fake:
         tmpf = FAKE + f".{pid}.tmp"
         cmds.append(["g++", *common, "-fPIC", "-Wall", "-shared", "-pthread",
@@ -74,13 +84,18 @@ def build(force: bool = False, fake: bool = True, cuda: bool = True) -> None:
         moves.append((tmpf, FAKE))
     if cmds:
         _run_all(cmds)
+    links = []
     if need_cuda:
-        tmp = LIB + f".{pid}.tmp"
-        _run_all([[_nvcc(), "-gencode", GENCODE, "-shared", "-Xcompiler", "-fPIC", ko, ro,
-                   "-lpthread", "-o", tmp]])
-        moves.append((tmp, LIB))
-        for o in (ko, ro):
-            os.remove(o)
+        links.append((ko, LIB))
+    if need_bounds:
+        links.append((kbo, BOUNDS))
+    if links:
+        _run_all([[_nvcc(), "-gencode", GENCODE, "-shared", "-Xcompiler", "-fPIC", k, ro, "-lpthread", "-o",
+                   out + f".{pid}.tmp"] for k, out in links])
+        for k, out in links:
+            moves.append((out + f".{pid}.tmp", out))
+            os.remove(k)
+        os.remove(ro)
     for a, b in moves:
         os.replace(a, b)
 

@@ -299,6 +299,7 @@ extern "C" int lk_baseline_run_trace(int, const lk_trace_item*, size_t, int, con
   return LK_EDEVICE;
 }
 extern "C" int lk_pingpong(int, int, uint64_t*) { return LK_EDEVICE; }
+extern "C" int lk_bounds_violations(int, uint64_t*, uint32_t*) { return LK_EINVAL; }
 extern "C" int lk_baseline_phase_run(int, int, int, uint64_t, int, void*, lk_phase_times*) { return LK_EDEVICE; }
 extern "C" int lk_baseline_graph(int, const lk_batch_item*, uint32_t, int, int, int, float*) { return LK_EDEVICE; }
 extern "C" int lk_launch_noalloc(int, const lk_desc*, const void* const*, int, void*, int, int, void*) {

@@ -64,7 +64,7 @@ __device__ __forceinline__ int4 add4(int4 x, int4 y) {
 #define LK_STAGES 4u
 #define LK_GEMM_STAGE_FLOATS 8192u     /* one GEMM stage: A rows 16 KB + B tile 16 KB */
 #define LK_HIST_COPIES 2u              /* lane-private counter copies (32 KB each), P = 1 */
-#define LK_NUM_BARS 8u                 /* mbarriers: one per stage; two for MMA completion */
+#define LK_NUM_BARS 8u                 /* mbarriers: one per stage; the tensor-core GEMM's MMA completion in 4-7 */
 #define LK_WARP_BARS (32u * LK_STAGES)  /* then one per stage of each warp's own ring (histogram) */
 #define LK_ALL_BARS (LK_NUM_BARS + LK_WARP_BARS)
 
@@ -123,6 +123,12 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
     const uint32_t st = (uint32_t)(ch % LK_STAGES);
     const uint64_t v0 = beg + ch * stage_vec;
     const uint32_t nv = (uint32_t)((end - v0) < stage_vec ? (end - v0) : stage_vec);
+    if (!LK_INB(v0 >= beg && v0 + nv <= end && ((uintptr_t)(in0 + v0) & 15u) == 0 &&
+                    (NIN == 1 || ((uintptr_t)(in1 + v0) & 15u) == 0), LK_OOB_STREAM_LOAD) ||
+        !LK_INB(((size_t)st * NIN + NIN) * stage_vec * 16u <= SmemCfg<P>::stream_bytes, LK_OOB_STREAM_SMEM)) {
+      mbar_expect_tx(&bars[st], 0u);   /* skipped: the phase completes with no bytes */
+      return;
+    }
     mbar_expect_tx(&bars[st], nv * 16u * NIN);
     bulk_g2s(sbuf(st, 0), in0 + v0, nv * 16u, &bars[st]);
     if (NIN > 1) bulk_g2s(sbuf(st, 1), in1 + v0, nv * 16u, &bars[st]);
@@ -198,6 +204,7 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
+  if (!LK_INB(beg <= end && end <= nv, LK_OOB_SHARE)) end = beg;
   int4* o = reinterpret_cast<int4*>(d.out);
   const uint32_t T = blockDim.x;
   bool ok = true;
@@ -224,7 +231,8 @@ __device__ __forceinline__ bool body_add(const lk_slot& d, int r, int S, unsigne
                              [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4* s1) {
                                const int4* a = reinterpret_cast<const int4*>(s0);
                                const int4* b = reinterpret_cast<const int4*>(s1);
-                               for (uint32_t v = threadIdx.x; v < cnt; v += T) st_stream(o + v0 + v, add4(a[v], b[v]));
+                               for (uint32_t v = threadIdx.x; v < cnt; v += T)
+                                 if (LK_INB(v0 + v < end, LK_OOB_STORE)) st_stream(o + v0 + v, add4(a[v], b[v]));
                              });
   }
   if (r == S - 1) {
@@ -242,10 +250,11 @@ __device__ __forceinline__ bool body_copy(const lk_slot& d, int r, int S, unsign
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
+  if (!LK_INB(beg <= end && end <= nv, LK_OOB_SHARE)) end = beg;
   uint4* o = reinterpret_cast<uint4*>(d.out);
   const bool ok = stream<1, true, P>(reinterpret_cast<const uint4*>(d.in0), nullptr, beg, end, dsm + SmemCfg<P>::work_bytes, bars,
                                   phase, pace, [&](uint64_t v0, uint32_t cnt, const uint4* s0, const uint4*) {
-                                    if (threadIdx.x == 0) {
+                                    if (threadIdx.x == 0 && LK_INB(v0 + cnt <= end, LK_OOB_STORE)) {
                                       bulk_s2g(o + v0, s0, cnt * 16u);
                                       bulk_commit();
                                     }
@@ -265,6 +274,7 @@ __device__ __forceinline__ bool body_sum(const lk_slot& d, int r, int S, unsigne
   const uint64_t n = d.n, nv = n >> 2;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
+  if (!LK_INB(beg <= end && end <= nv, LK_OOB_SHARE)) end = beg;
   const uint32_t T = blockDim.x;
   float acc0 = 0.f, acc1 = 0.f;
   bool ok = true;
@@ -377,17 +387,8 @@ __device__ __forceinline__ void hist_zero(uint32_t* sh, uint32_t words) {
  * (two copies, 64 KB).  A bin's row is 256 bytes, so the byte offset of
  * bin v is v << 8: one byte permute moves byte b of a loaded word into
  * bits 8..15, and an add of the lane's base makes the address.  Lane l
- * still touches only bank l. */
-__device__ __forceinline__ void count4_row(uint32_t lane_addr, uint32_t w) {
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const uint32_t off = __byte_perm(w, 0u, 0x4404u | ((uint32_t)b << 4));
-    asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + off) : "memory");
-  }
-}
-
-/* The 16 bytes of one vector: every address is formed before the first
- * reduction, so the reductions issue back to back. */
+ * still touches only bank l.  The 16 bytes of one vector: every address is
+ * formed before the first reduction, so the reductions issue back to back. */
 __device__ __forceinline__ void count16_row(uint32_t lane_addr, uint4 q) {
   const uint32_t w[4] = {q.x, q.y, q.z, q.w};
   uint32_t a[16];
@@ -434,6 +435,13 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
   share(end - beg, (int)warp, (int)W, wbeg, wend);
   wbeg += beg;
   wend += beg;
+  /* the warp's part, its ring slice and barriers, and the farthest counter
+   * address any byte can form (row 255 of this lane and copy) */
+  if (!LK_INB(wbeg <= wend && wend <= end, LK_OOB_SHARE) ||
+      !LK_INB((size_t)(warp + 1) * LK_STAGES * stage_vec * 16u <= SmemCfg<P>::stream_bytes &&
+                  LK_NUM_BARS + (warp + 1) * LK_STAGES <= LK_ALL_BARS, LK_OOB_STREAM_SMEM) ||
+      !LK_INB(lane_addr - smem_addr(dsm) + 0xff00u + 4u <= SmemCfg<P>::work_bytes, LK_OOB_HIST_COUNTER))
+    wend = wbeg;
   const uint64_t total = wend - wbeg;
   const uint64_t nch = (total + stage_vec - 1) / stage_vec;
   /* the warp's rate: the CTA's, split evenly over its warps */
@@ -447,6 +455,10 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
     const uint32_t st = (uint32_t)(ch % LK_STAGES);
     const uint64_t v0 = wbeg + ch * stage_vec;
     const uint32_t nv = (uint32_t)((wend - v0) < stage_vec ? (wend - v0) : stage_vec);
+    if (!LK_INB(v0 + nv <= wend && ((uintptr_t)(in + v0) & 15u) == 0, LK_OOB_STREAM_LOAD)) {
+      mbar_expect_tx(&wb[st], 0u);   /* skipped: the phase completes with no bytes */
+      return;
+    }
     mbar_expect_tx(&wb[st], nv * 16u);
     bulk_g2s(ring + (size_t)st * stage_vec, in + v0, nv * 16u, &wb[st]);
   };
@@ -506,6 +518,7 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   const uint64_t nv = d.n >> 4;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
+  if (!LK_INB(beg <= end && end <= nv, LK_OOB_SHARE)) end = beg;
   const bool tail = (r == S - 1) && (d.n & 15);
   const uint32_t T = blockDim.x, W = T / 32, lane = threadIdx.x & 31;
   uint32_t* sh = reinterpret_cast<uint32_t*>(dsm);
@@ -799,6 +812,7 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
                                              uint32_t& phase, Pace pace) {
   uint64_t beg, end;
   share(d.n, r, S, beg, end);
+  if (!LK_INB(end <= d.n, LK_OOB_SHARE)) end = beg;
   if (beg >= end) return true;
   const float* A = reinterpret_cast<const float*>(d.in0);
   const float* B = reinterpret_cast<const float*>(d.in1);
@@ -814,6 +828,10 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
     const uint32_t st = (uint32_t)((u - beg) % LK_TC_STAGES);
     unsigned char* sa = dsm + st * 32768u;
     fence_proxy_async_smem();
+    if (!LK_INB(u >= beg && u < end, LK_OOB_GEMM_LOAD) || !LK_INB((st + 1) * 32768u <= LK_TC_OPS, LK_OOB_GEMM_SMEM)) {
+      mbar_expect_tx(&bars[st], 0u);   /* skipped: the phase completes with no bytes */
+      return;
+    }
     mbar_expect_tx(&bars[st], 32768u);
     bulk_g2s(sa, A + u * 4096, 16384u, &bars[st]);
     bulk_g2s(sa + 16384u, B + u * 4096, 16384u, &bars[st]);
@@ -843,6 +861,8 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
    * ops0 + 32 KB b (operands, then the epilogue's row exchange) */
   const uint32_t dt0 = s_tmem + 256u * h;
   unsigned char* ops0 = dsm + LK_TC_OPS + h * 65536u;
+  /* both halves' two buffers inside the shared memory and the 512 TMEM columns */
+  const bool bufs_ok = LK_INB(LK_TC_OPS + (h + 1) * 65536u <= LK_TC_SMEM && 256u * (h + 1) <= 512u, LK_OOB_GEMM_SMEM);
   /* epilogue: warp quarter q holds D rows 32q..32q+31 (rows 64-127 are the
    * A_lo products of output rows 0-63) */
   const uint32_t quarter = warp & 3u;
@@ -881,7 +901,8 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
         const uint32_t f = lt + 128u * q, i = f >> 4, c4 = f & 15u, pos = (c4 ^ (i & 7u)) << 2;
         const float4 x = *reinterpret_cast<const float4*>(part + i * 64u + pos);
         const float4 y = *reinterpret_cast<const float4*>(part + (i + 64u) * 64u + pos);
-        st_stream(reinterpret_cast<float4*>(ct + i * 64u + c4 * 4u), make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w));
+        if (LK_INB(u < end && i * 64u + c4 * 4u + 4u <= 4096u, LK_OOB_GEMM_STORE))
+          st_stream(reinterpret_cast<float4*>(ct + i * 64u + c4 * 4u), make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w));
       }
     } else {
       done = false;
@@ -928,10 +949,12 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
       }
       tc_fence_after_sync();
       const uint32_t ah = smem_addr(ops), bh = ah + 16384u;
+      if (bufs_ok) {
 #pragma unroll
-      for (uint32_t j = 0; j < 4; ++j)
-        umma_f16(dt0 + 128u * b, umma_desc(ah + 256u * j, 128u, 1024u), umma_desc(bh + 256u * j, 128u, 1024u),
-                 LK_TC_IDESC, j > 0);
+        for (uint32_t j = 0; j < 4; ++j)
+          umma_f16(dt0 + 128u * b, umma_desc(ah + 256u * j, 128u, 1024u), umma_desc(bh + 256u * j, 128u, 1024u),
+                   LK_TC_IDESC, j > 0);
+      }
       umma_commit(&bars[LK_TC_MMA_BAR + 2u * h + b]);
     }
     /* while the tensor core works on tile u, finish the previous tile */
@@ -986,6 +1009,7 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   const uint32_t rows = 64 / U;
   uint64_t beg, end;
   share(tiles * U, r, S, beg, end);
+  if (!LK_INB(end <= tiles * U, LK_OOB_SHARE)) end = beg;
   if (beg >= end) return true;
   const float* A = reinterpret_cast<const float*>(d.in0);
   const float* B = reinterpret_cast<const float*>(d.in1);
@@ -1001,6 +1025,11 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
     const uint32_t rb = (uint32_t)(u % U);
     float* sA = sm + st * LK_GEMM_STAGE_FLOATS;
     fence_proxy_async_smem();
+    if (!LK_INB(tile < tiles && rb < U && (uint64_t)(rb + 1) * rows <= 64u, LK_OOB_GEMM_LOAD) ||
+        !LK_INB((st + 1) * LK_GEMM_STAGE_FLOATS * 4u <= SmemCfg<P>::dyn_bytes, LK_OOB_GEMM_SMEM)) {
+      mbar_expect_tx(&bars[st], 0u);   /* skipped: the phase completes with no bytes */
+      return;
+    }
     mbar_expect_tx(&bars[st], rows * 256u + 16384u);
     bulk_g2s(sA, A + tile * 4096 + (uint64_t)rb * rows * 64, rows * 256u, &bars[st]);
     bulk_g2s(sA + 4096, B + tile * 4096, 16384u, &bars[st]);
@@ -1072,9 +1101,11 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
             for (int j = 0; j < 4; ++j) c[i][j] = fmaf(av[i][q], bv[q][j], c[i][j]);
       }
       float* crow = C + tile * 4096 + (uint64_t)(rb * rows + r0) * 64 + c0;
+      if (LK_INB(tile < tiles && rb * rows + r0 + 4u <= 64u && c0 + 4u <= 64u, LK_OOB_GEMM_STORE)) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(crow + i * 64) = make_float4(c[i][0], c[i][1], c[i][2], c[i][3]);
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<float4*>(crow + i * 64) = make_float4(c[i][0], c[i][1], c[i][2], c[i][3]);
+      }
     }
   }
   __syncthreads();          /* every stage is free for the next body */

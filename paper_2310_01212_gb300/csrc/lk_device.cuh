@@ -9,6 +9,34 @@
 
 namespace lk {
 
+/* ---- bounds checks of the checking build (-DLK_DEBUG_BOUNDS) ------------
+ * LK_INB(cond, site) guards one access: in the checking build a false
+ * `cond` counts a violation, records the first site and returns false, so
+ * the caller skips the access instead of faulting; in the product build it
+ * is `true` and `cond` is not evaluated.  Sites name the access path. */
+enum : uint32_t {
+  LK_OOB_SHARE = 1,        /* a CTA's or warp's share outside the operand       */
+  LK_OOB_STREAM_LOAD = 2,  /* a staged chunk outside the share, or misaligned   */
+  LK_OOB_STREAM_SMEM = 3,  /* a stage outside the streaming region              */
+  LK_OOB_STORE = 4,        /* an element store outside the share                */
+  LK_OOB_HIST_COUNTER = 5, /* a histogram counter outside the work region      */
+  LK_OOB_GEMM_LOAD = 6,    /* a GEMM tile or row block outside the operands     */
+  LK_OOB_GEMM_STORE = 7,   /* a GEMM store outside the output tile              */
+  LK_OOB_GEMM_SMEM = 8,    /* a GEMM stage, operand buffer or TMEM column out   */
+};
+#ifdef LK_DEBUG_BOUNDS
+__device__ unsigned long long g_lk_oob_count;
+__device__ unsigned int g_lk_oob_site;
+__device__ __forceinline__ bool lk_inb(bool ok, uint32_t site) {
+  if (!ok && atomicAdd(&g_lk_oob_count, 1ull) == 0ull) atomicExch(&g_lk_oob_site, site);
+  return ok;
+}
+__device__ __forceinline__ bool lk_oob_seen() { return *(volatile unsigned long long*)&g_lk_oob_count != 0ull; }
+#define LK_INB(cond, site) ::lk::lk_inb((cond), (site))
+#else
+#define LK_INB(cond, site) true
+#endif
+
 __device__ __forceinline__ uint64_t gtime() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

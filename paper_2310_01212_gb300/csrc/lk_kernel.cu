@@ -352,6 +352,9 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
     case LK_OP_NOP: break;
     default: return LK_DERR_BADDESC;
   }
+#ifdef LK_DEBUG_BOUNDS
+  if (lk_oob_seen()) return LK_DERR_BOUNDS;
+#endif
   return ok ? 0 : LK_DERR_STAGING;
 }
 
@@ -1294,6 +1297,26 @@ extern "C" int lk_launch_noalloc(int device, const lk_desc* d, const void* const
   return launch_ordinary(sl, ctas, threads, (lk_scratch*)scratch, (cudaStream_t)stream) == cudaSuccess
              ? LK_OK
              : LK_EDEVICE;
+}
+
+extern "C" int lk_bounds_violations(int device, uint64_t* count, uint32_t* first_site) {
+#ifdef LK_DEBUG_BOUNDS
+  if (!count || !first_site) return LK_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
+  unsigned long long c = 0;
+  unsigned int s = 0;
+  if (cudaMemcpyFromSymbol(&c, lk::g_lk_oob_count, sizeof c) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&s, lk::g_lk_oob_site, sizeof s) != cudaSuccess)
+    return LK_EDEVICE;
+  *count = c;
+  *first_site = s;
+  return LK_OK;
+#else
+  (void)device;
+  (void)count;
+  (void)first_site;
+  return LK_EINVAL;   /* the product build checks no bounds */
+#endif
 }
 
 extern "C" int lk_pingpong(int device, int iters, uint64_t* rtt_ns) {

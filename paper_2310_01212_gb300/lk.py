@@ -35,7 +35,8 @@ LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_
 LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7
 LK_OP_SPIN = 8
 LK_OP_BATCH = 9
-LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING = range(7)
+(LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING,
+ LK_DERR_BOUNDS) = range(8)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
              LK_OP_COPY_I32: 1, 6: 1, 7: 1, 8: 0}
 OP_NAMES = {LK_OP_NOP: "nop", LK_OP_ADD_I32: "add_i32", LK_OP_HIST_U8: "hist_u8", LK_OP_SUM_F32: "sum_f32",
@@ -105,16 +106,18 @@ _libs: dict = {}
 _lock = threading.Lock()
 
 
-def library_path(fake: bool = False) -> str:
-    return _build.FAKE if fake else _build.LIB
+def library_path(fake: bool = False, bounds: bool = False) -> str:
+    return _build.FAKE if fake else (_build.BOUNDS if bounds else _build.LIB)
 
 
-def load(fake: bool = False) -> ctypes.CDLL:
-    """Load liblk.so (or the fake-device test build).  Raises if it is missing."""
+def load(fake: bool = False, bounds: bool = False) -> ctypes.CDLL:
+    """Load liblk.so (or the fake-device test build, or the bounds-checking
+    build liblk_bounds.so).  Raises if it is missing."""
+    key = (bool(fake), bool(bounds) and not fake)
     with _lock:
-        if fake in _libs:
-            return _libs[fake]
-        path = library_path(fake)
+        if key in _libs:
+            return _libs[key]
+        path = library_path(*key)
         if not os.path.exists(path):
             raise OSError(f"{path} is missing: run paper_2310_01212_gb300.build.build() "
                           "(no CPU fallback exists)")
@@ -144,6 +147,7 @@ def load(fake: bool = False) -> ctypes.CDLL:
             "lk_baseline_run_trace": (I, [I, P, SZ, I, ctypes.POINTER(I), I, I, I, I, P]),
             "lk_pingpong": (I, [I, I, ctypes.POINTER(U64)]),
             "lk_launch_noalloc": (I, [I, ctypes.POINTER(lk_desc), ctypes.POINTER(P), I, P, I, I, P]),
+            "lk_bounds_violations": (I, [I, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint32)]),
             "lk_submit_batch": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(lk_batch_tune), ctypes.POINTER(U64)]),
             "lk_serve": (I, [P, P, SZ, ctypes.POINTER(lk_serve_params), P]),
             "lk_phase_run": (I, [I, I, I, U64, I, P, P]),
@@ -154,7 +158,7 @@ def load(fake: bool = False) -> ctypes.CDLL:
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        _libs[fake] = lib
+        _libs[key] = lib
         return lib
 
 
@@ -239,9 +243,9 @@ def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, 
 class Context:
     """A running LightKernel context (owns an lk_ctx*)."""
 
-    def __init__(self, sizes, fake: bool = False, **kw):
+    def __init__(self, sizes, fake: bool = False, bounds: bool = False, **kw):
         self.kernel_ms = -1.0
-        self.lib = load(fake)
+        self.lib = load(fake, bounds)
         self.sizes = list(sizes)
         self._params, self._keep = make_params(self.sizes, **kw)
         self.ptr = ctypes.c_void_p()
@@ -424,6 +428,17 @@ def lk_baseline_run_trace(items: np.ndarray, ctas_of_slot, threads: int, n_threa
     rc = lib.lk_baseline_run_trace(device, items.ctypes.data, items.size, len(ctas_of_slot), cs, threads,
                                    n_threads, mode, pin_cpu_base, res.ctypes.data)
     return rc, res
+
+
+def lk_bounds_violations(device: int = 0) -> tuple[int, int]:
+    """(violations, first site) counted by the bounds-checking build since
+    it was loaded.  Call it with no context running on the device."""
+    lib = load(bounds=True)
+    cnt, site = ctypes.c_uint64(), ctypes.c_uint32()
+    rc = lib.lk_bounds_violations(device, ctypes.byref(cnt), ctypes.byref(site))
+    if rc != LK_OK:
+        raise LkError(rc, "lk_bounds_violations")
+    return int(cnt.value), int(site.value)
 
 
 def lk_pingpong(iters: int, device: int = 0) -> np.ndarray:

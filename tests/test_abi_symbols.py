@@ -26,13 +26,23 @@ def test_header_declares_the_boundary():
         assert must in names
 
 
-@pytest.mark.parametrize("fake", [False, True])
-def test_library_exports_every_declared_symbol(native_built, fake):
+@pytest.mark.parametrize("fake,bounds", [(False, False), (True, False), (False, True)])
+def test_library_exports_every_declared_symbol(native_built, fake, bounds):
     from paper_2310_01212_gb300 import lk
 
-    lib = ctypes.CDLL(lk.library_path(fake))
+    lib = ctypes.CDLL(lk.library_path(fake, bounds))
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_product_build_checks_no_bounds(native_built):
+    # lk_bounds_violations answers only in liblk_bounds.so; the product
+    # library refuses it without touching the device
+    from paper_2310_01212_gb300 import lk
+
+    lib = lk.load()
+    cnt, site = ctypes.c_uint64(), ctypes.c_uint32()
+    assert lib.lk_bounds_violations(0, ctypes.byref(cnt), ctypes.byref(site)) == lk.LK_EINVAL
 
 
 def test_strerror_without_gpu(native_built):
