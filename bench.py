@@ -417,7 +417,6 @@ def main():
     torch.cuda.synchronize()
     dist.barrier()
     wall = time.perf_counter() - t_timed
-    clk = clocks.stop()
     lat = np.concatenate(lat)
     lat_arr = np.concatenate(lat_arr)
 
@@ -458,6 +457,9 @@ def main():
     if rc != lk.LK_OK:
         raise RuntimeError(f"occupancy-grid baseline failed: {lk.lk_strerror(rc)}")
     base_occ = (res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0
+    # the clock sampler (nvidia-smi, every 200 ms) ran through both arms, so
+    # that any disturbance it causes falls on both alike
+    clk = clocks.stop()
 
     # ---- dispatch alone: closed-loop NOPs, persistent kernel vs launch+sync ---------
     nop = np.zeros(2 * items_per_step, dtype=lk.TRACE_ITEM_DTYPE)
