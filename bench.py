@@ -630,7 +630,8 @@ def main():
             with lk.lk_init(init_kw["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000,
                             **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
                 lk.lk_set_rate(ctx, 1, be_rate)
-                rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000)
+                rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000,
+                                         pin_cpu_base=pin)
             if rc != lk.LK_OK:
                 raise RuntimeError(f"isolation trace failed: {lk.lk_strerror(rc)}")
             crit = rr[:periods]
