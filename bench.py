@@ -478,6 +478,37 @@ def main():
     nop_mbox = (r4["t_complete_ns"] - r4["t_submit_ns"])[skip:] / 1000.0
     nop_base = (r2["t_complete_ns"] - r2["t_submit_ns"])[skip:] / 1000.0
 
+    # ---- the small configuration: 4 SMs as 2 clusters of 2, closed loop -----------
+    # 10,000 int32 adds of 4,096 elements, round-robin, one outstanding at a
+    # time; the same items as launch+sync of 2 CTAs each; outputs checked
+    scfg = wl.SMALL
+    sa, sb = wl.small_inputs(scfg)
+    n_small, n_el = sa.shape
+    dsa, dsb = torch.from_numpy(sa).to(dev), torch.from_numpy(sb).to(dev)
+    sout = torch.zeros((n_small, n_el), dtype=torch.int32, device=dev)
+    sit = np.zeros(n_small, dtype=lk.TRACE_ITEM_DTYPE)
+    sit["cluster"] = np.arange(n_small) % len(scfg["sizes"])
+    sit["op"] = lk.LK_OP_ADD_I32
+    sit["n"] = n_el
+    row = np.arange(n_small, dtype=np.uint64) * np.uint64(4 * n_el)
+    sit["in0"], sit["in1"], sit["out"] = dsa.data_ptr() + row, dsb.data_ptr() + row, sout.data_ptr() + row
+    torch.cuda.synchronize()
+    with lk.lk_init(scfg["sizes"], device=dev, threads_per_cta=scfg["threads"], idle_lease_ns=5_000_000_000) as ctx:
+        rc, rs = lk.lk_run_trace(ctx, sit, n_threads=1, closed_loop=True, pin_cpu_base=pin)
+    if rc != lk.LK_OK:
+        raise RuntimeError(f"small-config trace failed: {lk.lk_strerror(rc)}")
+    small_exact = bool(np.array_equal(sout.cpu().numpy(), oracle.add_i32(sa, sb)))
+    rc, rsb = lk.lk_baseline_run_trace(sit, scfg["sizes"], threads=scfg["threads"], n_threads=1, device=dev,
+                                       pin_cpu_base=pin)
+    if rc != lk.LK_OK:
+        raise RuntimeError(f"small-config baseline failed: {lk.lk_strerror(rc)}")
+    small = {"workload": "4 SMs as 2 LK clusters of 2 (256 threads/CTA); 10,000 closed-loop int32 adds of 4,096 "
+                         "elements uniform in [-2^20, 2^20], seed 0, round-robin",
+             "lk_us": lat_summary((rs["t_complete_ns"] - rs["t_submit_ns"]) / 1000.0),
+             "launch_sync_us": lat_summary((rsb["t_complete_ns"] - rsb["t_submit_ns"]) / 1000.0),
+             "bit_exact": small_exact}
+    del dsa, dsb, sout
+
     # ---- the paper's one-deep mailbox against the ring (Sec. II.D, Table 1) ---------
     # one SM (the paper's cluster), closed-loop NOPs; then the last timed step's
     # mixed trace (open loop, Poisson arrivals) through one-deep mailboxes
@@ -755,6 +786,7 @@ def main():
         "baseline_launch_sync_us": lat_summary(base),
         "baseline_occupancy_grid_us": dict(lat_summary(base_occ), grid=occ_grid,
                                            note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),
+        "config_small": small,
         "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
                             "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base)},
         "paper_mailbox_vs_ring": mbox,
