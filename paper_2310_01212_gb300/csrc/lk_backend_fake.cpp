@@ -16,6 +16,7 @@
  *   LK_FAKE_STALL_US=t     each descriptor takes t microseconds
  *   LK_FAKE_DROP_AFTER=m   completions after the m-th are never published
  *   LK_FAKE_FAIL_AFTER=m   after m descriptors the cluster stops with LK_DERR_BADDESC
+ *   LK_FAKE_FAIL_CODE=e    ... or with device error e instead (e.g. 7, LK_DERR_BOUNDS)
  *   LK_FAKE_NO_BOOT=1      the CTAs never report boot
  */
 #include <stdlib.h>
@@ -115,6 +116,7 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
   const uint64_t stall = env_u64("LK_FAKE_STALL_US", 0) * 1000ull;
   const uint64_t drop_after = env_u64("LK_FAKE_DROP_AFTER", ~0ull);
   const uint64_t fail_after = env_u64("LK_FAKE_FAIL_AFTER", ~0ull);
+  const int fail_code = (int)env_u64("LK_FAKE_FAIL_CODE", LK_DERR_BADDESC);
   const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
   const bool mailbox = (a.flags & LK_KFLAG_MAILBOX) != 0;
   uint64_t finished = 0;
@@ -170,7 +172,7 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       cmd = dsc.cmd;
     }
     if (cmd == LK_CMD_EXIT) break;
-    if (k >= fail_after) { err = LK_DERR_BADDESC; break; }
+    if (k >= fail_after) { err = fail_code; break; }
     const uint64_t t_pick = now_ns();
     st_rel(&a.cword[c].status, (uint64_t)LK_ST_WORKING);
     if (stall) std::this_thread::sleep_for(std::chrono::nanoseconds(stall));

@@ -138,6 +138,20 @@ def test_device_error_surfaces(fake_env):
     assert c.dispose() == lk.LK_EDEVICE
 
 
+def test_bounds_violation_surfaces_as_a_device_error(fake_env):
+    """A descriptor that the bounds-checking build stops (LK_DERR_BOUNDS)
+    fails its wait with LK_EDEVICE and names the reason, like any device error."""
+    fake_env["LK_FAKE_FAIL_AFTER"] = "0"
+    fake_env["LK_FAKE_FAIL_CODE"] = str(lk.LK_DERR_BOUNDS)
+    c = ctx_([4])
+    h = lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)
+    with pytest.raises(lk.LkError) as e:
+        lk.lk_wait(c, h)
+    assert e.value.code == lk.LK_EDEVICE
+    assert lk.lk_device_error(c) == lk.LK_DERR_BOUNDS
+    assert c.dispose() == lk.LK_EDEVICE
+
+
 def test_idle_lease_expires_and_heartbeat_extends(fake_env):
     c = ctx_(idle_lease_ns=300_000_000)
     for _ in range(6):              # 0.6 s of beats: stays up
