@@ -505,7 +505,8 @@ int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n
                       int ctas, int threads, void* stream);
 
 /* ---- the bounds-checking build ---------------------------------------- */
-/* liblk_bounds.so is this library compiled with -DLK_DEBUG_BOUNDS: every
+/* The paper has no counterpart: this is a test aid of this library.
+ * liblk_bounds.so is this library compiled with -DLK_DEBUG_BOUNDS: every
  * body checks, before each global-memory access path and shared-memory or
  * TMEM region it uses, that the index or address lies inside the operand
  * (as the descriptor's n sizes it), the CTA's or warp's share, and the
