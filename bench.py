@@ -11,9 +11,12 @@ slices of 4 GiB of device pools at random offsets (larger than L2).
 Each step boots a context (one persistent-kernel launch), runs the step's
 trace through it and disposes it.  The line reports the p99 latency over all
 timed items, the same trace as ordinary cudaLaunchKernel+cudaStreamSynchronize
-launches, the host-mapped round-trip floor, the work bodies' HBM bandwidth in
-finite mode (roofline), an end-to-end run with host buffers, and the oracle
-timed on the host cores.
+launches (the submitting threads of both arms pinned to the same host cores),
+the host-mapped round-trip floor, the small configuration (4 SMs as 2 x 2,
+closed loop), the one-deep mailbox, batching, serving, isolation and the
+paper's life cycle, the work bodies' HBM bandwidth in finite mode
+(roofline), an end-to-end run with host buffers, and the oracle timed on the
+host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lk|reference]
 """
