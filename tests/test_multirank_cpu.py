@@ -73,3 +73,17 @@ def test_submitter_cores_are_disjoint_per_rank(monkeypatch):
     assert [bench.submitter_cpus(r) for r in range(4)] == [2, 6, 10, -1]
     monkeypatch.setattr(os, "sched_getaffinity", lambda pid: {0, 1, 2, 3})
     assert bench.submitter_cpus(0) == -1
+
+
+def test_percentiles_are_nearest_rank():
+    """The bench's percentiles take the nearest rank over all samples: the
+    ceil(q n)-th smallest value, never an interpolation."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    v = list(range(100, 0, -1))                 # 1..100, unsorted
+    assert bench.pct(v, 0.50) == 50 and bench.pct(v, 0.99) == 99 and bench.pct(v, 1.0) == 100
+    assert bench.pct([3.0], 0.999) == 3.0 and bench.pct([], 0.5) is None
+    assert bench.pct([1, 2, 3, 4, 5, 6, 7, 8, 9, 1000], 0.99) == 1000   # ceil(9.9) = 10th
+    s = bench.lat_summary([5.0, 1.0, 3.0])
+    assert (s["p50"], s["max"], s["count"]) == (3.0, 5.0, 3)
