@@ -257,13 +257,48 @@ def run_reference(args, dist: Dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / (args.warmup + args.steps),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "binary64 accumulation (oracle)", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "sample": f"{per_step} items per step, bodies in equal shares",
-                       "host": hi},
+            "config": bench_config(args), "host": hi,
             "latency_us": lat_summary(lat),
             "cpu_baseline": {"value": v, "unit": "us", "cores": 1, "kind": "oracle",
-                             "sample": f"{lat.size} items of the workload's body mix, one host thread"},
+                             "sample": f"{lat.size} items of the workload's body mix ({per_step} per step, "
+                                       f"bodies in equal shares), per-item time, one host thread"},
             "e2e": {"value": v, "unit": "us", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def r1(x):
+    return None if x is None else round(float(x), 1)
+
+
+def bench_config(args, cfg=None) -> dict:
+    """The workload as both arms report it (identical dicts)."""
+    return {"workload": WORKLOAD, "partition": "4 clusters x 37 SMs", "threads_per_cta": 256,
+            "items_per_step": args.items, "rate_per_s": 20000.0,
+            "parallelism": f"replicas x{args.gpus} (no collective)",
+            "l2": "inputs larger than L2: 4 GiB of device pools, random 16-B-aligned offsets"}
+
+
+# ---- oracle checks of the bench's outputs (checking code stays out of the package) ----
+def check_batching_parity(pools, meta: dict) -> int:
+    """Number of items of a batching parity batch whose output differs from
+    the oracle (int32 adds bit-exact, sums within 1e-4 sum|x|)."""
+    import oracle
+    from paper_2310_01212_gb300 import lk
+
+    bad = 0
+    add_out = pools.out_add.view(-1)
+    for i in range(meta["op"].size):
+        k = int(meta["n"][i])
+        if meta["op"][i] == lk.LK_OP_ADD_I32:
+            a = pools.i32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
+            b = pools.i32[int(meta["off1"][i]):int(meta["off1"][i]) + k].cpu().numpy()
+            o = add_out[int(meta["offo"][i]):int(meta["offo"][i]) + k].cpu().numpy()
+            bad += 0 if np.array_equal(o, oracle.add_i32(a, b)) else 1
+        else:
+            x = pools.f32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
+            o = float(pools.out_sum[int(meta["offo"][i]), 0].cpu())
+            bad += 0 if abs(o - oracle.sum_f32(x)) <= 1e-4 * oracle.abs_sum_f32(x) else 1
+    return bad
 
 
 # ---- the LightKernel arm ------------------------------------------------------------
@@ -305,9 +340,52 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM}, "fallback"
 
 
-def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, threads: int = 256):
+def check_body_output(name: str, op: int, cnt: int, a, b, o, seed: int) -> dict:
+    """Compare the output of a finite-mode bandwidth launch with the oracle at
+    the size it was timed: add / copy on seeded 1M-element windows at random
+    offsets, the sum and the histogram whole, a seeded 1 % of the GEMM tiles.
+    Returns {"checked": what, "mismatches": k}."""
+    import oracle
+    from paper_2310_01212_gb300 import lk, synth
+
+    win = 1 << 20
+    if op in (lk.LK_OP_ADD_I32, lk.LK_OP_COPY_I32):
+        starts = synth.choice(seed, 31, 4, (cnt - win) // 4 + 1) * 4
+        bad = 0
+        for st in starts:
+            st = int(st)
+            x = a[st:st + win].cpu().numpy()
+            want = oracle.add_i32(x, b[st:st + win].cpu().numpy()) if op == lk.LK_OP_ADD_I32 else oracle.copy_i32(x)
+            bad += int(np.count_nonzero(o[st:st + win].cpu().numpy() != want))
+        return {"checked": f"{len(starts)} windows of {win} elements at seeded offsets", "mismatches": bad}
+    if op == lk.LK_OP_SUM_F32:
+        x = a.cpu().numpy()
+        ok = abs(float(o[0].cpu()) - oracle.sum_f32(x)) <= 1e-4 * oracle.abs_sum_f32(x)
+        return {"checked": f"the whole sum of {cnt} values", "mismatches": 0 if ok else 1}
+    if op == lk.LK_OP_HIST_U8:
+        ok = np.array_equal(o.cpu().numpy().astype(np.int64), oracle.hist_u8(a.cpu().numpy()))
+        return {"checked": f"the whole histogram of {cnt} bytes", "mismatches": 0 if ok else 1}
+    pick = np.sort(synth.choice(seed, 32, max(1, cnt // 100), cnt))
+    A = a.view(cnt, 64, 64)[torch_index(pick, a)].cpu().numpy()
+    B = b.view(cnt, 64, 64)[torch_index(pick, b)].cpu().numpy()
+    C = o.view(cnt, 64, 64)[torch_index(pick, o)].cpu().numpy()
+    err = np.abs(C.astype(np.float64) - oracle.gemm64_f32(A, B)) > 1e-4 * oracle.gemm64_abs_bound(A, B)
+    bad = int(np.count_nonzero(err.reshape(len(pick), -1).any(axis=1)))
+    return {"checked": f"{len(pick)} of {cnt} tiles (seeded 1 %), every element", "mismatches": bad}
+
+
+def torch_index(idx: np.ndarray, like):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int64)).to(like.device)
+
+
+def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, threads: int = 256,
+                   seed: int = 0):
     """Finite mode on every SM as one cluster: `per_launch` descriptors of one
-    body per launch; CUDA-event time of each launch (boot included)."""
+    body per launch; CUDA-event time of each launch (boot included).  After
+    each body's launches its output is checked against the oracle at the
+    timed size (check_body_output); a mismatch fails the leg."""
     import torch
 
     i32, u8, f32 = pools.i32, pools.u8, pools.f32
@@ -336,8 +414,13 @@ def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, th
                                        out=[o] * per_launch, threads_per_cta=t_cta, exec_log_cap=per_launch + 1)
             ms.append(t)
         avg = float(np.mean(ms))
+        torch.cuda.synchronize()
+        chk = check_body_output(name, op, cnt, a, b, o, seed)
+        if chk["mismatches"]:
+            raise RuntimeError(f"body bandwidth leg {name}: {chk['mismatches']} mismatches against the oracle")
         res[name] = {"gbs": nbytes * per_launch / (avg * 1e-3) / 1e9, "launch_ms": avg, "bytes_per_launch":
-                     nbytes * per_launch, "descriptors_per_launch": per_launch, "threads_per_cta": t_cta}
+                     nbytes * per_launch, "descriptors_per_launch": per_launch, "threads_per_cta": t_cta,
+                     "parity": chk}
         if op == lk.LK_OP_GEMM64_F32:
             res[name]["tflops"] = 524288.0 * cnt * per_launch / (avg * 1e-3) / 1e12
     return res
@@ -350,8 +433,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lk", choices=["lk", "reference"])
     ap.add_argument("--items", type=int, default=ITEMS_PER_STEP)
-    ap.add_argument("--iso-periods", type=int, default=2000, help="critical periods (1 ms each) per isolation run")
-    ap.add_argument("--batches", type=int, default=8, help="batches of the batching stream to time")
+    ap.add_argument("--iso-periods", type=int, default=60_000,
+                    help="critical periods (1 ms each) of the disjoint-layout isolation run, alone and loaded")
+    ap.add_argument("--iso-sweep-periods", type=int, default=2000,
+                    help="critical periods of each co-resident and rate-capped isolation run")
+    ap.add_argument("--batch-items", type=int, default=100_000,
+                    help="descriptors of the batching stream's seeded prefix (whole batches)")
+    ap.add_argument("--graph-batches", type=int, default=8,
+                    help="batches of that prefix also timed as CUDA graphs of ordinary launches")
+    ap.add_argument("--detail", default="bench_detail.json",
+                    help="file that receives every leg's full result (the printed line keeps the headline)")
     ap.add_argument("--serve-seconds", type=float, default=0.25, help="seconds of arrivals per serving rate")
     ap.add_argument("--phase-runs", type=int, default=100, help="runs of the paper's life-cycle measurement")
     args = ap.parse_args()
@@ -563,40 +654,70 @@ def main():
     from paper_2310_01212_gb300 import autotune
 
     tuned = autotune.load()
-    bbat = [wl.batching_batch(pools, seed, b) for b in range(args.batches)]
+    # a seeded prefix of the 1,000,000-descriptor stream: whole batches until
+    # at least --batch-items descriptors
+    bbat = []
+    while sum(len(it) for it, _ in bbat) < args.batch_items:
+        bbat.append(wl.batching_batch(pools, seed, len(bbat)))
+    gsub = bbat[: max(1, min(args.graph_batches, len(bbat)))]
     par_items, par_meta = wl.batching_parity_batch(pools, seed)
     torch.cuda.synchronize()
-    lk_s = []
+    lk_sub_s = []
+    tune_kw = dict(max_parts=tuned["max_parts"], part_bytes=tuned["part_bytes"])
     with lk.lk_init([n_sms], device=dev, threads_per_cta=tuned["threads"], max_batch_units=1 << 16,
                     idle_lease_ns=30_000_000_000) as ctx:
-        h = lk.lk_submit_batch(ctx, 0, par_items, max_parts=tuned["max_parts"], part_bytes=tuned["part_bytes"])
+        h = lk.lk_submit_batch(ctx, 0, par_items, **tune_kw)
         if lk.lk_wait(ctx, h, 60_000_000_000) != lk.LK_OK:
             raise RuntimeError("parity batch did not finish")
         # check now: the timed batches below write into the same output arenas
         torch.cuda.current_stream().synchronize()
-        batch_bad = wl.check_batching_parity(pools, par_meta, oracle)
-        for items, _ in bbat:
+        batch_bad = check_batching_parity(pools, par_meta)
+        # the graph-compared subset, one batch at a time (post, wait)
+        for items, _ in gsub:
             t0 = time.perf_counter_ns()
-            h = lk.lk_submit_batch(ctx, 0, items, max_parts=tuned["max_parts"], part_bytes=tuned["part_bytes"])
+            h = lk.lk_submit_batch(ctx, 0, items, **tune_kw)
             if h is None or lk.lk_wait(ctx, h, 120_000_000_000) != lk.LK_OK:
                 raise RuntimeError("batch did not finish")
-            lk_s.append((time.perf_counter_ns() - t0) / 1e9)
+            lk_sub_s.append((time.perf_counter_ns() - t0) / 1e9)
+        # the whole prefix: batch b+1 is posted while batch b runs (two unit
+        # tables per cluster), then b is waited for
+        t0 = time.perf_counter_ns()
+        prev = None
+        for items, _ in bbat:
+            h = lk.lk_submit_batch(ctx, 0, items, **tune_kw)
+            if h is None:
+                raise RuntimeError("batch tables busy")
+            if prev is not None and lk.lk_wait(ctx, prev, 120_000_000_000) != lk.LK_OK:
+                raise RuntimeError("batch did not finish")
+            prev = h
+        if lk.lk_wait(ctx, prev, 120_000_000_000) != lk.LK_OK:
+            raise RuntimeError("batch did not finish")
+        lk_all_s = (time.perf_counter_ns() - t0) / 1e9
     graph_s = []
-    for items, _ in bbat:
+    for items, _ in gsub:
         ms = lk.lk_baseline_graph(items, n_sms, threads=tuned["threads"], reps=2, device=dev)
         graph_s.append(float(ms[-1]) / 1e3)
-    bbytes = np.array([m["bytes"] for _, m in bbat])
-    bcount = np.array([len(it) for it, _ in bbat])
-    batching = {"batches": len(bbat), "items": int(bcount.sum()), "bytes": float(bbytes.sum()),
-                "items_per_batch": bcount.tolist(),
-                "lk_gbs": float(bbytes.sum() / np.sum(lk_s) / 1e9),
-                "graph_gbs": float(bbytes.sum() / np.sum(graph_s) / 1e9),
-                "lk_items_per_s": float(bcount.sum() / np.sum(lk_s)),
-                "graph_items_per_s": float(bcount.sum() / np.sum(graph_s)),
-                "lk_batch_ms": [round(1e3 * x, 3) for x in lk_s], "graph_batch_ms": [round(1e3 * x, 3) for x in graph_s],
+    sub_bytes = float(sum(m["bytes"] for _, m in gsub))
+    sub_count = int(sum(len(it) for it, _ in gsub))
+    all_bytes = float(sum(m["bytes"] for _, m in bbat))
+    all_count = int(sum(len(it) for it, _ in bbat))
+    batching = {"batches": len(bbat), "items": all_count, "bytes": all_bytes,
+                "lk_gbs": all_bytes / lk_all_s / 1e9, "lk_items_per_s": all_count / lk_all_s,
+                "lk_seconds": lk_all_s,
+                "graph_compared": {"batches": len(gsub), "items": sub_count, "bytes": sub_bytes,
+                                   "lk_gbs": sub_bytes / np.sum(lk_sub_s) / 1e9,
+                                   "graph_gbs": sub_bytes / np.sum(graph_s) / 1e9,
+                                   "lk_items_per_s": sub_count / np.sum(lk_sub_s),
+                                   "graph_items_per_s": sub_count / np.sum(graph_s),
+                                   "lk_batch_ms": [round(1e3 * x, 3) for x in lk_sub_s],
+                                   "graph_batch_ms": [round(1e3 * x, 3) for x in graph_s],
+                                   "how": "the first batches of the prefix, one post and wait each, against "
+                                          "one CUDA graph of ordinary launches per batch"},
+                "items_per_batch": [len(it) for it, _ in bbat],
                 "tuned": tuned, "cluster": f"{n_sms} SMs as one cluster",
                 "parity_mismatches": batch_bad, "parity_items": int(len(par_items)),
-                "sample": f"seeded prefix: {len(bbat)} batches of the 1M-descriptor stream"}
+                "sample": f"seeded prefix: {len(bbat)} batches ({all_count} descriptors) of the 1M-descriptor "
+                          f"stream, batch b+1 posted while batch b runs"}
 
     # ---- serving: continuous admission under open-loop arrivals, per rate ----------
     scfg = wl.SERVING
@@ -642,12 +763,10 @@ def main():
     hist_in = pools.u8[: iso["hist_n"]]
     hist_out = torch.zeros(256, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
-    periods = args.iso_periods
-
-    def iso_run(init_kw, be_rate=0, alone=True):
-        """Critical periods alone, then under best-effort load, on one layout;
-        be_rate caps the best-effort cluster's loads (bytes/us, 0 = none)."""
-        out = {}
+    def iso_run(init_kw, periods, be_rate=0, alone=True):
+        """`periods` critical periods alone, then under best-effort load, on one
+        layout; be_rate caps the best-effort cluster's loads (bytes/us, 0 = none)."""
+        out = {"periods": periods}
         for loaded in ((False, True) if alone else (True,)):
             be_items = 0
             if loaded:
@@ -685,14 +804,14 @@ def main():
                 out["load_covered_critical_run"] = bool(float(be["t_complete_ns"].max()) >= last_crit)
         return out
 
-    iso_res = iso_run({"sizes": iso["sizes"]})
+    iso_res = iso_run({"sizes": iso["sizes"]}, args.iso_periods)
     # several persistent CTAs per SM (Sec. II.C's next step): the critical
     # cluster's 16 CTAs share SMs 0-15 with a best-effort cluster that spans
     # every SM, instead of owning 16 SMs the best-effort work cannot use
     with lk.lk_init([n_sms], device=dev, idle_lease_ns=5_000_000_000) as ctx:
         sm_ids = lk.lk_cluster_info(ctx, 0)          # the SM ids the GPU reports, ascending
     nc = iso["sizes"][0]
-    co = iso_run({"sizes": [nc, n_sms], "ctas_per_sm": 2, "smids": sm_ids[:nc] + sm_ids})
+    co = iso_run({"sizes": [nc, n_sms], "ctas_per_sm": 2, "smids": sm_ids[:nc] + sm_ids}, args.iso_sweep_periods)
     co["inflation_p999"] = co["loaded_us"]["p999"] / co["alone_us"]["p999"]
     co["layout"] = (f"ctas_per_sm = 2; critical: one CTA on each of the {nc} lowest SM ids; best effort: "
                     f"one CTA on every one of the {n_sms} SMs (the other CTA of the critical SMs)")
@@ -700,13 +819,12 @@ def main():
     # critical tail against the throughput given up, on the disjoint layout
     paced = {}
     for cap_gbs in (1000, 2000, 3000, 4000):
-        pr = iso_run({"sizes": iso["sizes"]}, be_rate=cap_gbs * 1000, alone=False)
+        pr = iso_run({"sizes": iso["sizes"]}, args.iso_sweep_periods, be_rate=cap_gbs * 1000, alone=False)
         paced[str(cap_gbs)] = {"loaded_us": pr["loaded_us"], "best_effort_gbs": pr["best_effort_gbs"],
                                "inflation_p999": pr["loaded_us"]["p999"] / iso_res["alone_us"]["p999"],
                                "load_covered_critical_run": pr["load_covered_critical_run"]}
     iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
     iso_res["inflation_max"] = iso_res["loaded_us"]["max"] / iso_res["alone_us"]["max"]
-    iso_res["periods"] = periods
     iso_res["coresident"] = co
     iso_res["best_effort_rate_cap_gbs"] = paced
     iso_sum_ok = abs(float(crit_out[0].cpu()) - oracle.sum_f32(pools.f32[: iso["crit_n"]].cpu().numpy())) <= \
@@ -771,21 +889,13 @@ def main():
     kms = dist.max(float(np.mean(kernel_ms)))
     if dist.rank != 0:
         return
-    line = {
-        "metric": METRIC, "value": p99, "unit": "us", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": kms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32 / uint8->int32 / fp32 (GEMM tiles: fp32 split into two bf16 parts on tcgen05, fp32 accumulate)",
-        "data": "synthetic (seeded device pools)",
-        "config": {"workload": WORKLOAD, "partition": "4 clusters x 37 SMs", "threads_per_cta": cfg["threads"],
-                   "items_per_step": items_per_step, "rate_per_s": cfg["rate_per_s"],
-                   "parallelism": f"replicas x{args.gpus} (no collective)",
-                   "l2": "inputs larger than L2: 4 GiB of device pools, random 16-B-aligned offsets",
-                   "step": "lk_init + trace + lk_dispose (one persistent-kernel launch)",
-                   "submitter_cpus": list(range(pin, pin + 4)) if pin >= 0 else "not pinned",
-                   "host": host_info()},
+    detail = {
+        "config": bench_config(args, cfg),
+        "step": "lk_init + trace + lk_dispose (one persistent-kernel launch)",
+        "submitter_cpus": list(range(pin, pin + 4)) if pin >= 0 else "not pinned",
+        "host": host_info(),
         "latency_us": lat_summary(lat),
         "arrival_to_complete_us": lat_summary(lat_arr),
-        "max_us": mx,
         "baseline_launch_sync_us": lat_summary(base),
         "baseline_occupancy_grid_us": dict(lat_summary(base_occ), grid=occ_grid,
                                            note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),
@@ -796,23 +906,77 @@ def main():
         "pingpong_floor_us": lat_summary(rtt),
         "throughput_items_per_s": items_all / wall_all,
         "wall_ms_per_step": 1000.0 * wall_all / args.steps,
-        "body_hbm_gbs": {k: round(v["gbs"], 1) for k, v in bw.items()},
         "body_detail": bw,
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
+        "e2e": {"latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy"},
         "paper_phases": phases,
         "batching": batching,
         "serving": serving,
         "isolation": iso_res,
-        "gpu_launches": args.steps,
-        "gpu_launches_note": "one persistent-kernel launch per timed step; items need no launch",
         "clocks": clk,
         "parity": {"sampled_items": int(len(pick)), "mismatches": bad, "exec_log": log_verdict},
     }
-    print(json.dumps(line))
+    with open(args.detail, "w") as fh:
+        json.dump(detail, fh, indent=1)
+
+    def trio(d):
+        return [r1(d["p50"]), r1(d["p99"]), r1(d["max"])]
+
+    body_frac = {k: round(v["gbs"] / hbm, 3) for k, v in bw.items()}
+    sat = max(serving["rates"].values(), key=lambda e: e["throughput_gbs"])
+    sat_c = max(serving["coalesced"]["rates"].values(), key=lambda e: e["throughput_gbs"]) \
+        if serving["coalesced"]["rates"] else None
+    gcmp = batching["graph_compared"]
+    headline = {
+        "lk_us_p50_p99_max": trio(lat_summary(lat)),
+        "launch_sync_us_p50_p99_max": trio(lat_summary(base)),
+        "occupancy_grid_us_p50_p99_max": trio(lat_summary(base_occ)),
+        "arrival_to_complete_us_p50_p99_max": trio(lat_summary(lat_arr)),
+        "floor_p50_us": r1(pct(rtt, 0.5)),
+        "nop_p50_us": {"relay": r1(pct(nop_lk, 0.5)), "direct": r1(pct(nop_direct, 0.5)),
+                       "mailbox": r1(pct(nop_mbox, 0.5)), "launch_sync": r1(pct(nop_base, 0.5)),
+                       "ring_1sm": r1(mbox["ring_1sm_nop_us"]["p50"])},
+        "floor_over_nop_p50": round(pct(rtt, 0.5) / pct(nop_lk, 0.5), 3),
+        "small_us_p99_max": {"lk": [r1(small["lk_us"]["p99"]), r1(small["lk_us"]["max"])],
+                             "launch_sync": [r1(small["launch_sync_us"]["p99"]), r1(small["launch_sync_us"]["max"])],
+                             "bit_exact": small["bit_exact"]},
+        "body_gbs": {k: round(v["gbs"]) for k, v in bw.items()},
+        "body_frac_of_measured_hbm": body_frac,
+        "isolation": {"periods": iso_res["periods"], "alone_p999_us": r1(iso_res["alone_us"]["p999"]),
+                      "loaded_p999_us": r1(iso_res["loaded_us"]["p999"]),
+                      "inflation_p999": round(iso_res["inflation_p999"], 2),
+                      "inflation_max": round(iso_res["inflation_max"], 2),
+                      "cap_2tbs_inflation_p999": round(iso_res["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2)},
+        "batching_gbs": {"lk_prefix": round(batching["lk_gbs"]), "prefix_items": batching["items"],
+                         "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
+        "serving_saturation_gbs": {"chunks": round(sat["throughput_gbs"]),
+                                   "coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
+        "parity": {"sampled_items_bad": bad, "exec_log_violations": log_verdict["violations"],
+                   "body_checks_bad": sum(v["parity"]["mismatches"] for v in bw.values()),
+                   "batching_bad": batching["parity_mismatches"], "small_exact": small["bit_exact"]},
+    }
+    line = {
+        "metric": METRIC, "value": p99, "unit": "us", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": kms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32 / uint8->int32 / fp32 (GEMM whole tiles: fp32 split in two bf16 parts, tcgen05, fp32 accumulate)",
+        "data": "synthetic (seeded device pools)",
+        "config": bench_config(args, cfg),
+        "max_us": mx,
+        "headline": headline,
+        "roofline": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in roofline.items()
+                     if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
+        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None,
+        "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "launch_sync_p99": r1(pct(e2e_base, 0.99))},
+        "gpu_launches": args.steps,
+        "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "detail_file": os.path.basename(args.detail),
+    }
+    print(json.dumps(line, separators=(",", ":")))
 
 
 if __name__ == "__main__":

@@ -495,11 +495,19 @@ int lk_dispose_timed(lk_ctx* ctx, uint64_t timeout_ns, float* kernel_ms);
  *   device: CUDA ordinal; in[0..n_in-1], out: device pointers, 16-byte
  *   aligned, as lk_submit.  ctas: 1..1024 (the array holds one partial sum per
  *   CTA: more is rejected with LK_EINVAL, nothing launched).
+ * The argument checks are lk_submit's (op, inputs, n limits, alignment, the
+ * pointers an op dereferences; d->aux is checked and then ignored), made
+ * before any CUDA call.
  * The first call on a device looks up the array's device address and clears
  * it (an asynchronous memset on `stream`); make that first call before any
  * stream capture.  All calls on a device share the one array and each
  * launch's last CTA leaves it zeroed for the next, so calls whose launches
- * overlap on the GPU race on it: serialise them (one stream, or events).
+ * overlap on the GPU race on it: serialise them (one stream, or events).  A
+ * launch that is refused (LK_EDEVICE) or that never starts (an earlier error
+ * on the stream) does not touch the array; a launch whose CTAs run always
+ * ends with its last CTA re-zeroing it, a body that gives up on a staging
+ * copy included; only a fault that destroys the CUDA context leaves it
+ * undefined, and the array goes with that context.
  * Returns LK_OK (launched), LK_EINVAL, LK_EDEVICE (CUDA error). */
 int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
                       int ctas, int threads, void* stream);

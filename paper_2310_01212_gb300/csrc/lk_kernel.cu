@@ -41,6 +41,7 @@
 #include "lk_backend.h"
 #include "lk_bodies.cuh"
 #include "lk_layout.h"
+#include "lk_validate.h"
 
 using namespace lk;
 
@@ -1180,14 +1181,11 @@ extern "C" int lk_baseline_graph(int device, const lk_batch_item* items, uint32_
   if ((count > 0 && !items) || max_ctas < 1 || max_ctas > LK_MAX_CTAS || threads < 64 || threads > 1024 ||
       threads % 32 || reps < 1 || !ms)
     return LK_EINVAL;
-  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1, 0};
   for (uint32_t i = 0; i < count; ++i) {
     const lk_batch_item& it = items[i];
-    if (it.op >= LK_OP_COUNT) return LK_EINVAL;
-    const void* ins[2] = {it.in0, it.in1};
-    for (int j = 0; j < need[it.op]; ++j)
-      if (((uintptr_t)ins[j] & 15u) || (it.n > 0 && !ins[j])) return LK_EINVAL;
-    if ((uintptr_t)it.out & 15u) return LK_EINVAL;
+    const lk_desc d{it.op, 0, it.n, 0};
+    const int need = lk_op_inputs(it.op);
+    if (need < 0 || lk_validate_desc(&d, it.in0, it.in1, need, it.out) != LK_OK) return LK_EINVAL;
   }
   if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
   preload_all();
@@ -1244,31 +1242,27 @@ extern "C" int lk_baseline_graph(int device, const lk_batch_item* items, uint32_
  * lk_baseline_run_trace takes that block from cudaMalloc; this entry point
  * takes it from the file-scope array below instead, so it never allocates.
  * Capacity: one lk_scratch (5,248 bytes), i.e. at most LK_MAX_CTAS CTAs per
- * launch.  Every GPU that loads this library keeps the array until exit. */
+ * launch.  Every GPU that loads this library keeps the array until exit.
+ * State between calls: lk_ordinary ignores a body's staging failure and still
+ * counts every CTA's arrival, so a launch whose CTAs run always ends with
+ * its last CTA re-zeroing the counter and bins; a refused launch never
+ * touches the array. */
 static __device__ __align__(256) lk_scratch g_noalloc_scratch;
 
 namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[256];   /* device address of g_noalloc_scratch, per device */
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 }  // namespace
 
 extern "C" int lk_launch_noalloc(int device, const lk_desc* d, const void* const* in, int n_in, void* out,
                                  int ctas, int threads, void* stream) {
-  if (!d || d->flags != 0 || device < 0 || device >= 256) return LK_EINVAL;
-  static const int need[LK_OP_COUNT] = {0, 2, 1, 1, 2, 1, 1, 1, 0};
-  if (d->op >= LK_OP_COUNT || n_in != need[d->op] || (n_in > 0 && !in)) return LK_EINVAL;
+  /* the descriptor checks of lk_submit (op, inputs, sizes, alignment, the
+   * pointers each op dereferences), then this entry point's own limits */
+  if (!d || device < 0 || device >= 256 || n_in < 0 || n_in > 2 || (n_in > 0 && !in)) return LK_EINVAL;
+  const int vrc = lk_validate_desc(d, n_in > 0 ? in[0] : nullptr, n_in > 1 ? in[1] : nullptr, n_in, out);
+  if (vrc != LK_OK) return vrc;
   if (ctas < 1 || ctas > LK_MAX_CTAS) return LK_EINVAL;   /* beyond the static scratch */
   if (threads < 64 || threads > 1024 || threads % 32) return LK_EINVAL;
-  if (d->n > (1ull << 40) || (d->op == LK_OP_HIST_U8 && d->n > 0x7fffffffull) ||
-      (d->op == LK_OP_GEMM64_F32 && d->n > (1ull << 28)))
-    return LK_EINVAL;
-  for (int i = 0; i < n_in; ++i)
-    if (!aligned16(in[i]) || (d->n > 0 && !in[i])) return LK_EINVAL;
-  if (!aligned16(out)) return LK_EINVAL;
-  if ((d->op == LK_OP_SUM_F32 || d->op == LK_OP_HIST_U8) && !out) return LK_EINVAL;
-  if (d->op != LK_OP_NOP && d->op != LK_OP_SUM_F32 && d->op != LK_OP_HIST_U8 && d->n > 0 && !out) return LK_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
   preload_all();
   if (g_preload_err != cudaSuccess) return LK_EDEVICE;

@@ -28,6 +28,7 @@
 
 #include "lk_backend.h"
 #include "lk_layout.h"
+#include "lk_validate.h"
 
 namespace {
 
@@ -109,61 +110,11 @@ static int device_err_to_rc(uint32_t e) {
   return LK_EDEVICE;
 }
 
-/* Inputs each op takes and whether it writes `out`. */
-static int op_inputs(uint32_t op) {
-  switch (op) {
-    case LK_OP_NOP: return 0;
-    case LK_OP_ADD_I32: return 2;
-    case LK_OP_HIST_U8: return 1;
-    case LK_OP_SUM_F32: return 1;
-    case LK_OP_GEMM64_F32: return 2;
-    case LK_OP_COPY_I32: return 1;
-    case LK_OP_COMBINE_SUM: return 1;
-    case LK_OP_COMBINE_HIST: return 1;
-    case LK_OP_SPIN: return 0;
-    default: return -1;
-  }
-}
-
-static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+static int op_inputs(uint32_t op) { return lk_op_inputs(op); }
 
 /* Argument checks shared by lk_submit and the finite / trace paths. */
 static int validate(const lk_desc* d, const void* in0, const void* in1, int n_in, void* out) {
-  if (!d) return LK_EINVAL;
-  int need = op_inputs(d->op);
-  if (need < 0 || n_in != need) return LK_EINVAL;
-  if (d->flags != 0) return LK_EINVAL;
-  if (d->n > (1ull << 40) || d->aux >= (1ull << 40) || (d->aux != 0 && d->aux < LK_RATE_MIN)) return LK_EINVAL;
-  const void* ins[2] = {in0, in1};
-  for (int i = 0; i < need; ++i) {
-    if (!aligned16(ins[i]) || (uintptr_t)ins[i] > LK_LOW48) return LK_EINVAL;
-    if (d->n > 0 && !ins[i]) return LK_EINVAL;
-  }
-  if (!aligned16(out) || (uintptr_t)out > LK_LOW48) return LK_EINVAL;
-  switch (d->op) {
-    case LK_OP_NOP: break;
-    case LK_OP_SUM_F32:
-      if (!out) return LK_EINVAL;
-      break;
-    case LK_OP_HIST_U8:
-      if (!out) return LK_EINVAL;
-      if (d->n > 0x7fffffffull) return LK_EINVAL;   /* bins are int32 */
-      break;
-    case LK_OP_GEMM64_F32:
-      if (d->n > (1ull << 28)) return LK_EINVAL;
-      if (d->n > 0 && !out) return LK_EINVAL;
-      break;
-    case LK_OP_COMBINE_SUM:
-    case LK_OP_COMBINE_HIST:
-      if (!out || d->n > (1ull << 20)) return LK_EINVAL;
-      break;
-    case LK_OP_SPIN:
-      if (d->n > 0xffffffffull) return LK_EINVAL;   /* out is optional */
-      break;
-    default:
-      if (d->n > 0 && !out) return LK_EINVAL;
-  }
-  return LK_OK;
+  return lk_validate_desc(d, in0, in1, n_in, out);
 }
 
 /* Publish ticket t into slot s (see lk_wire): a release fence orders every

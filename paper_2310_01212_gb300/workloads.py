@@ -318,24 +318,6 @@ def batching_parity_batch(pools: Pools, seed: int, count: int = 48, n_hi: int = 
     return it, meta
 
 
-def check_batching_parity(pools: Pools, meta: dict, oracle) -> int:
-    """Number of items of a parity batch whose output differs from the oracle."""
-    bad = 0
-    add_out = pools.out_add.view(-1)
-    for i in range(meta["op"].size):
-        k = int(meta["n"][i])
-        if meta["op"][i] == lk.LK_OP_ADD_I32:
-            a = pools.i32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
-            b = pools.i32[int(meta["off1"][i]):int(meta["off1"][i]) + k].cpu().numpy()
-            o = add_out[int(meta["offo"][i]):int(meta["offo"][i]) + k].cpu().numpy()
-            bad += 0 if np.array_equal(o, oracle.add_i32(a, b)) else 1
-        else:
-            x = pools.f32[int(meta["off0"][i]):int(meta["off0"][i]) + k].cpu().numpy()
-            o = float(pools.out_sum[int(meta["offo"][i]), 0].cpu())
-            bad += 0 if abs(o - oracle.sum_f32(x)) <= 1e-4 * oracle.abs_sum_f32(x) else 1
-    return bad
-
-
 def serving_requests(pools: Pools, seed: int, rate: float, seconds: float, cfg: dict = SERVING,
                      s_hi: int | None = None, outputs=None):
     """Open-loop Poisson requests at `rate` per second for `seconds`; inputs are

@@ -119,13 +119,62 @@ def test_gemm_integer_matrices_match_numpy_exactly(oracle_lib):
     assert np.array_equal(C, want.astype(np.float64))
 
 
-def test_gemm_abs_bound(oracle_lib):
+# ---- the per-element GEMM bound sum_k |a_ik b_kj| -------------------------------------
+# Pinned by values the mathematics fixes, not by a second copy of the formula:
+# each case below fails a bound that takes |sum_k a b| instead of sum_k |a b|,
+# drops the absolute value of one operand, or transposes an operand.
+
+def test_gemm_abs_bound_all_ones_is_64(oracle_lib):
+    ones = np.ones((2, 64, 64), np.float32)
+    assert np.all(oracle_lib.gemm64_abs_bound(ones, ones) == 64.0)
+    # negated operands: the products are all +1 or all -1, the bound stays 64
+    assert np.all(oracle_lib.gemm64_abs_bound(-ones, ones) == 64.0)
+
+
+def test_gemm_abs_bound_identity_is_abs_b(oracle_lib):
+    B = synth.normal_f32(9, 2, 3 * 4096).reshape(3, 64, 64)
+    I = np.broadcast_to(np.eye(64, dtype=np.float32), (3, 64, 64)).copy()
+    assert np.array_equal(oracle_lib.gemm64_abs_bound(I, B), np.abs(B).astype(np.float64))
+    # B = I: the bound is |A| (a transposed operand would give |A|^T)
+    A = synth.normal_f32(9, 3, 3 * 4096).reshape(3, 64, 64)
+    assert np.array_equal(oracle_lib.gemm64_abs_bound(A, I), np.abs(A).astype(np.float64))
+
+
+def test_gemm_abs_bound_signed_diagonal(oracle_lib):
+    # A = diag(d) with signs: bound[i][j] = |d_i| |b_ij| exactly (one product per sum)
+    d = synth.normal_f32(9, 4, 64)
+    A = np.diag(d)[None].astype(np.float32)
+    B = synth.normal_f32(9, 5, 4096).reshape(1, 64, 64)
+    want = np.abs(d.astype(np.float64))[:, None] * np.abs(B[0].astype(np.float64))
+    assert np.array_equal(oracle_lib.gemm64_abs_bound(A, B)[0], want)
+
+
+def test_gemm_abs_bound_signed_integers_exact(oracle_lib):
+    # signed integer tiles: sum_k |a||b| is an exact integer, computed in int64;
+    # |sum_k a b| (an easy slip) differs from it almost everywhere
+    A = synth.int32_uniform(9, 6, 4 * 4096, -1000, 1000).reshape(4, 64, 64)
+    B = synth.int32_uniform(9, 7, 4 * 4096, -1000, 1000).reshape(4, 64, 64)
+    want = np.matmul(np.abs(A.astype(np.int64)), np.abs(B.astype(np.int64)))
+    got = oracle_lib.gemm64_abs_bound(A.astype(np.float32), B.astype(np.float32))
+    assert np.array_equal(got, want.astype(np.float64))
+    signed = np.abs(np.matmul(A.astype(np.int64), B.astype(np.int64)))
+    assert np.count_nonzero(signed != want) > 0.99 * want.size
+
+
+def test_gemm_abs_bound_cancelling_row(oracle_lib):
+    # row 0 of A = (1, -1, 0, ...), B all ones: C[0][j] = 0, bound[0][j] = 2
+    A = np.zeros((1, 64, 64), np.float32)
+    A[0, 0, 0], A[0, 0, 1] = 1.0, -1.0
+    B = np.ones((1, 64, 64), np.float32)
+    assert np.all(oracle_lib.gemm64_f32(A, B)[0, 0] == 0.0)
+    assert np.all(oracle_lib.gemm64_abs_bound(A, B)[0, 0] == 2.0)
+    assert np.all(oracle_lib.gemm64_abs_bound(A, B)[0, 1:] == 0.0)
+
+
+def test_gemm_abs_bound_dominates_the_product(oracle_lib):
     A = synth.normal_f32(9, 1, 4096).reshape(1, 64, 64)
     B = synth.normal_f32(9, 2, 4096).reshape(1, 64, 64)
-    bound = oracle_lib.gemm64_abs_bound(A, B)
-    want = np.abs(A[0].astype(np.float64))[:, :, None] * np.abs(B[0].astype(np.float64))[None, :, :]
-    assert np.allclose(bound[0], want.sum(axis=1), rtol=1e-13, atol=0)
-    assert np.all(bound >= np.abs(oracle_lib.gemm64_f32(A, B)))
+    assert np.all(oracle_lib.gemm64_abs_bound(A, B) >= np.abs(oracle_lib.gemm64_f32(A, B)))
 
 
 # ---- the compute-bound loop (Sec. III) ----------------------------------------------
