@@ -266,7 +266,7 @@ def run_reference(args, dist: Dist):
     print(json.dumps(line))
 
 
-def r1(x):
+def rnd1(x):
     return None if x is None else round(float(x), 1)
 
 
@@ -276,6 +276,80 @@ def bench_config(args, cfg=None) -> dict:
             "items_per_step": args.items, "rate_per_s": 20000.0,
             "parallelism": f"replicas x{args.gpus} (no collective)",
             "l2": "inputs larger than L2: 4 GiB of device pools, random 16-B-aligned offsets"}
+
+
+def build_headline(d: dict, hbm: float) -> dict:
+    """The headline numbers of the printed line, from the detail dict (every
+    value there is already a summary; nothing is recomputed)."""
+    def trio(x):
+        return [rnd1(x["p50"]), rnd1(x["p99"]), rnd1(x["max"])]
+
+    nop = d["dispatch_nop_us"]
+    bw = d["body_detail"]
+    iso = d["isolation"]
+    small = d["config_small"]
+    bat = d["batching"]
+    gcmp = bat["graph_compared"]
+    srv = d["serving"]
+    sat = max(srv["rates"].values(), key=lambda e: e["throughput_gbs"])
+    sat_c = max(srv["coalesced"]["rates"].values(), key=lambda e: e["throughput_gbs"]) \
+        if srv["coalesced"]["rates"] else None
+    return {
+        "lk_us_p50_p99_max": trio(d["latency_us"]),
+        "launch_sync_us_p50_p99_max": trio(d["baseline_launch_sync_us"]),
+        "occupancy_grid_us_p50_p99_max": trio(d["baseline_occupancy_grid_us"]),
+        "arrival_to_complete_us_p50_p99_max": trio(d["arrival_to_complete_us"]),
+        "floor_p50_us": rnd1(d["pingpong_floor_us"]["p50"]),
+        "nop_p50_us": {"relay": rnd1(nop["lk"]["p50"]), "direct": rnd1(nop["lk_direct"]["p50"]),
+                       "mailbox": rnd1(nop["lk_mailbox"]["p50"]), "launch_sync": rnd1(nop["launch_sync"]["p50"]),
+                       "ring_1sm": rnd1(d["paper_mailbox_vs_ring"]["ring_1sm_nop_us"]["p50"])},
+        "floor_over_nop_p50": round(d["pingpong_floor_us"]["p50"] / nop["lk"]["p50"], 3),
+        "nop_device_p50_us": {k[:-3]: rnd1(v["p50"]) for k, v in nop["lk_device_phases"].items()
+                              if k.endswith("_us")},
+        "small_us_p99_max": {"lk": [rnd1(small["lk_us"]["p99"]), rnd1(small["lk_us"]["max"])],
+                             "launch_sync": [rnd1(small["launch_sync_us"]["p99"]),
+                                             rnd1(small["launch_sync_us"]["max"])],
+                             "bit_exact": small["bit_exact"]},
+        "body_gbs": {k: round(v["gbs"]) for k, v in bw.items()},
+        "body_frac_of_measured_hbm": {k: round(v["gbs"] / hbm, 3) for k, v in bw.items()},
+        "isolation": {"periods": iso["periods"], "alone_p999_us": rnd1(iso["alone_us"]["p999"]),
+                      "loaded_p999_us": rnd1(iso["loaded_us"]["p999"]),
+                      "inflation_p999": round(iso["inflation_p999"], 2),
+                      "inflation_max": round(iso["inflation_max"], 2),
+                      "cap_2tbs_inflation_p999": round(iso["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2)},
+        "batching_gbs": {"lk_prefix": round(bat["lk_gbs"]), "prefix_items": bat["items"],
+                         "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
+        "serving_saturation_gbs": {"chunks": round(sat["throughput_gbs"]),
+                                   "coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
+        "parity": {"sampled_items_bad": d["parity"]["mismatches"],
+                   "exec_log_violations": d["parity"]["exec_log"]["violations"],
+                   "body_checks_bad": sum(v["parity"]["mismatches"] for v in bw.values()),
+                   "batching_bad": bat["parity_mismatches"], "small_exact": small["bit_exact"]},
+    }
+
+
+def exec_log_phases(log) -> dict:
+    """Per descriptor, from one context's execution log (device %globaltimer,
+    32 ns ticks): pick -> last CTA start (relay), last start -> last end
+    (body), last end -> completion stamp of the last CTA to arrive; medians
+    and p99 in us over the descriptors."""
+    key = log["cluster"].astype(np.int64) << 40 | log["seq"].astype(np.int64)
+    uk, inv = np.unique(key, return_inverse=True)
+    pick = np.zeros(uk.size, np.int64)
+    start = np.zeros(uk.size, np.int64)
+    end = np.zeros(uk.size, np.int64)
+    done = np.zeros(uk.size, np.int64)
+    pick[inv] = log["t_pick_ns"].astype(np.int64)
+    np.maximum.at(start, inv, log["t_start_ns"].astype(np.int64))
+    np.maximum.at(end, inv, log["t_end_ns"].astype(np.int64))
+    np.maximum.at(done, inv, log["t_done_ns"].astype(np.int64))
+    ok = done > 0
+    out = {"descriptors": int(ok.sum())}
+    for name, v in (("pick_to_last_start", start - pick), ("last_start_to_last_end", end - start),
+                    ("last_end_to_done", done - end), ("pick_to_done", done - pick)):
+        v = v[ok] / 1000.0
+        out[name + "_us"] = {"p50": pct(v, 0.5), "p99": pct(v, 0.99)}
+    return out
 
 
 # ---- oracle checks of the bench's outputs (checking code stays out of the package) ----
@@ -559,8 +633,10 @@ def main():
     nop = np.zeros(2 * items_per_step, dtype=lk.TRACE_ITEM_DTYPE)
     nop["cluster"] = np.arange(nop.size) % 4
     nop["op"] = lk.LK_OP_NOP
-    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000) as ctx:
+    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000,
+                    exec_log_cap=nop.size // len(sizes) + 64) as ctx:
         rc, r1 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True, pin_cpu_base=pin)
+        nop_phases = exec_log_phases(lk.lk_exec_log(ctx)[0])
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT) as ctx:
         rc, r3 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True, pin_cpu_base=pin)
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_MAILBOX) as ctx:
@@ -901,7 +977,8 @@ def main():
                                            note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),
         "config_small": small,
         "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
-                            "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base)},
+                            "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base),
+                            "lk_device_phases": nop_phases},
         "paper_mailbox_vs_ring": mbox,
         "pingpong_floor_us": lat_summary(rtt),
         "throughput_items_per_s": items_all / wall_all,
@@ -922,42 +999,7 @@ def main():
     with open(args.detail, "w") as fh:
         json.dump(detail, fh, indent=1)
 
-    def trio(d):
-        return [r1(d["p50"]), r1(d["p99"]), r1(d["max"])]
-
-    body_frac = {k: round(v["gbs"] / hbm, 3) for k, v in bw.items()}
-    sat = max(serving["rates"].values(), key=lambda e: e["throughput_gbs"])
-    sat_c = max(serving["coalesced"]["rates"].values(), key=lambda e: e["throughput_gbs"]) \
-        if serving["coalesced"]["rates"] else None
-    gcmp = batching["graph_compared"]
-    headline = {
-        "lk_us_p50_p99_max": trio(lat_summary(lat)),
-        "launch_sync_us_p50_p99_max": trio(lat_summary(base)),
-        "occupancy_grid_us_p50_p99_max": trio(lat_summary(base_occ)),
-        "arrival_to_complete_us_p50_p99_max": trio(lat_summary(lat_arr)),
-        "floor_p50_us": r1(pct(rtt, 0.5)),
-        "nop_p50_us": {"relay": r1(pct(nop_lk, 0.5)), "direct": r1(pct(nop_direct, 0.5)),
-                       "mailbox": r1(pct(nop_mbox, 0.5)), "launch_sync": r1(pct(nop_base, 0.5)),
-                       "ring_1sm": r1(mbox["ring_1sm_nop_us"]["p50"])},
-        "floor_over_nop_p50": round(pct(rtt, 0.5) / pct(nop_lk, 0.5), 3),
-        "small_us_p99_max": {"lk": [r1(small["lk_us"]["p99"]), r1(small["lk_us"]["max"])],
-                             "launch_sync": [r1(small["launch_sync_us"]["p99"]), r1(small["launch_sync_us"]["max"])],
-                             "bit_exact": small["bit_exact"]},
-        "body_gbs": {k: round(v["gbs"]) for k, v in bw.items()},
-        "body_frac_of_measured_hbm": body_frac,
-        "isolation": {"periods": iso_res["periods"], "alone_p999_us": r1(iso_res["alone_us"]["p999"]),
-                      "loaded_p999_us": r1(iso_res["loaded_us"]["p999"]),
-                      "inflation_p999": round(iso_res["inflation_p999"], 2),
-                      "inflation_max": round(iso_res["inflation_max"], 2),
-                      "cap_2tbs_inflation_p999": round(iso_res["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2)},
-        "batching_gbs": {"lk_prefix": round(batching["lk_gbs"]), "prefix_items": batching["items"],
-                         "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
-        "serving_saturation_gbs": {"chunks": round(sat["throughput_gbs"]),
-                                   "coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
-        "parity": {"sampled_items_bad": bad, "exec_log_violations": log_verdict["violations"],
-                   "body_checks_bad": sum(v["parity"]["mismatches"] for v in bw.values()),
-                   "batching_bad": batching["parity_mismatches"], "small_exact": small["bit_exact"]},
-    }
+    headline = build_headline(detail, hbm)
     line = {
         "metric": METRIC, "value": p99, "unit": "us", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": kms, "higher_is_better": False, "scaling": "weak",
@@ -971,7 +1013,7 @@ def main():
                      if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
         "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None,
         "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "launch_sync_p99": r1(pct(e2e_base, 0.99))},
+                "launch_sync_p99": rnd1(pct(e2e_base, 0.99))},
         "gpu_launches": args.steps,
         "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "detail_file": os.path.basename(args.detail),

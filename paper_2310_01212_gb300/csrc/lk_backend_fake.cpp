@@ -6,7 +6,8 @@
  * layout as the persistent kernel: per cluster, one thread acquires ring
  * slots in FIFO order (or, with LK_INIT_MAILBOX, runs the one-deep four-phase
  * mailbox handshake), reports WORKING / FINISHED in the from_GPU words,
- * release-stores `done`, writes execution-log records for every rank, honours
+ * release-stores every rank's completion word (mailbox mode: `done`), writes
+ * execution-log records for every rank, honours
  * EXIT, the abort word and the idle lease.  Work bodies are not run: this
  * backend exists to test the host runtime (tickets, ring-full refusals,
  * handles, waits, timeouts, dispose) on a machine without a GPU.
@@ -119,6 +120,7 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
   const int fail_code = (int)env_u64("LK_FAKE_FAIL_CODE", LK_DERR_BADDESC);
   const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
   const bool mailbox = (a.flags & LK_KFLAG_MAILBOX) != 0;
+  const int32_t rd_off = a.rd_off[c];   /* "device" memory is host memory here */
   uint64_t finished = 0;
   int err = 0;
   /* bounded wait for `ready` (abort, idle lease), as the kernel's waits */
@@ -196,7 +198,9 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
     }
     if (k < drop_after) {
       finished = k + 1;
-      if (!mailbox) st_rel(&a.cword[c].done, k + 1);
+      /* ring modes: every rank publishes its own completion word */
+      if (!mailbox)
+        for (size_t r = 0; r < ctas.size(); ++r) st_rel(&a.rdone[rd_off + r], k + 1);
       st_rel(&a.cword[c].status, (uint64_t)LK_ST_FINISHED);
     }
   }

@@ -78,15 +78,22 @@ __device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
  * thread: every extra read in flight on the slot's line makes the host's
  * stores to that line wait for ownership again.  The acquire fence after a
  * successful probe pairs with the host's release fence before its stores.
- * Returns 0 or an LK_DERR_* reason (lease ran out, abort). */
+ * Each probe also loads *pre (device memory, relaxed, in flight beside the
+ * probe, so it costs no extra time) into *pre_val: the completion word the
+ * caller gates on next, read while it waits anyway; the same fence makes
+ * that load an acquire.  Returns 0 or an LK_DERR_* reason (lease ran out,
+ * abort). */
 __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, uint64_t tag, uint64_t seq,
-                                           lk_slot& out) {
+                                           lk_slot& out, const uint64_t* pre, uint64_t* pre_val) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
   uint64_t w[6];
   for (uint32_t it = 1;; ++it) {
+    uint64_t pv;
+    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(pv) : "l"(pre) : "memory");
     probe(s, w);
+    *pre_val = pv;
     if (tags_match(w, tag)) break;
     if ((it & 63) == 0) {
       if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
@@ -187,6 +194,23 @@ __device__ __forceinline__ void relay_publish(lk_wire* rs, uint64_t k, const lk_
   asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[6]), "l"(tag | (d.t_pick & LK_LOW48)) : "memory");
 }
 
+__device__ __forceinline__ void relay_probe(const lk_wire* rs, uint64_t* w) {
+  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(&rs->w[0]) : "memory");
+  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[2]), "=l"(w[3]) : "l"(&rs->w[2]) : "memory");
+  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
+  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
+}
+__device__ __forceinline__ bool relay_current(const uint64_t* w, uint64_t tag) {
+  return tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag;
+}
+
+/* A relayed member waits for descriptor k in relay slot rs.  Two probes are
+ * kept in flight, half a round trip apart (the first probe's round trip sets
+ * the stagger, at most 1 us): a probe can only see the slot as it was when it
+ * reached L2, so one probe at a time samples the slot once per round trip,
+ * and two staggered probes twice.  Members read L2, not host memory, so the
+ * extra reads delay no host store.  Returns 0, -1 (the master stopped) or an
+ * LK_DERR_* reason. */
 __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster* dc, const lk_wire* rs, uint64_t k,
                                             lk_slot& out) {
   const uint64_t tag = (k / LK_BCAST_DEPTH + 1) & 0xffffull;
@@ -194,27 +218,43 @@ __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
   const uint64_t limit = a.lease_ns + 1000000000ull;
-  uint64_t w[8];
-  for (uint32_t it = 1;; ++it) {
-    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(&rs->w[0]) : "memory");
-    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[2]), "=l"(w[3]) : "l"(&rs->w[2]) : "memory");
-    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
-    asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
-    if (tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag) break;
-    if ((it & 255) == 0) {
-      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
-      if (ld_acquire_gpu(&dc->gen) == LK_GEN_STOP) return -1;
-      const uint64_t now = gtime();
-      if (now - t_last > limit) {
-        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
-        if (h == hb) return LK_DERR_STALL;
-        hb = h;
-        t_last = now;
-      }
+  uint64_t wa[8], wb[8];
+  bool in_b = false;   /* the current copy arrived in wb (element-wise select keeps both in registers) */
+  relay_probe(rs, wa);
+  if (!relay_current(wa, tag)) {
+    uint64_t rtt = gtime() - t_last;
+    rtt = rtt > 2000u ? 2000u : rtt;
+    relay_probe(rs, wa);
+    const uint64_t t1 = gtime();
+    while (gtime() - t1 < rtt / 2) {
     }
-    bo.pause();
+    relay_probe(rs, wb);
+    for (uint32_t it = 1;; ++it) {
+      if (relay_current(wa, tag)) break;
+      relay_probe(rs, wa);
+      if (relay_current(wb, tag)) {
+        in_b = true;
+        break;
+      }
+      relay_probe(rs, wb);
+      if ((it & 127) == 0) {
+        if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+        if (ld_acquire_gpu(&dc->gen) == LK_GEN_STOP) return -1;
+        const uint64_t now = gtime();
+        if (now - t_last > limit) {
+          const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
+          if (h == hb) return LK_DERR_STALL;
+          hb = h;
+          t_last = now;
+        }
+      }
+      bo.pause();
+    }
   }
   fence_acq_rel_gpu();
+  uint64_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) w[i] = in_b ? wb[i] : wa[i];
   lk_wire_decode(w, k + 1, &out);
   /* the master's pickup time: its low 48 bits under this reader's high bits */
   const uint64_t now = gtime();
@@ -458,7 +498,8 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(64) lk_slot s_desc;
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
-  __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag */
+  __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag (mailbox mode) */
+  __shared__ int32_t s_last;           /* this CTA arrived last on the descriptor's slot */
   __shared__ float s_red[32];
   __shared__ __align__(8) uint64_t s_bars[LK_ALL_BARS];
   __shared__ uint64_t s_tstart;
@@ -559,9 +600,10 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   const bool mailbox = (a.flags & LK_KFLAG_MAILBOX) != 0;   /* implies relay */
   lk_dcluster* dc = a.dcl + c;
   const lk_wire* ring = a.ring + (size_t)c * (a.ring_mask + 1);
+  uint64_t* my_done = a.rdone + a.rd_off[c] + r;   /* this CTA's host-visible completion word */
   uint32_t phase = 0;
   int final_err = 0;
-  uint64_t known_done = 0;   /* latest dev_done this CTA has seen */
+  uint64_t known_done = 0;   /* mailbox master: descriptors it completed */
 
   for (uint64_t k = 0;; ++k) {
     const uint32_t slot = (uint32_t)(k % LK_BCAST_DEPTH);
@@ -571,36 +613,43 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       lk_slot dsc;
       const lk_wire* w = ring + (k & a.ring_mask);
       const uint64_t tag = lk_lap_tag(k, a.ring_log2);
+      /* slot k mod D (relay copy, partials, histogram accumulator, arrival
+       * counter) is free once descriptor k+1-D, its previous user, finished */
+      const uint64_t need = k + 1 > LK_BCAST_DEPTH ? k + 1 - LK_BCAST_DEPTH : 0;
+      uint64_t slot_seen = 0;
       if (master && mailbox) {
         err = take_from_mailbox(a, c, k, dsc);
         if (!err) dsc.t_pick = gtime();
+        slot_seen = known_done;   /* the mailbox master completes each descriptor itself */
       } else if (!relay || master) {
-        err = take_from_ring(a, w, tag, k + 1, dsc);
+        err = take_from_ring(a, w, tag, k + 1, dsc, &dc->slot_done[slot], &slot_seen);
         if (!err) dsc.t_pick = gtime();
       } else {
         err = take_from_relay(a, dc, &dc->relay[slot], k, dsc);
       }
-      /* A relayed member needs no check below: the master completes
-       * descriptor k-1 (every rank finished it) before it relays k, so every
-       * earlier descriptor has finished by the time a member sees k.  Members
-       * that read the ring themselves (LK_INIT_DIRECT) can run ahead. */
-      const bool gated = relay && !master;
-      /* relay-ring slot k mod D (relay copy, partials, histogram accumulator)
-       * is free once descriptor k+1-D has finished */
-      if (!err && !gated && k + 1 > LK_BCAST_DEPTH && known_done < k + 1 - LK_BCAST_DEPTH &&
-          (master ? relay : dsc.cmd != LK_CMD_EXIT)) {
-        const int ww = wait_word(a, &dc->dev_done, k + 1 - LK_BCAST_DEPTH, false, &known_done);
+      /* Who gates: the CTA that reads the ring or mailbox for the cluster --
+       * the master, which relays descriptor k only once slot k mod D is free
+       * (so a relayed member needs no check: the slot it reads was free when
+       * the master wrote it), or, with LK_INIT_DIRECT, every CTA for itself
+       * (EXIT uses no slot there). */
+      const bool self_gate = relay ? master : (!err && dsc.cmd != LK_CMD_EXIT);
+      if (!err && self_gate && need && slot_seen < need) {
+        const int ww = wait_word(a, &dc->slot_done[slot], need, false);
         err = ww < 0 ? LK_DERR_STALL : ww;
+      }
+      /* a batch starts once every earlier descriptor of the cluster finished
+       * (its ticket and combine state are then at rest): the latest user of
+       * each slot */
+      if (!err && self_gate && dsc.cmd == LK_CMD_WORK + LK_OP_BATCH) {
+        for (uint64_t j = 1; j <= k && j <= LK_BCAST_DEPTH && !err; ++j) {
+          const uint64_t q = k - j;
+          const int ww = wait_word(a, &dc->slot_done[q % LK_BCAST_DEPTH], q + 1, false);
+          err = ww < 0 ? LK_DERR_STALL : ww;
+        }
       }
       if (relay && master) {
         if (!err) relay_publish(&dc->relay[slot], k, dsc);
         else st_release_gpu(&dc->gen, LK_GEN_STOP);
-      }
-      /* a batch starts once every earlier descriptor of the cluster finished
-       * (its ticket and combine state are then at rest) */
-      if (!err && !gated && dsc.cmd == LK_CMD_WORK + LK_OP_BATCH && k > 0 && known_done < k) {
-        const int ww = wait_word(a, &dc->dev_done, k, false, &known_done);
-        err = ww < 0 ? LK_DERR_STALL : ww;
       }
       if (err) {
         if (err > 0) {
@@ -616,6 +665,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       }
       s_err = 0;
       s_found = 0;
+      s_last = 0;
       s_tstart = gtime();
     }
     __syncthreads();
@@ -631,31 +681,69 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
-    /* ---- finish: every rank raises its flag; rank 0 completes ---------- */
     uint64_t t_end = 0, t_done = 0;
-    if (tid == 0) {
-      t_end = gtime();
-      if (S > 1) st_release_gpu(&dc->flag[r], k + 1);   /* orders this CTA's writes (after the barrier) */
-    }
-    if (master) {
-      if (S > 1) {
-        const int gerr = gather_flags(a, dc->flag, S, k + 1, &s_found);
-        if (gerr && (tid & 31) == 0) s_err = gerr;
-      }
-      __syncthreads();
-      if (!s_err) {
-        if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
-        else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+    if (tid == 0) t_end = gtime();
+    if (mailbox) {
+      /* ---- finish, one-deep mailbox: rank 0 gathers every rank's flag,
+       * combines, and answers THREAD_FINISHED ---------------------------- */
+      if (tid == 0 && S > 1) st_release_gpu(&dc->flag[r], k + 1);   /* orders this CTA's writes (after the barrier) */
+      if (master) {
+        if (S > 1) {
+          const int gerr = gather_flags(a, dc->flag, S, k + 1, &s_found);
+          if (gerr && (tid & 31) == 0) s_err = gerr;
+        }
         __syncthreads();
-        if (tid == 0) {
-          if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every rank has left the claim loop */
-          /* one system-scope fence orders every output write (this CTA's,
-           * and the other ranks' through their flags) before both stores */
-          fence_acq_rel_sys();
-          asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&dc->dev_done), "l"(k + 1) : "memory");
-          known_done = k + 1;
-          if (mailbox) st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);   /* the host re-arms */
-          else st_relaxed_sys(&a.cword[c].done, d.seq);
+        if (!s_err) {
+          if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
+          else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+          __syncthreads();
+          if (tid == 0) {
+            if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every rank has left the claim loop */
+            /* one system-scope fence orders every output write (this CTA's,
+             * and the other ranks' through their flags) before the stores */
+            fence_acq_rel_sys();
+            asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&dc->slot_done[slot]), "l"(k + 1) : "memory");
+            known_done = k + 1;
+            st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);   /* the host re-arms */
+            t_done = gtime();
+          }
+        }
+      }
+    } else {
+      /* ---- finish, ring modes: every CTA publishes its own completion
+       * word (the paper's per-SM from_GPU mailbox); the host takes the
+       * minimum over the cluster's words, so nothing between the last CTA's
+       * end and the host waits on another CTA.  A sum, histogram or batch
+       * needs one CTA to finish the descriptor's shared state first: each
+       * CTA arrives on the slot's counter before publishing, and the last
+       * arriver combines (the host's minimum includes its word, published
+       * after the combine).  Other ops arrive after publishing, off the
+       * host's path; their arrivals only pick the CTA that frees the slot. */
+      const bool comb = op == LK_OP_SUM_F32 || op == LK_OP_HIST_U8 || op == LK_OP_BATCH;
+      if (comb) {
+        if (tid == 0 && !s_err)
+          s_last = S == 1 || atom_add_acq_rel_gpu(&dc->arrive[slot].count, 1u) == (uint32_t)(S - 1);
+        __syncthreads();
+        if (s_last) {   /* CTA-uniform after the barrier */
+          if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
+          else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
+          __syncthreads();   /* the combine's writes before thread 0's fence */
+        }
+      }
+      if (tid == 0 && !s_err) {
+        /* every output write of this CTA (and of the combine, when this CTA
+         * ran it; the barrier above orders the other threads' writes) before
+         * the host-visible word */
+        fence_acq_rel_sys();
+        st_relaxed_sys(my_done, k + 1);
+        if (!comb) s_last = S == 1 || atom_add_acq_rel_gpu(&dc->arrive[slot].count, 1u) == (uint32_t)(S - 1);
+        if (s_last) {
+          /* every CTA has arrived: free the slot (the arrivals, acquire-
+           * release, order their reads of the relay slot and their partials
+           * before this release) */
+          if (S > 1) dc->arrive[slot].count = 0;
+          if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every CTA has left the claim loop */
+          st_release_gpu(&dc->slot_done[slot], k + 1);
           t_done = gtime();
         }
       }

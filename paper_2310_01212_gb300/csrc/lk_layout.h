@@ -7,14 +7,20 @@
  *                   64-byte line each, published with a lap tag in every word
  *                   (lk_wire below).  Table 1's single to_GPU integer becomes
  *                   the slot's `cmd` (THREAD_WORK + op, THREAD_EXIT).
- *   cword[c]        per-cluster from_GPU words: `done` (seq of the last
- *                   finished descriptor, monotone), `status` (Table 1 code),
- *                   each on its own 128-byte line.
+ *   rdone[..]       the from_GPU completion words: one per CTA, the seq of
+ *                   the last descriptor that CTA finished (monotone); a
+ *                   cluster's words are contiguous from rd_off[c], 16 to a
+ *                   128-byte line, and the cluster has finished seq once
+ *                   every one of its words reaches it.
+ *   cword[c]        per-cluster from_GPU words: `done` (one-deep mailbox
+ *                   mode: seq of the last finished descriptor), `status`
+ *                   (Table 1 code), each on its own 128-byte line.
  *   ctrl            abort word, heartbeat, boot / exit counters, first error.
  *   info[g]         (cluster, rank, smid) of CTA g, written at boot.
  * Device memory (cluster-internal relay, L2-resident):
- *   dcl[c]          relay ring (D slots), generation, device-side done,
- *                   per-rank finished counts, per-rank partial sums,
+ *   dcl[c]          relay ring (D slots), generation, per-slot completion
+ *                   words and arrival counters, per-rank finished counts
+ *                   (one-deep mailbox mode), per-rank partial sums,
  *                   histogram accumulators.
  *   log[g][cap]     execution-log records (lk_exec_rec) of CTA g.
  */
@@ -27,6 +33,7 @@
 #define LK_BCAST_DEPTH 8          /* descriptors a cluster may have in flight */
 #define LK_MAX_CTAS 1024          /* upper bound on CTAs per context          */
 #define LK_MAX_CLUSTERS 256
+#define LK_RDONE_ALIGN 16         /* completion words per 128-byte line        */
 
 /* A descriptor as the device uses it (decoded; also the relay-ring format). */
 typedef struct __attribute__((aligned(64))) {
@@ -123,14 +130,26 @@ typedef struct {
 } lk_cta_info;
 
 /* Per-cluster state in device memory.  `flag[r]` is the number of
- * descriptors rank r has finished (monotone); rank 0 gathers the flags and
- * completes each descriptor, so no counter is shared by all CTAs. */
+ * descriptors rank r has finished (monotone; one-deep mailbox mode, where
+ * rank 0 gathers the flags and completes each descriptor).  In the ring
+ * modes every CTA publishes its own completion word to the host instead;
+ * descriptor k (0-based) uses slot k mod D of the relay ring, the partials
+ * and the histogram accumulators, and its last CTA to arrive on
+ * arrive[k mod D] (the one that also combines a sum or histogram) resets
+ * the counter and release-stores slot_done[k mod D] = k + 1, which gates the
+ * slot's reuse by descriptor k + D. */
+typedef struct __attribute__((aligned(LK_LINE))) {
+  uint32_t count;
+  uint8_t pad[LK_LINE - 4];
+} lk_line_counter;
+
 typedef struct __attribute__((aligned(LK_LINE))) {
   uint64_t gen;                          /* LK_GEN_STOP once the master stopped         */
   uint8_t pad0[LK_LINE - 8];
-  uint64_t dev_done;                     /* descriptors finished (rank 0 writes)        */
-  uint8_t pad1[LK_LINE - 8];
-  uint64_t flag[LK_MAX_CTAS];            /* per-rank finished count                     */
+  uint64_t slot_done[LK_BCAST_DEPTH];    /* seq of the last finished descriptor of slot */
+  uint8_t pad1[LK_LINE - 8 * LK_BCAST_DEPTH];
+  lk_line_counter arrive[LK_BCAST_DEPTH]; /* CTAs that finished the slot's descriptor   */
+  uint64_t flag[LK_MAX_CTAS];            /* per-rank finished count (mailbox mode)      */
   lk_wire relay[LK_BCAST_DEPTH];         /* relay ring (lap-tagged like the host ring)  */
   uint32_t hist[LK_BCAST_DEPTH][256];    /* histogram accumulators, zero at rest        */
   float partial[LK_BCAST_DEPTH][LK_MAX_CTAS]; /* per-rank partial sums                  */
@@ -179,6 +198,8 @@ typedef struct __attribute__((aligned(LK_LINE))) {
 typedef struct {
   lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */
   lk_cword* cword;               /* [C] host-mapped                                     */
+  uint64_t* rdone;               /* host-mapped per-CTA completion words (rd_off[c] + r) */
+  int32_t* rd_off;               /* [C] device: first completion word of each cluster   */
   lk_mbox* mbox;                 /* [C] host-mapped (LK_KFLAG_MAILBOX), else NULL       */
   lk_ctrl* ctrl;                 /* host-mapped                                         */
   lk_cta_info* info;             /* [G] host-mapped                                     */

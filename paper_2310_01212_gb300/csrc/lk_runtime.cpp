@@ -69,6 +69,8 @@ struct lk_ctx {
   lk_wire* ring_h = nullptr;     /* host view of the ring (live mode) */
   uint32_t R_log2 = 10;
   lk_cword* cword_h = nullptr;
+  uint64_t* rdone_h = nullptr;   /* per-CTA completion words (ring modes) */
+  std::vector<int> rd_off;       /* first completion word of each cluster */
   lk_ctrl* ctrl_h = nullptr;
   lk_cta_info* info_h = nullptr;
 
@@ -162,10 +164,25 @@ static void mbox_observe(lk_ctx* ctx, int c) {
   st_rel(&ctx->mbox_h[c].to_gpu, (uint64_t)LK_CMD_NOP);
 }
 
-/* Finished descriptors of cluster c (FIFO: every seq <= the value). */
+/* Finished descriptors of cluster c (FIFO: every seq <= the value).  Ring
+ * modes: every CTA of the cluster publishes the seq of the last descriptor
+ * it finished, so the cluster has finished the minimum of its words.  The
+ * words are read with plain loads, all in flight together, and one acquire
+ * fence follows (acquire loads would each wait for the one before). */
 static uint64_t cl_done(lk_ctx* ctx, int c) {
-  if (ctx->mailbox) mbox_observe(ctx, c);
-  return ld_acq(&ctx->cword_h[c].done);
+  if (ctx->mailbox) {
+    mbox_observe(ctx, c);
+    return ld_acq(&ctx->cword_h[c].done);
+  }
+  const uint64_t* w = ctx->rdone_h + ctx->rd_off[c];
+  const int S = ctx->sizes[c];
+  uint64_t m = ld_rlx(&w[0]);
+  for (int r = 1; r < S; ++r) {
+    const uint64_t v = ld_rlx(&w[r]);
+    m = v < m ? v : m;
+  }
+  __atomic_thread_fence(__ATOMIC_ACQUIRE);
+  return m;
 }
 
 /* Mailbox post: only when the previous descriptor finished, was re-armed and
@@ -210,7 +227,7 @@ static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* 
   Tail& tl = ctx->tail[c];
   uint64_t t = tl.t.load(std::memory_order_relaxed);
   for (;;) {
-    uint64_t done = ld_acq(&ctx->cword_h[c].done);
+    uint64_t done = cl_done(ctx, c);
     if (t - done >= ctx->R) return LK_EAGAIN;   /* slot t mod R still holds descriptor t-R+1 */
     if (tl.t.compare_exchange_weak(t, t + 1, std::memory_order_acq_rel, std::memory_order_relaxed)) break;
   }
@@ -265,13 +282,21 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if ((p->flags & LK_INIT_DIRECT) && (p->flags & LK_INIT_MAILBOX)) return LK_EINVAL;
   ctx->mailbox = live && (p->flags & LK_INIT_MAILBOX);
 
-  /* host-mapped block: [ring (live only)] cword[C] ctrl info[G] [unit tables (live only)] */
+  /* host-mapped block: [ring (live only)] cword[C] rdone[..] ctrl info[G] [unit tables (live only)] */
   ctx->max_units = live ? (p->max_batch_units ? p->max_batch_units : 8192u) : 0u;
   if (ctx->max_units > (1u << 22)) return LK_EINVAL;
   size_t off_ring = 0;
   size_t ring_bytes = (size_t)ctx->C * R * sizeof(lk_wire);
   size_t off_cw = live ? align_up(ring_bytes, LK_LINE) : 0;
-  size_t off_ctrl = align_up(off_cw + ctx->C * sizeof(lk_cword), LK_LINE);
+  /* per-CTA completion words: each cluster's on lines of its own */
+  ctx->rd_off.assign(ctx->C, 0);
+  size_t rd_words = 0;
+  for (int c = 0; c < ctx->C; ++c) {
+    ctx->rd_off[c] = (int)rd_words;
+    rd_words += align_up((size_t)ctx->sizes[c], LK_RDONE_ALIGN);
+  }
+  size_t off_rd = align_up(off_cw + ctx->C * sizeof(lk_cword), LK_LINE);
+  size_t off_ctrl = align_up(off_rd + rd_words * sizeof(uint64_t), LK_LINE);
   size_t off_info = align_up(off_ctrl + sizeof(lk_ctrl), LK_LINE);
   size_t off_units = align_up(off_info + ctx->G * sizeof(lk_cta_info), LK_LINE);
   size_t units_bytes = (size_t)ctx->C * LK_BATCH_BUFFERS * ctx->max_units * sizeof(lk_unit);
@@ -283,6 +308,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   char* mh = (char*)ctx->mapped_h;
   char* md = (char*)ctx->mapped_d;
   ctx->cword_h = (lk_cword*)(mh + off_cw);
+  ctx->rdone_h = (uint64_t*)(mh + off_rd);
   ctx->ctrl_h = (lk_ctrl*)(mh + off_ctrl);
   ctx->info_h = (lk_cta_info*)(mh + off_info);
   if (ctx->max_units) {
@@ -294,11 +320,12 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
     for (int c = 0; c < ctx->C; ++c) ctx->mbox_h[c].to_gpu = LK_CMD_NOP;   /* idle */
   }
 
-  /* device block: [ring (finite only)] dcl[C] cl_start pin_smid boot_smid boot_count log_count log */
+  /* device block: [ring (finite only)] dcl[C] cl_start rd_off pin_smid boot_smid boot_count log_count log */
   size_t d_ring = 0;
   size_t d_dcl = live ? 0 : align_up(ring_bytes, LK_LINE);
   size_t d_start = align_up(d_dcl + ctx->C * sizeof(lk_dcluster), LK_LINE);
-  size_t d_pin = align_up(d_start + (ctx->C + 1) * sizeof(int32_t), LK_LINE);
+  size_t d_rdoff = align_up(d_start + (ctx->C + 1) * sizeof(int32_t), LK_LINE);
+  size_t d_pin = align_up(d_rdoff + ctx->C * sizeof(int32_t), LK_LINE);
   size_t d_bsm = align_up(d_pin + (p->smids ? ctx->total : 0) * sizeof(int32_t), LK_LINE);
   size_t d_bcnt = align_up(d_bsm + ctx->G * sizeof(int32_t), LK_LINE);
   size_t d_lcnt = align_up(d_bcnt + sizeof(uint32_t), LK_LINE);
@@ -313,6 +340,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   rc = lkb_zero_device(ctx->device, db, d_log);
   if (rc != LK_OK) return rc;
   rc = lkb_copy_h2d(ctx->device, db + d_start, ctx->cl_start.data(), (ctx->C + 1) * sizeof(int32_t));
+  if (rc == LK_OK) rc = lkb_copy_h2d(ctx->device, db + d_rdoff, ctx->rd_off.data(), ctx->C * sizeof(int32_t));
   if (rc == LK_OK && p->smids)
     rc = lkb_copy_h2d(ctx->device, db + d_pin, p->smids, ctx->total * sizeof(int32_t));
   if (rc != LK_OK) return rc;
@@ -321,6 +349,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   memset(&a, 0, sizeof a);
   a.ring = (lk_wire*)(live ? (void*)(md + off_ring) : (void*)(db + d_ring));
   a.cword = (lk_cword*)(md + off_cw);
+  a.rdone = (uint64_t*)(md + off_rd);
+  a.rd_off = (int32_t*)(db + d_rdoff);
   a.mbox = ctx->mailbox ? (lk_mbox*)(md + off_mbox) : nullptr;
   a.ctrl = (lk_ctrl*)(md + off_ctrl);
   a.info = (lk_cta_info*)(md + off_info);
@@ -679,7 +709,7 @@ int lk_status(lk_ctx* ctx, int cluster) {
   if (st == LK_ST_EXITED || st == LK_ST_ERROR || ctx->mailbox) return (int)st;
   const uint64_t tail = ctx->tail[cluster].t.load(std::memory_order_acquire);
   if (tail == 0) return LK_ST_INIT;
-  return ld_acq(&ctx->cword_h[cluster].done) >= tail ? LK_ST_FINISHED : LK_ST_WORKING;
+  return cl_done(ctx, cluster) >= tail ? LK_ST_FINISHED : LK_ST_WORKING;
 }
 
 int lk_device_error(lk_ctx* ctx) {
