@@ -292,8 +292,11 @@ def build_headline(d: dict, hbm: float) -> dict:
     gcmp = bat["graph_compared"]
     srv = d["serving"]
     sat = max(srv["rates"].values(), key=lambda e: e["throughput_gbs"])
-    sat_c = max(srv["coalesced"]["rates"].values(), key=lambda e: e["throughput_gbs"]) \
-        if srv["coalesced"]["rates"] else None
+    hd = srv["host_dispatcher"]["rates"]
+    sat_h = max(hd.values(), key=lambda e: e["throughput_gbs"]) if hd else None
+    hc = srv["host_dispatcher_coalesced"]["rates"]
+    sat_c = max(hc.values(), key=lambda e: e["throughput_gbs"]) if hc else None
+    low = srv["rates"][min(srv["rates"], key=int)]
     return {
         "lk_us_p50_p99_max": trio(d["latency_us"]),
         "launch_sync_us_p50_p99_max": trio(d["baseline_launch_sync_us"]),
@@ -319,8 +322,10 @@ def build_headline(d: dict, hbm: float) -> dict:
                       "cap_2tbs_inflation_p999": round(iso["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2)},
         "batching_gbs": {"lk_prefix": round(bat["lk_gbs"]), "prefix_items": bat["items"],
                          "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
-        "serving_saturation_gbs": {"chunks": round(sat["throughput_gbs"]),
-                                   "coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
+        "serving_saturation_gbs": {"device_queue": round(sat["throughput_gbs"]),
+                                   "host_dispatcher": round(sat_h["throughput_gbs"]) if sat_h else None,
+                                   "host_coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
+        "serving_lowest_rate_us_p50_p99": [rnd1(low["latency_us"]["p50"]), rnd1(low["latency_us"]["p99"])],
         "parity": {"sampled_items_bad": d["parity"]["mismatches"],
                    "exec_log_violations": d["parity"]["exec_log"]["violations"],
                    "body_checks_bad": sum(v["parity"]["mismatches"] for v in bw.values()),
@@ -349,6 +354,18 @@ def exec_log_phases(log) -> dict:
                     ("last_end_to_done", done - end), ("pick_to_done", done - pick)):
         v = v[ok] / 1000.0
         out[name + "_us"] = {"p50": pct(v, 0.5), "p99": pct(v, 0.99)}
+    # per CTA: median of its own start - pick (who is late to see the relay)
+    rk = log["cluster"].astype(np.int64) << 20 | log["rank"].astype(np.int64)
+    per = {}
+    d = (log["t_start_ns"].astype(np.int64) - log["t_pick_ns"].astype(np.int64)) / 1000.0
+    for key in np.unique(rk):
+        m = rk == key
+        per[int(key)] = (float(np.median(d[m])), int(log["smid"][m][0]), int(key & 0xfffff))
+    meds = np.array([v[0] for v in per.values()])
+    worst = sorted(per.values(), reverse=True)[:5]
+    out["per_cta_pick_to_start_us"] = {"min": float(meds.min()), "p50": float(np.median(meds)),
+                                       "max": float(meds.max()),
+                                       "worst5_us_smid_rank": [[round(a, 3), b, c] for a, b, c in worst]}
     return out
 
 
@@ -637,8 +654,10 @@ def main():
                     exec_log_cap=nop.size // len(sizes) + 64) as ctx:
         rc, r1 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True, pin_cpu_base=pin)
         nop_phases = exec_log_phases(lk.lk_exec_log(ctx)[0])
-    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT) as ctx:
+    with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_DIRECT,
+                    exec_log_cap=nop.size // len(sizes) + 64) as ctx:
         rc, r3 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True, pin_cpu_base=pin)
+        nop_phases_direct = exec_log_phases(lk.lk_exec_log(ctx)[0])
     with lk.lk_init(sizes, device=dev, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_MAILBOX) as ctx:
         rc, r4 = lk.lk_run_trace(ctx, nop, n_threads=1, closed_loop=True, pin_cpu_base=pin)
     rc2, r2 = lk.lk_baseline_run_trace(nop, sizes, threads=cfg["threads"], n_threads=1, device=dev, pin_cpu_base=pin)
@@ -796,39 +815,55 @@ def main():
                           f"stream, batch b+1 posted while batch b runs"}
 
     # ---- serving: continuous admission under open-loop arrivals, per rate ----------
+    # the device-resident queue at every rate (the clusters' CTAs claim work
+    # units themselves); the host dispatcher (chunks posted per cluster) and
+    # its coalesced variant at the top rates for comparison; unit sizes swept
+    # at the top rate
     scfg = wl.SERVING
     arena = torch.empty(scfg["arena_bytes"], dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     serving = {"budget_bytes": scfg["budget_bytes"], "arena_bytes": scfg["arena_bytes"],
-               "chunk_bytes": scfg["chunk_bytes"], "window": scfg["window"], "producers": scfg["producers"],
-               "seconds_per_rate": args.serve_seconds, "partition": "4 clusters x 37 SMs", "rates": {}}
-    # the same rates with small requests coalesced many to a batch post
-    # (throughput mode: one dispatch serves many small requests)
-    serving["coalesced"] = {"coalesce_bytes": scfg["coalesce_bytes"], "coalesce_part_bytes": scfg["coalesce_part_bytes"],
-                            "rates": {}}
+               "part_bytes": scfg["part_bytes"], "window_units_per_cta": scfg["queue_window"],
+               "producers": scfg["producers"], "seconds_per_rate": args.serve_seconds,
+               "partition": "4 clusters x 37 SMs", "rates": {},
+               "host_dispatcher": {"chunk_bytes": scfg["chunk_bytes"], "window": scfg["window"], "rates": {}},
+               "host_dispatcher_coalesced": {"coalesce_bytes": scfg["coalesce_bytes"],
+                                             "coalesce_part_bytes": scfg["coalesce_part_bytes"], "rates": {}},
+               "part_bytes_sweep_top_rate": {}}
+    top = scfg["rates"][-3:]
+    runs = [("rates", r, dict(mode=lk.LK_SERVE_QUEUE, part_bytes=scfg["part_bytes"], window=scfg["queue_window"]))
+            for r in scfg["rates"]]
+    runs += [("host_dispatcher", r, dict(mode=lk.LK_SERVE_CHUNKS, chunk_bytes=scfg["chunk_bytes"],
+                                         window=scfg["window"])) for r in top]
+    runs += [("host_dispatcher_coalesced", r, dict(mode=lk.LK_SERVE_CHUNKS, chunk_bytes=scfg["chunk_bytes"],
+                                                   window=scfg["window"], coalesce_bytes=scfg["coalesce_bytes"],
+                                                   coalesce_part_bytes=scfg["coalesce_part_bytes"]))
+             for r in top[-1:]]
+    runs += [("part_bytes_sweep_top_rate", scfg["rates"][-1], dict(mode=lk.LK_SERVE_QUEUE, part_bytes=pb,
+                                                                   window=scfg["queue_window"]))
+             for pb in (1 << 20, 4 << 20, 8 << 20)]
     with lk.lk_init(scfg["sizes"], device=dev, threads_per_cta=scfg["threads"], idle_lease_ns=30_000_000_000) as ctx:
-        for mode, rates, co in (("rates", scfg["rates"], 0), ("coalesced", scfg["rates"][-3:], scfg["coalesce_bytes"])):
-            for rate in rates:
-                reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
-                rc, res = lk.lk_serve(ctx, reqs, n_producers=scfg["producers"], budget_bytes=scfg["budget_bytes"],
-                                      arena=arena, arena_bytes=scfg["arena_bytes"], window=scfg["window"],
-                                      chunk_bytes=scfg["chunk_bytes"], timeout_ns=300_000_000_000,
-                                      coalesce_bytes=co, coalesce_part_bytes=scfg["coalesce_part_bytes"])
-                if rc != lk.LK_OK:
-                    raise RuntimeError(f"serving at {rate}/s failed: {lk.lk_strerror(rc)}")
-                lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
-                wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
-                span = float(res["t_complete_ns"].max()) / 1e9
-                entry = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
-                         "admission_wait_us": lat_summary(wait_s),
-                         "throughput_req_per_s": reqs.size / span,
-                         "throughput_gbs": float(inb.sum()) / span / 1e9,
-                         "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
-                         "chunks": int(res["chunks"].sum())}
-                if mode == "rates":
-                    serving["rates"][str(rate)] = entry
-                else:
-                    serving["coalesced"]["rates"][str(rate)] = entry
+        for where, rate, kw in runs:
+            reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
+            rc, res = lk.lk_serve(ctx, reqs, n_producers=scfg["producers"], budget_bytes=scfg["budget_bytes"],
+                                  arena=arena, arena_bytes=scfg["arena_bytes"], timeout_ns=300_000_000_000, **kw)
+            if rc != lk.LK_OK:
+                raise RuntimeError(f"serving ({where}) at {rate}/s failed: {lk.lk_strerror(rc)}")
+            lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
+            wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
+            span = float(res["t_complete_ns"].max()) / 1e9
+            entry = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
+                     "admission_wait_us": lat_summary(wait_s),
+                     "throughput_req_per_s": reqs.size / span,
+                     "throughput_gbs": float(inb.sum()) / span / 1e9,
+                     "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
+                     "units_or_chunks": int(res["chunks"].sum())}
+            if where == "rates":
+                serving["rates"][str(rate)] = entry
+            elif where == "part_bytes_sweep_top_rate":
+                serving[where][str(kw["part_bytes"])] = entry
+            else:
+                serving[where]["rates"][str(rate)] = entry
     del arena
 
     # ---- isolation: critical 16-SM cluster vs best-effort 132-SM cluster -----------
@@ -978,7 +1013,7 @@ def main():
         "config_small": small,
         "dispatch_nop_us": {"lk": lat_summary(nop_lk), "lk_direct": lat_summary(nop_direct),
                             "lk_mailbox": lat_summary(nop_mbox), "launch_sync": lat_summary(nop_base),
-                            "lk_device_phases": nop_phases},
+                            "lk_device_phases": nop_phases, "lk_direct_device_phases": nop_phases_direct},
         "paper_mailbox_vs_ring": mbox,
         "pingpong_floor_us": lat_summary(rtt),
         "throughput_items_per_s": items_all / wall_all,

@@ -93,6 +93,8 @@ extern "C" {
                            /* of the CTA's final values                                             */
 #define LK_OP_COUNT      9
 #define LK_OP_BATCH      9 /* a batch posted by lk_submit_batch (one descriptor, many items) */
+#define LK_OP_SERVE     10 /* lk_serve's device queue: the cluster's CTAs claim work units until */
+                           /* the queue closes (posted by lk_serve, LK_SERVE_QUEUE)             */
 
 /* ---- device-side error reasons (lk_device_error) ---------------------- */
 #define LK_DERR_NONE     0
@@ -140,6 +142,11 @@ typedef struct {
                                /* 2 -> two, each with half the shared memory (the      */
                                /* "multiple persistent threads" model Sec. II.C leaves  */
                                /* for later); 2 needs threads_per_cta <= 256            */
+  uint32_t serve_units;        /* entries of lk_serve's device queue (LK_SERVE_QUEUE):  */
+                               /* work units published and not yet read, and requests  */
+                               /* completed and not yet retired; power of two in       */
+                               /* [256, 2^22]; 0 -> 65536 (72 bytes of pinned host     */
+                               /* memory each)                                         */
 } lk_init_params;
 
 /* lk_init_params.flags: how descriptors reach a cluster's CTAs.
@@ -288,12 +295,27 @@ int lk_baseline_graph(int device, const lk_batch_item* items, uint32_t count, in
 /* ---- serving: continuous admission of requests ------------------------- */
 /* Not in the paper.  Requests arrive over time from several host producer
  * threads; one dispatcher admits them in arrival order while the bytes they
- * hold (inputs, outputs, scratch) fit in a device-memory budget, splits each
- * into chunks of at most chunk_bytes of input, and lets every cluster pull
- * the next chunks as its in-flight window frees up, so requests that arrive
- * while others run are interleaved with them.  A sum or histogram split into
- * several chunks is finished by one LK_OP_COMBINE_* descriptor; results do
- * not depend on what else runs (all clusters must have the same size). */
+ * hold (inputs, outputs, scratch) fit in a device-memory budget.  Two ways to
+ * run what is admitted (lk_serve_params.mode):
+ *   LK_SERVE_QUEUE (device-resident queue): each admitted request is split
+ *     into work units of at most part_bytes of input, which the host
+ *     publishes into a ring in pinned host-mapped memory, one unit of each
+ *     admitted request in turn (so a request that arrives while large ones
+ *     run is interleaved with them), at most window x (CTAs) units ahead of
+ *     the completed requests.  One LK_OP_SERVE descriptor per cluster turns
+ *     every CTA of every cluster into a worker: it claims the next unit index
+ *     from one device counter, runs that part, and the request's last part
+ *     combines it (sums in part order, histograms) and appends the request
+ *     to a completion ring the host reads.  The host only admits, publishes
+ *     and retires; no host round trip is spent per unit.
+ *   LK_SERVE_CHUNKS (host dispatcher): each request is split into chunks of
+ *     at most chunk_bytes of input, one descriptor each, which the host posts
+ *     to every cluster as its in-flight window (window chunks) frees up; a
+ *     split sum or histogram ends with one LK_OP_COMBINE_* descriptor.
+ * Either way results do not depend on what else runs (all clusters must have
+ * the same size). */
+#define LK_SERVE_CHUNKS 0
+#define LK_SERVE_QUEUE  1
 typedef struct {
   uint64_t t_arrival_ns;  /* arrival time relative to the run's start         */
   uint32_t op;            /* LK_OP_ADD_I32 .. LK_OP_COPY_I32                  */
@@ -314,13 +336,17 @@ typedef struct {
 
 typedef struct {
   int n_producers;            /* >= 1; request.producer < n_producers             */
-  int window;                 /* chunks each cluster may hold at once; 0 -> 2     */
-  uint64_t chunk_bytes;       /* input bytes per chunk; 0 -> 16 MiB              */
+  int window;                 /* CHUNKS: chunks each cluster may hold at once;     */
+                              /* QUEUE: units published ahead of the completed     */
+                              /* requests, per serving CTA; 0 -> 2                 */
+  uint64_t chunk_bytes;       /* CHUNKS: input bytes per chunk; 0 -> 16 MiB        */
   uint64_t budget_bytes;      /* admission budget: bytes held by admitted,         */
                               /* unfinished requests                              */
   void* arena;                /* device memory (256-byte aligned) for outputs of    */
                               /* requests with out == NULL and for the per-chunk   */
-                              /* partials of split sums and histograms             */
+                              /* partials of split sums and histograms; QUEUE: its */
+                              /* first lk_serve_queue_state_bytes(max_inflight)    */
+                              /* bytes hold the queue's device state               */
   uint64_t arena_bytes;
   uint64_t timeout_ns;        /* whole run; 0 -> 120 s                            */
   uint64_t coalesce_bytes;    /* requests of at most this many input bytes run as  */
@@ -330,15 +356,28 @@ typedef struct {
   uint32_t coalesce_max;      /* requests per coalesced post; 0 -> 256, <= 256     */
   uint32_t coalesce_part_bytes; /* input bytes per work unit of a coalesced item   */
                               /* (its CTAs: at most 8); 0 -> 256 KiB              */
+  uint32_t mode;              /* LK_SERVE_CHUNKS or LK_SERVE_QUEUE                  */
+  uint32_t max_inflight;      /* QUEUE: admitted, unfinished requests at most;     */
+                              /* 0 -> 4096                                        */
+  uint64_t part_bytes;        /* QUEUE: input bytes per work unit (a request has   */
+                              /* at most 1024 units); 0 -> 2 MiB; >= 64 KiB         */
 } lk_serve_params;
+
+/* Device bytes the queue's state takes at the start of the arena
+ * (LK_SERVE_QUEUE) for `max_inflight` request slots (0 -> 4096). */
+uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight);
 
 /* Run the requests through the context's clusters (all of one size) and
  * fill res[i] for each.  A request runs the same way whatever else is
- * served, so its result does not depend on the mix: as chunks of at most
- * chunk_bytes (one descriptor each, then one combine descriptor for split
- * sums and histograms), or, when it is at most coalesce_bytes, as one item
- * of a batch post split by coalesce_part_bytes.  Outputs taken from the arena are released when the
- * request completes (read them before the next call reuses the arena).
+ * served, so its result does not depend on the mix: QUEUE, as
+ * ceil(input bytes / part_bytes) units (res.chunks = units); CHUNKS, as
+ * chunks of at most chunk_bytes (one descriptor each, then one combine
+ * descriptor for split sums and histograms), or, when it is at most
+ * coalesce_bytes, as one item of a batch post split by coalesce_part_bytes
+ * (coalescing applies to CHUNKS only).  Outputs taken from the arena are
+ * released when the request completes (read them before the next call
+ * reuses the arena).  In QUEUE mode the context must have been created live
+ * (lk_init) and nothing else may be posted to it during the call.
  * Returns LK_OK if every request finished, LK_EINVAL, LK_ENOMEM (a request
  * needs more arena or budget than exists), or the first error. */
 int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,

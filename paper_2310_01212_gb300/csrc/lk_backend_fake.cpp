@@ -140,8 +140,43 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
     }
     return 0;
   };
+  /* LK_OP_SERVE: claim units from the queue's device counter until it
+   * closes, as every CTA of the cluster does on the GPU (here one thread
+   * claims for the cluster); no body runs, the last part of a request
+   * appends it to the completion ring */
+  auto serve = [&](lk_qstate* qs) {
+    for (;;) {
+      const uint64_t u = __atomic_fetch_add(&qs->head, 1ull, __ATOMIC_ACQ_REL);
+      lk_qunit* e = qs->units + (u & qs->qmask);
+      bool closed = false;
+      int w = wait_for([&] {
+        if (ld_acq(&e->seq) == u + 1) return true;
+        const uint64_t cl = ld_acq(qs->close);
+        if ((cl >> 63) && u >= (cl & ~(1ull << 63))) {
+          closed = true;
+          return true;
+        }
+        return false;
+      });
+      if (w) return w;
+      if (closed) return 0;
+      const uint64_t meta = __atomic_load_n(&e->meta, __ATOMIC_RELAXED);
+      st_rel(&e->ack, u + 1);
+      const uint32_t parts = (uint32_t)((meta >> 16) & 0xffffu), rslot = (uint32_t)(meta >> 32);
+      if (rslot >= qs->nslots || parts < 1) return (int)LK_DERR_BADDESC;
+      if (stall) std::this_thread::sleep_for(std::chrono::nanoseconds(stall));
+      lk_qslot* sl = qs->slots + rslot;
+      const bool last = parts == 1 || __atomic_fetch_add(&sl->done, 1u, __ATOMIC_ACQ_REL) == parts - 1;
+      if (last) {
+        if (parts > 1) __atomic_store_n(&sl->done, 0u, __ATOMIC_RELAXED);
+        const uint64_t pos = __atomic_fetch_add(&qs->cq_tail, 1ull, __ATOMIC_ACQ_REL);
+        st_rel(&qs->cq[pos & qs->qmask], ((pos >> qs->qlog2) + 1) << 32 | rslot);
+      }
+    }
+  };
   for (uint64_t k = 0;; ++k) {
     uint32_t cmd = 0;
+    uint64_t in0 = 0;
     if (mailbox) {
       /* the one-deep mailbox: acknowledge the host's re-arm, then take work */
       lk_mbox* mb = a.mbox + c;
@@ -172,9 +207,14 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       lk_slot dsc;
       lk_wire_decode(w, k + 1, &dsc);
       cmd = dsc.cmd;
+      in0 = dsc.in0;
     }
     if (cmd == LK_CMD_EXIT) break;
     if (k >= fail_after) { err = fail_code; break; }
+    if (cmd == LK_CMD_WORK + LK_OP_SERVE) {
+      err = serve(reinterpret_cast<lk_qstate*>(in0));
+      if (err) break;
+    }
     const uint64_t t_pick = now_ns();
     st_rel(&a.cword[c].status, (uint64_t)LK_ST_WORKING);
     if (stall) std::this_thread::sleep_for(std::chrono::nanoseconds(stall));

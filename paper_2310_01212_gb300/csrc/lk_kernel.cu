@@ -66,10 +66,16 @@ __device__ __forceinline__ bool tags_match(const uint64_t* w, uint64_t tag) {
   return (w[0] >> LK_TAG_SHIFT) == tag && (w[1] >> LK_TAG_SHIFT) == tag && (w[2] >> LK_TAG_SHIFT) == tag &&
          (w[3] >> LK_TAG_SHIFT) == tag && (w[4] >> LK_TAG_SHIFT) == tag && (w[5] >> LK_TAG_SHIFT) == tag;
 }
+/* One probe of a ring slot: three vector loads in flight together, the last
+ * an acquire.  When every tag is current, that acquire load has read a word
+ * the host stored after its release fence, so it synchronises with the
+ * host's post; the fence the caller issues next is then nearly free
+ * (measured on GB300: a system-scope fence after relaxed system-scope loads
+ * cost 0.48 us of a host round trip, after an acquire load nothing). */
 __device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
   ld_relaxed_sys_v2(&s->w[0], w[0], w[1]);
   ld_relaxed_sys_v2(&s->w[2], w[2], w[3]);
-  ld_relaxed_sys_v2(&s->w[4], w[4], w[5]);
+  asm volatile("ld.acquire.sys.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&s->w[4]) : "memory");
 }
 
 /* Wait until ring slot `s` holds ticket k (every tagged word carries lap tag
@@ -88,6 +94,7 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, 
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
+  uint64_t abort_v = 0, hb_v = hb;   /* loaded at the previous check, used at the next */
   uint64_t w[6];
   for (uint32_t it = 1;; ++it) {
     uint64_t pv;
@@ -96,14 +103,15 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, 
     *pre_val = pv;
     if (tags_match(w, tag)) break;
     if ((it & 63) == 0) {
-      if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
+      if (abort_v) return LK_DERR_ABORT;
       const uint64_t now = gtime();
       if (now - t_last > a.lease_ns) {
-        const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
-        if (h == hb) return LK_DERR_LEASE;
-        hb = h;
+        if (hb_v == hb) return LK_DERR_LEASE;
+        hb = hb_v;
         t_last = now;
       }
+      abort_v = ld_relaxed_sys(&a.ctrl->abort);
+      hb_v = ld_relaxed_sys(&a.ctrl->heartbeat);
     }
     bo.pause();
   }
@@ -129,7 +137,7 @@ __device__ __noinline__ int wait_to_gpu(const lk_kargs& a, const uint64_t* p, bo
   uint64_t t_last = gtime();
   uint64_t v;
   for (uint32_t it = 1;; ++it) {
-    v = ld_relaxed_sys(p);
+    v = ld_acquire_sys(p);   /* an acquire load: the fence below is then nearly free */
     if (want_nop ? v == LK_CMD_NOP : (v == LK_CMD_EXIT || v >= LK_CMD_WORK)) break;
     if ((it & 63) == 0) {
       if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
@@ -194,23 +202,22 @@ __device__ __forceinline__ void relay_publish(lk_wire* rs, uint64_t k, const lk_
   asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[6]), "l"(tag | (d.t_pick & LK_LOW48)) : "memory");
 }
 
+/* One probe of a relay slot: four vector loads, the last an acquire (when
+ * every tag is current it read a word the master stored after its fence,
+ * so it synchronises with the master; no separate fence follows). */
 __device__ __forceinline__ void relay_probe(const lk_wire* rs, uint64_t* w) {
   asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(&rs->w[0]) : "memory");
   asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[2]), "=l"(w[3]) : "l"(&rs->w[2]) : "memory");
   asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
-  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
-}
-__device__ __forceinline__ bool relay_current(const uint64_t* w, uint64_t tag) {
-  return tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag;
+  asm volatile("ld.acquire.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
 }
 
-/* A relayed member waits for descriptor k in relay slot rs.  Two probes are
- * kept in flight, half a round trip apart (the first probe's round trip sets
- * the stagger, at most 1 us): a probe can only see the slot as it was when it
- * reached L2, so one probe at a time samples the slot once per round trip,
- * and two staggered probes twice.  Members read L2, not host memory, so the
- * extra reads delay no host store.  Returns 0, -1 (the master stopped) or an
- * LK_DERR_* reason. */
+/* A relayed member waits for descriptor k in relay slot rs (L2).  One probe
+ * at a time (measured: a second staggered probe in flight did not lower the
+ * broadcast latency to 36 members, about 0.6 us).  The periodic checks
+ * (abort word, master stop, lease) read their words without waiting on
+ * them: each check uses the values loaded at the previous one.  Returns 0,
+ * -1 (the master stopped) or an LK_DERR_* reason. */
 __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster* dc, const lk_wire* rs, uint64_t k,
                                             lk_slot& out) {
   const uint64_t tag = (k / LK_BCAST_DEPTH + 1) & 0xffffull;
@@ -218,43 +225,27 @@ __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
   const uint64_t limit = a.lease_ns + 1000000000ull;
-  uint64_t wa[8], wb[8];
-  bool in_b = false;   /* the current copy arrived in wb (element-wise select keeps both in registers) */
-  relay_probe(rs, wa);
-  if (!relay_current(wa, tag)) {
-    uint64_t rtt = gtime() - t_last;
-    rtt = rtt > 2000u ? 2000u : rtt;
-    relay_probe(rs, wa);
-    const uint64_t t1 = gtime();
-    while (gtime() - t1 < rtt / 2) {
-    }
-    relay_probe(rs, wb);
-    for (uint32_t it = 1;; ++it) {
-      if (relay_current(wa, tag)) break;
-      relay_probe(rs, wa);
-      if (relay_current(wb, tag)) {
-        in_b = true;
-        break;
-      }
-      relay_probe(rs, wb);
-      if ((it & 127) == 0) {
-        if (ld_relaxed_sys(&a.ctrl->abort)) return LK_DERR_ABORT;
-        if (ld_acquire_gpu(&dc->gen) == LK_GEN_STOP) return -1;
-        const uint64_t now = gtime();
-        if (now - t_last > limit) {
-          const uint64_t h = ld_relaxed_sys(&a.ctrl->heartbeat);
-          if (h == hb) return LK_DERR_STALL;
-          hb = h;
-          t_last = now;
-        }
-      }
-      bo.pause();
-    }
-  }
-  fence_acq_rel_gpu();
+  uint64_t abort_v = 0, gen_v = 0, hb_v = hb;
   uint64_t w[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) w[i] = in_b ? wb[i] : wa[i];
+  for (uint32_t it = 1;; ++it) {
+    relay_probe(rs, w);
+    if (tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag) break;
+    if ((it & 127) == 0) {
+      /* act on the words loaded one check ago, then load them again */
+      if (abort_v) return LK_DERR_ABORT;
+      if (gen_v == LK_GEN_STOP) return -1;
+      const uint64_t now = gtime();
+      if (now - t_last > limit) {
+        if (hb_v == hb) return LK_DERR_STALL;
+        hb = hb_v;
+        t_last = now;
+      }
+      abort_v = ld_relaxed_sys(&a.ctrl->abort);
+      asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(gen_v) : "l"(&dc->gen) : "memory");
+      hb_v = ld_relaxed_sys(&a.ctrl->heartbeat);
+    }
+    bo.pause();
+  }
   lk_wire_decode(w, k + 1, &out);
   /* the master's pickup time: its low 48 bits under this reader's high bits */
   const uint64_t now = gtime();
@@ -493,6 +484,143 @@ __device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, in
   return 0;
 }
 
+/* Serving queue: thread 0 waits until unit u of the ring is published
+ * (its seq word reads u + 1), or the host closed the queue below u.  The
+ * entry is this CTA's alone (units are claimed once), so its probe delays
+ * no other reader.  The entry's fields follow an acquire fence; the ack
+ * tells the host the entry may be rewritten.  Returns 0 (w[0..4] = in0,
+ * in1, out, n_op, meta), 1 (closed: no unit u) or an LK_DERR_* reason. */
+__device__ __noinline__ int serve_take(const lk_kargs& a, const lk_qstate* qs, lk_qunit* e, uint64_t u,
+                                       const uint64_t* close, uint64_t* w) {
+  Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
+  uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
+  uint64_t t_last = gtime();
+  uint64_t close_v = 0, abort_v = 0, hb_v = hb;   /* loaded at one check, used at the next */
+  for (uint32_t it = 1;; ++it) {
+    uint64_t sq;
+    asm volatile("ld.acquire.sys.u64 %0, [%1];" : "=l"(sq) : "l"(&e->seq) : "memory");
+    if (sq == u + 1) break;
+    if ((it & 15) == 0) {
+      if ((close_v >> 63) && u >= (close_v & ~(1ull << 63))) return 1;
+      close_v = ld_relaxed_sys(close);
+    }
+    if ((it & 63) == 0) {
+      if (abort_v) return LK_DERR_ABORT;
+      const uint64_t now = gtime();
+      if (now - t_last > a.lease_ns) {
+        if (hb_v == hb) return LK_DERR_LEASE;
+        hb = hb_v;
+        t_last = now;
+      }
+      abort_v = ld_relaxed_sys(&a.ctrl->abort);
+      hb_v = ld_relaxed_sys(&a.ctrl->heartbeat);
+    }
+    bo.pause();
+  }
+  fence_acq_rel_sys();   /* nearly free after the acquire load (see probe()) */
+  ld_relaxed_sys_v2(&e->in0, w[0], w[1]);
+  ld_relaxed_sys_v2(&e->out, w[2], w[3]);
+  uint64_t ack;
+  ld_relaxed_sys_v2(&e->meta, w[4], ack);
+  st_relaxed_sys(&e->ack, u + 1);
+  return 0;
+}
+
+/* LK_OP_SERVE (lk_serve's device queue): the CTAs of every serving cluster
+ * claim work units from one device counter until the queue closes.  A unit
+ * is one part of one admitted request, run by this CTA with the body's
+ * (part, parts) split, so a result depends only on the request and the
+ * unit size.  Sum parts leave their partial in the request's slot and
+ * histogram parts add into its bins; the last part to finish (an
+ * acquire-release counter) writes the result (sums: binary64 in part order)
+ * and returns the slot to zero; then, after a system-scope fence, the
+ * request's slot id goes to the completion ring.  Returns an LK_DERR_* code
+ * or 0. */
+template <int MAXT, int P>
+__device__ __forceinline__ int run_serve(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
+                                         uint64_t* bars, uint32_t& phase, float* red) {
+  __shared__ uint64_t s_w[5];
+  __shared__ int s_take;
+  __shared__ float s_part;
+  __shared__ int s_lastp;
+  lk_qstate* qs = reinterpret_cast<lk_qstate*>(d.in0);
+  lk_qunit* units = reinterpret_cast<lk_qunit*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->units)));
+  uint64_t* cq = reinterpret_cast<uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->cq)));
+  const uint64_t* close = reinterpret_cast<const uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->close)));
+  lk_qslot* slots = reinterpret_cast<lk_qslot*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->slots)));
+  const uint64_t qmask = __ldcg(reinterpret_cast<const unsigned long long*>(&qs->qmask));
+  const uint32_t qlog2 = __ldcg(&qs->qlog2);
+  const uint32_t nslots = __ldcg(&qs->nslots);
+  uint32_t* my_hist = a.cta_hist + (size_t)(a.cl_start[c] + r) * 256u;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long u = atomicAdd(&qs->head, 1ull);
+      uint64_t w[5];
+      s_take = serve_take(a, qs, units + (u & qmask), u, close, w);
+      for (int i = 0; i < 5; ++i) s_w[i] = w[i];
+    }
+    __syncthreads();
+    const int take = s_take;   /* CTA-uniform */
+    if (take) return take == 1 ? 0 : take;
+    const uint32_t op = (uint32_t)(s_w[3] >> 56);
+    const uint32_t part = (uint32_t)(s_w[4] & 0xffffu);
+    const uint32_t parts = (uint32_t)((s_w[4] >> 16) & 0xffffu);
+    const uint32_t rslot = (uint32_t)(s_w[4] >> 32);
+    lk_slot it;
+    it.seq = d.seq;
+    it.cmd = LK_CMD_WORK + op;
+    it.flags = 0;
+    it.n = s_w[3] & LK_LOW48;
+    it.in0 = s_w[0];
+    it.in1 = s_w[1];
+    it.out = s_w[2];
+    it.aux = 0;
+    it.t_pick = 0;
+    bool ok = true;
+    if (rslot >= nslots || parts < 1 || parts > LK_SERVE_MAX_PARTS || part >= parts) return LK_DERR_BADDESC;
+    lk_qslot* sl = slots + rslot;
+    const Pace deadline{gtime() + 2000000000ull, 0};
+    if (op == LK_OP_SUM_F32) {
+      float* pout = parts > 1 ? &sl->partial[part] : &s_part;
+      ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
+    } else if (op == LK_OP_HIST_U8) {
+      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, parts > 1 ? sl->bins : my_hist);
+    } else {
+      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, 0,
+                             (a.flags & LK_KFLAG_GEMM_FFMA) == 0) == 0;
+    }
+    __syncthreads();
+    /* the last part of the request (a single part always is) finishes it */
+    if (threadIdx.x == 0) {
+      s_lastp = 1;
+      if (parts > 1) {
+        __threadfence();
+        s_lastp = atomicAdd(&sl->done, 1u) == parts - 1;
+        if (s_lastp) __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_lastp) {
+      if (op == LK_OP_SUM_F32) {
+        if (parts > 1) combine_sum(it, sl->partial, (int)parts);
+        else if (threadIdx.x == 0) *reinterpret_cast<float*>(it.out) = s_part;
+      } else if (op == LK_OP_HIST_U8) {
+        combine_hist(it, parts > 1 ? sl->bins : my_hist);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (parts > 1) sl->done = 0;
+        /* every output write of the request before its completion entry */
+        fence_acq_rel_sys();
+        const unsigned long long pos = atomicAdd(&qs->cq_tail, 1ull);
+        st_relaxed_sys(cq + (pos & qmask), (((uint64_t)pos >> qlog2) + 1) << 32 | rslot);
+      }
+    }
+    __syncthreads();   /* s_w / s_take are rewritten by the next claim */
+    if (!ok) return LK_DERR_STAGING;
+  }
+}
+
 template <int MAXT, int P>
 __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -674,10 +802,11 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = op == LK_OP_BATCH ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
-                                       : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r],
-                                                           dc->hist[slot], cta_rate(d.aux, S),
-                                                           (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
+    const int berr = op == LK_OP_BATCH   ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
+                     : op == LK_OP_SERVE ? run_serve<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
+                                         : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red,
+                                                             &dc->partial[slot][r], dc->hist[slot], cta_rate(d.aux, S),
+                                                             (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 

@@ -189,6 +189,48 @@ typedef struct __attribute__((aligned(LK_LINE))) {
   lk_hist_state hists[LK_BATCH_SPLIT_HISTS];
 } lk_bcluster;
 
+/* ---- the serving queue (lk_serve, LK_SERVE_QUEUE) ------------------------
+ * The host publishes work units (parts of admitted requests) into a ring in
+ * pinned host-mapped memory; every CTA of the serving clusters claims the
+ * next unit index from one device counter, waits for that entry to be
+ * published, runs the part and acknowledges the entry.  The last part of a
+ * request combines it (sums in part order, histograms) and appends the
+ * request's slot to a completion ring in host-mapped memory.  The host only
+ * admits, publishes and retires. */
+typedef struct __attribute__((aligned(64))) {
+  uint64_t in0, in1, out;
+  uint64_t n_op;     /* op << 56 | n (n < 2^48)                                   */
+  uint64_t meta;     /* part (bits 0-15) | parts (16-31) | request slot (32-63)    */
+  uint64_t ack;      /* device: u + 1 once the claimer has read the entry          */
+  uint64_t pad;
+  uint64_t seq;      /* host: u + 1 once unit u's fields are written (stored last, */
+                     /* after a release fence)                                     */
+} lk_qunit;          /* 64 bytes */
+
+#define LK_SERVE_MAX_PARTS 1024   /* work units of one request           */
+
+typedef struct __attribute__((aligned(LK_LINE))) {
+  uint32_t done;                  /* parts finished (the last one resets it)  */
+  uint8_t pad[LK_LINE - 4];
+  uint32_t bins[256];             /* histogram accumulator, zero at rest      */
+  float partial[LK_SERVE_MAX_PARTS]; /* per-part sums                        */
+} lk_qslot;
+
+typedef struct __attribute__((aligned(LK_LINE))) {
+  unsigned long long head;        /* next unit to claim (every serving CTA)   */
+  uint8_t pad0[LK_LINE - 8];
+  unsigned long long cq_tail;     /* completions appended                     */
+  uint8_t pad1[LK_LINE - 8];
+  lk_qunit* units;                /* host-mapped unit ring [qmask + 1]        */
+  uint64_t* cq;                   /* host-mapped completion ring [qmask + 1]: */
+                                  /* entry p = (p >> qlog2) + 1 << 32 | slot  */
+  uint64_t* close;                /* host-mapped: 0 open, else 1 << 63 | units */
+  lk_qslot* slots;                /* device: request slots                    */
+  uint64_t qmask;
+  uint32_t qlog2;
+  uint32_t nslots;
+} lk_qstate;                      /* device memory (the start of the arena)   */
+
 /* Everything the persistent kernel needs; passed by value at launch. */
 #define LK_KFLAG_DIRECT 1u       /* every CTA polls the ring; else the master relays  */
 #define LK_KFLAG_MAILBOX 2u      /* the master takes work from lk_mbox, not the ring   */

@@ -97,6 +97,16 @@ struct lk_ctx {
     uint64_t seq_of[LK_BATCH_BUFFERS] = {0};    /* batch seq that last used each table */
   };
   BatchState* batch = nullptr;   /* [C] */
+
+  /* lk_serve's device queue (live contexts): host-mapped unit ring,
+   * completion ring and close word */
+  uint32_t qn = 0, qlog2 = 0;
+  lk_qunit* q_units_h = nullptr;
+  lk_qunit* q_units_d = nullptr;
+  uint64_t* q_cq_h = nullptr;
+  uint64_t* q_cq_d = nullptr;
+  uint64_t* q_close_h = nullptr;
+  uint64_t* q_close_d = nullptr;
   lkb_launch* launch = nullptr;
   std::atomic<int> running{0};
 };
@@ -282,7 +292,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if ((p->flags & LK_INIT_DIRECT) && (p->flags & LK_INIT_MAILBOX)) return LK_EINVAL;
   ctx->mailbox = live && (p->flags & LK_INIT_MAILBOX);
 
-  /* host-mapped block: [ring (live only)] cword[C] rdone[..] ctrl info[G] [unit tables (live only)] */
+  /* host-mapped block: [ring (live only)] cword[C] rdone[..] ctrl info[G] [unit tables, mailboxes,
+   * serving queue (live only)] */
   ctx->max_units = live ? (p->max_batch_units ? p->max_batch_units : 8192u) : 0u;
   if (ctx->max_units > (1u << 22)) return LK_EINVAL;
   size_t off_ring = 0;
@@ -302,7 +313,15 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   size_t units_bytes = (size_t)ctx->C * LK_BATCH_BUFFERS * ctx->max_units * sizeof(lk_unit);
   size_t off_mbox = align_up(off_units + units_bytes, LK_LINE);
   size_t mbox_bytes = ctx->mailbox ? ctx->C * sizeof(lk_mbox) : 0;
-  size_t mapped_bytes = align_up(off_mbox + mbox_bytes, 4096);
+  /* the serving queue: unit ring, completion ring, close word (live only) */
+  ctx->qn = live ? (p->serve_units ? p->serve_units : 65536u) : 0u;
+  if (live && (ctx->qn < 256 || ctx->qn > (1u << 22) || (ctx->qn & (ctx->qn - 1)))) return LK_EINVAL;
+  ctx->qlog2 = 0;
+  while (ctx->qn && (1u << ctx->qlog2) < ctx->qn) ctx->qlog2++;
+  size_t off_q = align_up(off_mbox + mbox_bytes, LK_LINE);
+  size_t off_cq = align_up(off_q + (size_t)ctx->qn * sizeof(lk_qunit), LK_LINE);
+  size_t off_close = align_up(off_cq + (size_t)ctx->qn * sizeof(uint64_t), LK_LINE);
+  size_t mapped_bytes = align_up(off_close + (ctx->qn ? LK_LINE : 0), 4096);
   rc = lkb_alloc_mapped(ctx->device, mapped_bytes, &ctx->mapped_h, &ctx->mapped_d);
   if (rc != LK_OK) return rc;
   char* mh = (char*)ctx->mapped_h;
@@ -314,6 +333,14 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   if (ctx->max_units) {
     ctx->units_h = (lk_unit*)(mh + off_units);
     ctx->units_d = (lk_unit*)(md + off_units);
+  }
+  if (ctx->qn) {
+    ctx->q_units_h = (lk_qunit*)(mh + off_q);
+    ctx->q_units_d = (lk_qunit*)(md + off_q);
+    ctx->q_cq_h = (uint64_t*)(mh + off_cq);
+    ctx->q_cq_d = (uint64_t*)(md + off_cq);
+    ctx->q_close_h = (uint64_t*)(mh + off_close);
+    ctx->q_close_d = (uint64_t*)(md + off_close);
   }
   if (ctx->mailbox) {
     ctx->mbox_h = (lk_mbox*)(mh + off_mbox);
@@ -1023,11 +1050,236 @@ struct ServeReq {
 
 }  // namespace
 
+static uint64_t queue_state_bytes(uint32_t nslots) {
+  return align_up(sizeof(lk_qstate), 256) + align_up((uint64_t)nslots * sizeof(lk_qslot), 256);
+}
+
+extern "C" uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight) {
+  return queue_state_bytes(max_inflight ? max_inflight : 4096u);
+}
+
+/* lk_serve, LK_SERVE_QUEUE: the device-resident queue (see lk.h).  The
+ * host admits requests, publishes their units round-robin into the
+ * host-mapped unit ring while fewer than `window` x CTAs published units are
+ * unclaimed, and retires requests from the completion ring.  Units are
+ * claimed in index order, so the claimed count is tracked by walking the
+ * entries' acknowledgements in order. */
+static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
+                       lk_request_result* res) {
+  if (!ctx->qn || ctx->mailbox) return LK_EINVAL;   /* live ring-mode contexts only */
+  const uint32_t nslots = p->max_inflight ? p->max_inflight : 4096u;
+  const uint64_t part_bytes = p->part_bytes ? p->part_bytes : (2ull << 20);
+  const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
+  const int window = p->window > 0 ? p->window : 2;
+  const uint64_t W = std::min<uint64_t>((uint64_t)window * (uint64_t)ctx->total, ctx->qn / 2);
+  if (nslots > ctx->qn || part_bytes < 65536 || ((uintptr_t)p->arena & 255u) || !p->arena) return LK_EINVAL;
+  const uint64_t sbytes = queue_state_bytes(nslots);
+  if (p->arena_bytes < sbytes) return LK_ENOMEM;
+  struct QReq {
+    uint64_t in_bytes = 0, out_bytes = 0, held = 0, out_off = 0;
+    uint32_t parts = 1, published = 0, slot = 0;
+    bool arena_out = false;
+    void* out = nullptr;
+  };
+  std::vector<QReq> st(count);
+  for (size_t i = 0; i < count; ++i) {
+    const lk_request& r = reqs[i];
+    if (r.producer >= (uint32_t)p->n_producers) return LK_EINVAL;
+    if (r.op < LK_OP_ADD_I32 || r.op > LK_OP_COPY_I32) return LK_EINVAL;
+    lk_desc d{r.op, 0, r.n, 0};
+    int rc = validate(&d, r.in0, r.in1, op_inputs(r.op), r.out ? r.out : (void*)(uintptr_t)256);
+    if (rc != LK_OK) return rc;
+    QReq& q = st[i];
+    q.in_bytes = item_input_bytes(r.op, r.n);
+    q.out_bytes = r.op == LK_OP_ADD_I32 || r.op == LK_OP_COPY_I32 ? 4 * r.n
+                  : r.op == LK_OP_SUM_F32                        ? 16
+                  : r.op == LK_OP_HIST_U8                        ? 1024
+                                                                 : 16384 * r.n;
+    const uint64_t want = std::max<uint64_t>(1, (q.in_bytes + part_bytes - 1) / part_bytes);
+    q.parts = (uint32_t)std::min<uint64_t>(want, LK_SERVE_MAX_PARTS);
+    q.arena_out = r.out == nullptr;
+    q.held = q.in_bytes + q.out_bytes;
+    if (q.held > p->budget_bytes || (q.arena_out && q.out_bytes + 256 > p->arena_bytes - sbytes)) return LK_ENOMEM;
+    res[i] = lk_request_result{0, 0, nullptr, LK_PENDING, q.parts};
+  }
+  if (!ctx_alive(ctx)) return LK_ESTATE;
+
+  /* device state at the start of the arena: zeroed (copy engine), then the
+   * header the serving CTAs read; the host-mapped rings start empty */
+  int rc = lkb_zero_device(ctx->device, p->arena, sbytes);
+  lk_qstate hdr;
+  memset(&hdr, 0, sizeof hdr);
+  hdr.units = ctx->q_units_d;
+  hdr.cq = ctx->q_cq_d;
+  hdr.close = ctx->q_close_d;
+  hdr.slots = (lk_qslot*)((char*)p->arena + align_up(sizeof(lk_qstate), 256));
+  hdr.qmask = ctx->qn - 1;
+  hdr.qlog2 = ctx->qlog2;
+  hdr.nslots = nslots;
+  if (rc == LK_OK) rc = lkb_copy_h2d(ctx->device, p->arena, &hdr, sizeof hdr);
+  if (rc != LK_OK) return rc;
+  memset(ctx->q_units_h, 0, (size_t)ctx->qn * sizeof(lk_qunit));
+  memset(ctx->q_cq_h, 0, (size_t)ctx->qn * sizeof(uint64_t));
+  st_rel(ctx->q_close_h, (uint64_t)0);
+  beat(ctx);
+  /* one LK_OP_SERVE per cluster: every CTA becomes a worker of the queue */
+  std::vector<uint64_t> serve_seq(ctx->C, 0);
+  for (int c = 0; c < ctx->C; ++c) {
+    const lk_desc d{LK_OP_SERVE, 0, 0, 0};
+    const uint64_t t0 = now_ns();
+    for (;;) {
+      rc = post(ctx, c, LK_CMD_WORK + LK_OP_SERVE, &d, p->arena, nullptr, nullptr, &serve_seq[c]);
+      if (rc != LK_EAGAIN) break;
+      if (!ctx_alive(ctx) || now_ns() - t0 > timeout) break;
+      std::this_thread::yield();
+    }
+    if (rc != LK_OK) {
+      /* the clusters that did get the descriptor leave at once when the queue closes */
+      st_rel(ctx->q_close_h, (1ull << 63));
+      for (int b = 0; b < c; ++b) lk_wait(ctx, ((uint64_t)b << 48) | serve_seq[b], 10000000000ull);
+      return rc == LK_EAGAIN ? LK_ETIMEDOUT : rc;
+    }
+  }
+
+  /* producers: each releases its own requests at their arrival times */
+  std::mutex qmu;
+  std::deque<size_t> arrived;
+  std::atomic<uint64_t> start{0};
+  std::atomic<int> ready{0};
+  std::atomic<bool> stop{false};
+  std::vector<std::vector<size_t>> mine(p->n_producers);
+  for (size_t i = 0; i < count; ++i) mine[reqs[i].producer].push_back(i);
+  for (auto& v : mine)
+    std::stable_sort(v.begin(), v.end(), [&](size_t a, size_t b) { return reqs[a].t_arrival_ns < reqs[b].t_arrival_ns; });
+  auto producer = [&](int w) {
+    ready.fetch_add(1);
+    uint64_t t0;
+    while ((t0 = start.load(std::memory_order_acquire)) == 0) {}
+    for (size_t i : mine[w]) {
+      while (now_ns() < t0 + reqs[i].t_arrival_ns)
+        if (stop.load(std::memory_order_relaxed)) return;
+      std::lock_guard<std::mutex> g(qmu);
+      arrived.push_back(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 0; w < p->n_producers; ++w) th.emplace_back(producer, w);
+  while (ready.load() < p->n_producers) std::this_thread::yield();
+  const uint64_t t0 = now_ns();
+  start.store(t0, std::memory_order_release);
+
+  Arena arena(p->arena_bytes - sbytes);
+  std::vector<uint32_t> free_slots(nslots);
+  for (uint32_t k = 0; k < nslots; ++k) free_slots[k] = nslots - 1 - k;
+  std::vector<size_t> slot_req(nslots, 0);
+  std::deque<size_t> waiting;    /* arrived, not admitted (FIFO) */
+  std::deque<size_t> active;     /* admitted with units left to publish (round-robin) */
+  uint64_t held = 0, next_u = 0, acked = 0, cq_head = 0, last_beat = t0;
+  size_t finished = 0;
+  int first_err = LK_OK;
+  char* const out_base = (char*)p->arena + sbytes;
+  while (finished < count) {
+    const uint64_t now = now_ns();
+    if (now - t0 > timeout) {
+      for (size_t i = 0; i < count; ++i)
+        if (res[i].status == LK_PENDING) res[i].status = LK_ETIMEDOUT;
+      first_err = LK_ETIMEDOUT;
+      break;
+    }
+    if (!ctx_alive(ctx)) {
+      int e = device_err_to_rc(dev_error(ctx));
+      for (size_t i = 0; i < count; ++i)
+        if (res[i].status == LK_PENDING) res[i].status = e ? e : LK_ESTATE;
+      first_err = e ? e : LK_ESTATE;
+      break;
+    }
+    if (now - last_beat > 1000000ull) {
+      beat(ctx);
+      last_beat = now;
+    }
+    {
+      std::lock_guard<std::mutex> g(qmu);
+      while (!arrived.empty()) {
+        waiting.push_back(arrived.front());
+        arrived.pop_front();
+      }
+    }
+    /* admission in arrival order while the budget, a slot and the arena allow */
+    while (!waiting.empty() && !free_slots.empty()) {
+      const size_t i = waiting.front();
+      QReq& q = st[i];
+      if (held + q.held > p->budget_bytes) break;
+      uint64_t oo = 0;
+      if (q.arena_out && !arena.alloc(q.out_bytes, &oo)) break;
+      q.out_off = oo;
+      q.out = q.arena_out ? out_base + oo : reqs[i].out;
+      q.slot = free_slots.back();
+      free_slots.pop_back();
+      slot_req[q.slot] = i;
+      held += q.held;
+      res[i].t_admit_ns = now_ns() - t0;
+      active.push_back(i);
+      waiting.pop_front();
+    }
+    /* claimed units: their entries are acknowledged in claim (index) order */
+    while (acked < next_u && ld_acq(&ctx->q_units_h[acked & (ctx->qn - 1)].ack) == acked + 1) ++acked;
+    /* publish one unit of each active request in turn, at most W unclaimed */
+    while (!active.empty() && next_u - acked < W) {
+      const size_t i = active.front();
+      active.pop_front();
+      QReq& q = st[i];
+      const lk_request& r = reqs[i];
+      lk_qunit* e = &ctx->q_units_h[next_u & (ctx->qn - 1)];
+      st_rlx(&e->in0, (uint64_t)(uintptr_t)r.in0);
+      st_rlx(&e->in1, (uint64_t)(uintptr_t)r.in1);
+      st_rlx(&e->out, (uint64_t)(uintptr_t)q.out);
+      st_rlx(&e->n_op, ((uint64_t)r.op << 56) | (r.n & LK_LOW48));
+      st_rlx(&e->meta, (uint64_t)q.published | ((uint64_t)q.parts << 16) | ((uint64_t)q.slot << 32));
+      st_rel(&e->seq, next_u + 1);   /* the fields before the seq word */
+      ++next_u;
+      if (++q.published < q.parts) active.push_back(i);
+    }
+    /* retire completed requests */
+    for (;;) {
+      const uint64_t v = ld_acq(&ctx->q_cq_h[cq_head & (ctx->qn - 1)]);
+      if ((v >> 32) != (cq_head >> ctx->qlog2) + 1) break;
+      const uint32_t slot = (uint32_t)(v & 0xffffffffu);
+      ++cq_head;
+      if (slot >= nslots) {
+        first_err = LK_EDEVICE;
+        continue;
+      }
+      const size_t i = slot_req[slot];
+      QReq& q = st[i];
+      res[i].t_complete_ns = now_ns() - t0;
+      res[i].status = LK_OK;
+      res[i].out = q.out;
+      if (q.arena_out) arena.release(q.out_off, q.out_bytes);
+      held -= q.held;
+      free_slots.push_back(slot);
+      ++finished;
+    }
+  }
+  stop.store(true);
+  for (auto& x : th) x.join();
+  /* close the queue: every worker whose claimed unit lies beyond the last
+   * published one leaves, and each cluster's LK_OP_SERVE completes */
+  st_rel(ctx->q_close_h, (1ull << 63) | next_u);
+  beat(ctx);
+  for (int c = 0; c < ctx->C; ++c) {
+    const int w = lk_wait(ctx, ((uint64_t)c << 48) | serve_seq[c], 10000000000ull);
+    if (w != LK_OK && first_err == LK_OK) first_err = w;
+  }
+  return first_err;
+}
+
 extern "C" int lk_serve(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
                         lk_request_result* res) {
   if (!ctx || !p || (count > 0 && (!reqs || !res)) || p->n_producers < 1 || p->n_producers > 256) return LK_EINVAL;
   for (int c = 1; c < ctx->C; ++c)
     if (ctx->sizes[c] != ctx->sizes[0]) return LK_EINVAL;   /* results must not depend on the cluster */
+  if (p->mode == LK_SERVE_QUEUE) return serve_queue(ctx, reqs, count, p, res);
+  if (p->mode != LK_SERVE_CHUNKS) return LK_EINVAL;
   const int window = p->window > 0 ? p->window : 2;
   const uint64_t chunk_bytes = p->chunk_bytes ? p->chunk_bytes : (16ull << 20);
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;

@@ -35,6 +35,8 @@ LK_OP_NOP, LK_OP_ADD_I32, LK_OP_HIST_U8, LK_OP_SUM_F32, LK_OP_GEMM64_F32, LK_OP_
 LK_OP_COMBINE_SUM, LK_OP_COMBINE_HIST = 6, 7
 LK_OP_SPIN = 8
 LK_OP_BATCH = 9
+LK_OP_SERVE = 10
+LK_SERVE_CHUNKS, LK_SERVE_QUEUE = 0, 1
 (LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING,
  LK_DERR_BOUNDS) = range(8)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
@@ -57,7 +59,8 @@ class lk_init_params(ctypes.Structure):
                 ("backoff_base_ns", ctypes.c_uint64), ("backoff_cap_ns", ctypes.c_uint64),
                 ("idle_lease_ns", ctypes.c_uint64), ("boot_timeout_ns", ctypes.c_uint64),
                 ("exec_log_cap", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("max_batch_units", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+                ("max_batch_units", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("serve_units", ctypes.c_uint32)]
 
 
 class lk_desc(ctypes.Structure):
@@ -90,7 +93,8 @@ class lk_serve_params(ctypes.Structure):
     _fields_ = [("n_producers", ctypes.c_int), ("window", ctypes.c_int), ("chunk_bytes", ctypes.c_uint64),
                 ("budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
                 ("timeout_ns", ctypes.c_uint64), ("coalesce_bytes", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32),
-                ("coalesce_part_bytes", ctypes.c_uint32)]
+                ("coalesce_part_bytes", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("part_bytes", ctypes.c_uint64)]
 
 
 TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op", "<u4"), ("n", "<u8"),
@@ -150,6 +154,7 @@ def load(fake: bool = False, bounds: bool = False) -> ctypes.CDLL:
             "lk_bounds_violations": (I, [I, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint32)]),
             "lk_submit_batch": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(lk_batch_tune), ctypes.POINTER(U64)]),
             "lk_serve": (I, [P, P, SZ, ctypes.POINTER(lk_serve_params), P]),
+            "lk_serve_queue_state_bytes": (U64, [ctypes.c_uint32]),
             "lk_phase_run": (I, [I, I, I, U64, I, P, P]),
             "lk_baseline_phase_run": (I, [I, I, I, U64, I, P, P]),
             "lk_baseline_graph": (I, [I, P, ctypes.c_uint32, I, I, I, ctypes.POINTER(ctypes.c_float)]),
@@ -230,12 +235,12 @@ def _operands(op: int, n: int, ins, out, ctas: int = 0) -> tuple:
 def make_params(sizes, device: int = 0, smids=None, threads_per_cta: int = 256, ring_depth: int = 1024,
                 backoff_base_ns: int = 0, backoff_cap_ns: int = 256, idle_lease_ns: int = 10_000_000_000,
                 boot_timeout_ns: int = 10_000_000_000, exec_log_cap: int = 0, flags: int = 0,
-                max_batch_units: int = 0, ctas_per_sm: int = 0):
+                max_batch_units: int = 0, ctas_per_sm: int = 0, serve_units: int = 0):
     """lk_init_params plus the arrays it points to (kept alive by the tuple)."""
     sz = (ctypes.c_int * len(sizes))(*sizes)
     sm = None if smids is None else (ctypes.c_int * len(smids))(*smids)
     p = lk_init_params(device, len(sizes), sz, sm, threads_per_cta, ring_depth, backoff_base_ns, backoff_cap_ns,
-                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags, max_batch_units, ctas_per_sm)
+                       idle_lease_ns, boot_timeout_ns, exec_log_cap, flags, max_batch_units, ctas_per_sm, serve_units)
     return p, (sz, sm)
 
 
@@ -506,15 +511,28 @@ def lk_baseline_graph(items: np.ndarray, max_ctas: int, threads: int = 256, reps
 
 def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int, arena=None, arena_bytes: int = 0,
              window: int = 0, chunk_bytes: int = 0, timeout_ns: int = 0, coalesce_bytes: int = 0,
-             coalesce_max: int = 0, coalesce_part_bytes: int = 0):
-    """Serve REQUEST_DTYPE requests; returns (rc, REQUEST_RES_DTYPE results)."""
+             coalesce_max: int = 0, coalesce_part_bytes: int = 0, mode: int = LK_SERVE_CHUNKS,
+             max_inflight: int = 0, part_bytes: int = 0):
+    """Serve REQUEST_DTYPE requests; returns (rc, REQUEST_RES_DTYPE results).
+    mode LK_SERVE_QUEUE runs them through the device-resident queue (the
+    arena's first lk_serve_queue_state_bytes(max_inflight) bytes hold its
+    state); LK_SERVE_CHUNKS through the host dispatcher."""
     reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
     res = np.zeros(reqs.size, dtype=REQUEST_RES_DTYPE)
     prm = lk_serve_params(n_producers, window, chunk_bytes, budget_bytes, _ptr(arena) or None, arena_bytes, timeout_ns,
-                          coalesce_bytes, coalesce_max, coalesce_part_bytes)
+                          coalesce_bytes, coalesce_max, coalesce_part_bytes, mode, max_inflight, part_bytes)
     rc = ctx.lib.lk_serve(ctx.ptr, reqs.ctypes.data if reqs.size else None, reqs.size, ctypes.byref(prm),
                           res.ctypes.data if reqs.size else None)
     return rc, res
+
+
+def lk_serve_queue_state_bytes(max_inflight: int = 0) -> int:
+    """Arena bytes the device queue's state takes (LK_SERVE_QUEUE)."""
+    try:
+        lib = load()
+    except OSError:
+        lib = load(True)
+    return int(lib.lk_serve_queue_state_bytes(max_inflight))
 
 
 PHASE_DTYPE = np.dtype([("init_ns", "<u8"), ("trigger_ns", "<u8"), ("wait_ns", "<u8"), ("dispose_ns", "<u8")])

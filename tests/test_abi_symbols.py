@@ -64,12 +64,14 @@ int main(void) {
          sizeof(lk_trace_item), sizeof(lk_trace_result));
   printf("%zu %zu %zu %zu\\n", offsetof(lk_exec_rec, order), offsetof(lk_exec_rec, t_done_ns),
          offsetof(lk_trace_item, in0), offsetof(lk_init_params, exec_log_cap));
+  printf("%zu %zu %zu %zu\\n", sizeof(lk_serve_params), offsetof(lk_serve_params, mode),
+         offsetof(lk_serve_params, part_bytes), offsetof(lk_init_params, serve_units));
   return 0;
 }
 """)
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-std=c11", f"-I{ROOT}/include", str(src), "-o", str(exe)])
-    l1, l2 = subprocess.check_output([str(exe)], text=True).split("\n")[:2]
+    l1, l2, l3 = subprocess.check_output([str(exe)], text=True).split("\n")[:3]
     from paper_2310_01212_gb300 import lk
 
     assert [int(x) for x in l1.split()] == [ctypes.sizeof(lk.lk_init_params), ctypes.sizeof(lk.lk_desc),
@@ -79,6 +81,8 @@ int main(void) {
                                            lk.EXEC_REC_DTYPE.fields["t_done_ns"][1],
                                            lk.TRACE_ITEM_DTYPE.fields["in0"][1],
                                            lk.lk_init_params.exec_log_cap.offset]
+    assert [int(x) for x in l3.split()] == [ctypes.sizeof(lk.lk_serve_params), lk.lk_serve_params.mode.offset,
+                                           lk.lk_serve_params.part_bytes.offset, lk.lk_init_params.serve_units.offset]
 
 
 def test_cuda_library_targets_sm_103a_only(native_built):

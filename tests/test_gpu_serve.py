@@ -1,8 +1,9 @@
 """GPU parity of the serving loop (lk_serve): requests of uneven size arriving
-from 8 producers are admitted, split into chunks that interleave across the
-clusters (or, when small, coalesced many to a batch post), combined, and
-every output matches the oracle; each result is bit-identical when the
-request is served alone."""
+from 8 producers are admitted and run -- through the device-resident queue
+(work units the clusters' CTAs claim themselves), or by the host dispatcher
+(chunks that interleave across the clusters, or, when small, coalesced many
+to a batch post) -- combined, and every output matches the oracle; each
+result is bit-identical when the request is served alone."""
 import numpy as np
 import pytest
 
@@ -12,9 +13,14 @@ from paper_2310_01212_gb300 import lk, workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=[0, 256 << 10], ids=["chunks", "coalesced"])
+MODES = {"chunks": dict(mode=lk.LK_SERVE_CHUNKS, window=2, chunk_bytes=1 << 20, coalesce_bytes=0),
+         "coalesced": dict(mode=lk.LK_SERVE_CHUNKS, window=2, chunk_bytes=1 << 20, coalesce_bytes=256 << 10),
+         "queue": dict(mode=lk.LK_SERVE_QUEUE, window=2, part_bytes=1 << 20)}
+
+
+@pytest.fixture(scope="module", params=list(MODES))
 def served(request, native_built, oracle_lib):
-    coalesce = request.param
+    kw = MODES[request.param]
     torch = need_gpu()
     pools = wl.Pools.create(5, i32_bytes=256 << 20, u8_bytes=256 << 20, f32_bytes=256 << 20, slots=4, n_add=16)
     reqs, _ = wl.serving_requests(pools, 5, 40_000.0, 0.006, s_hi=24 << 20)
@@ -34,8 +40,8 @@ def served(request, native_built, oracle_lib):
     torch.cuda.synchronize()
     with lk.lk_init([8, 8, 8, 8], idle_lease_ns=10_000_000_000) as c:
         rc, res = lk.lk_serve(c, reqs, n_producers=8, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
-                              window=2, chunk_bytes=1 << 20, coalesce_bytes=coalesce)
-    return torch, pools, reqs, outs, rc, res, arena, coalesce
+                              **kw)
+    return torch, pools, reqs, outs, rc, res, arena, kw
 
 
 def _inputs(pools, r):
@@ -53,10 +59,10 @@ def _inputs(pools, r):
 
 
 def test_served_outputs_match_oracle(served, oracle_lib):
-    torch, pools, reqs, outs, rc, res, arena, coalesce = served
+    torch, pools, reqs, outs, rc, res, arena, kw = served
     assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
     assert reqs.size >= 100 and res["chunks"].max() > 1
-    if coalesce:
+    if kw.get("coalesce_bytes"):
         assert np.sum(res["chunks"] == 1) > 10
     for r, o in zip(reqs, outs):
         op = int(r["op"])
@@ -73,7 +79,7 @@ def test_served_outputs_match_oracle(served, oracle_lib):
 
 
 def test_each_result_same_alone_and_in_the_mix(served):
-    torch, pools, reqs, outs, rc, res, arena, coalesce = served
+    torch, pools, reqs, outs, rc, res, arena, kw = served
     pick = [i for i in range(reqs.size) if int(reqs[i]["op"]) in (lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8)][:12]
     pick += [i for i in range(reqs.size) if int(reqs[i]["op"]) in (lk.LK_OP_ADD_I32, lk.LK_OP_GEMM64_F32)][:8]
     # outputs exist before the context starts (an allocation while it runs may wait for the device)
@@ -87,7 +93,7 @@ def test_each_result_same_alone_and_in_the_mix(served):
             one["producer"] = 0
             one["out"] = alone_out.data_ptr()
             rc1, r1 = lk.lk_serve(c, one, n_producers=1, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
-                                  window=2, chunk_bytes=1 << 20, coalesce_bytes=coalesce)
+                                  **kw)
             assert rc1 == lk.LK_OK and r1["chunks"][0] == res["chunks"][i]
             a, m = host(alone_out), host(outs[i])
             if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32:

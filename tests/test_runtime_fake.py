@@ -674,3 +674,112 @@ def test_rate_caps_are_checked(fake_env):
 def test_gemm_ffma_flag_accepted(fake_env):
     with ctx_(flags=lk.LK_INIT_GEMM_FFMA | lk.LK_INIT_MAILBOX) as c:
         assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)) == lk.LK_OK
+
+
+# ---- serving through the device-resident queue (LK_SERVE_QUEUE) --------------------------
+def _queue_arena(extra=1 << 20, max_inflight=64):
+    """A real host buffer stands in for the arena (the fake's device memory
+    is host memory): the queue's state lives at its start."""
+    n = lk.lk_serve_queue_state_bytes(max_inflight) + extra
+    buf = np.zeros(n + 256, dtype=np.uint8)
+    base = (buf.ctypes.data + 255) // 256 * 256
+    return buf, base, n
+
+
+def _serve_q(c, reqs, **kw):
+    buf, base, n = _queue_arena(max_inflight=kw.get("max_inflight", 64))
+    kw.setdefault("max_inflight", 64)
+    kw.setdefault("part_bytes", 1 << 20)
+    rc, res = lk.lk_serve(c, reqs, n_producers=4, budget_bytes=kw.pop("budget_bytes", 1 << 34), arena=base,
+                          arena_bytes=n, mode=lk.LK_SERVE_QUEUE, **kw)
+    del buf
+    return rc, res
+
+
+def test_queue_serves_every_request_with_its_units(fake_env):
+    with ctx_(sizes=(2, 2, 2)) as c:
+        reqs = _reqs(80, [lk.LK_OP_ADD_I32, lk.LK_OP_SUM_F32, lk.LK_OP_HIST_U8, lk.LK_OP_GEMM64_F32, lk.LK_OP_COPY_I32],
+                     [1 << 10, 5 << 20, 3 << 20, 40, 0])
+        rc, res = _serve_q(c, reqs)
+        assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+        assert np.all(res["t_complete_ns"] >= res["t_admit_ns"])
+        assert np.all(res["t_admit_ns"] >= reqs["t_arrival_ns"])
+        # units: ceil(input bytes / 1 MiB), at least one
+        want = {lk.LK_OP_ADD_I32: 1, lk.LK_OP_SUM_F32: 20, lk.LK_OP_HIST_U8: 3, lk.LK_OP_GEMM64_F32: 2,
+                lk.LK_OP_COPY_I32: 1}
+        for r, q in zip(reqs, res):
+            assert q["chunks"] == want[int(r["op"])], (int(r["op"]), q["chunks"])
+        assert np.all(res["out"] % 256 == 0)
+        # the context serves ordinary descriptors again afterwards
+        assert lk.lk_wait(c, lk.lk_submit(c, 1, lk.LK_OP_NOP, 0)) == lk.LK_OK
+
+
+def test_queue_serves_twice_and_empty(fake_env):
+    with ctx_(sizes=(1, 1)) as c:
+        for k in range(3):
+            reqs = _reqs(0 if k == 1 else 30, [lk.LK_OP_SUM_F32, lk.LK_OP_COPY_I32], [3 << 20, 1 << 12])
+            rc, res = _serve_q(c, reqs)
+            assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+
+
+def test_queue_interleaves_a_late_small_request(fake_env):
+    """A small request that arrives while a large one is still being
+    published is not queued behind all of its units: round-robin publication
+    with a bounded window lets it finish first."""
+    fake_env["LK_FAKE_STALL_US"] = "300"
+    with ctx_(sizes=(1, 1)) as c:
+        big = _reqs(1, [lk.LK_OP_COPY_I32], [256 << 20], gap_ns=0, out=A)   # 1024 units of 1 MiB
+        small = _reqs(1, [lk.LK_OP_COPY_I32], [1 << 10], gap_ns=0, out=A)
+        small["t_arrival_ns"] = 5_000_000
+        rc, res = _serve_q(c, np.concatenate([big, small]), window=2)
+        assert rc == lk.LK_OK and res["chunks"][0] == 1024
+        assert res["t_complete_ns"][1] < res["t_complete_ns"][0]
+        assert res["t_complete_ns"][1] - res["t_admit_ns"][1] < 50_000_000
+
+
+def test_queue_budget_limits_admission(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "1000"
+    with ctx_(sizes=(1, 1)) as c:
+        reqs = _reqs(6, [lk.LK_OP_COPY_I32], [1 << 20], producers=2, gap_ns=0, out=A)   # 8 MiB held each
+        rc, res = _serve_q(c, reqs, budget_bytes=8 << 20)
+        assert rc == lk.LK_OK
+        order = np.argsort(res["t_admit_ns"])
+        assert np.all(res["t_admit_ns"][order][1:] >= res["t_complete_ns"][order][:-1])
+
+
+def test_queue_slots_limit_admission(fake_env):
+    fake_env["LK_FAKE_STALL_US"] = "500"
+    with ctx_(sizes=(2,)) as c:
+        reqs = _reqs(12, [lk.LK_OP_SUM_F32], [1 << 10], gap_ns=0)
+        rc, res = _serve_q(c, reqs, max_inflight=2)
+        assert rc == lk.LK_OK and np.all(res["status"] == lk.LK_OK)
+        # never more than two admitted and unfinished at once
+        ev = sorted([(t, 1) for t in res["t_admit_ns"]] + [(t, -1) for t in res["t_complete_ns"]],
+                    key=lambda e: (e[0], e[1]))
+        live = np.cumsum([e[1] for e in ev])
+        assert live.max() <= 2
+
+
+@pytest.mark.parametrize("kw", [dict(part_bytes=1 << 12), dict(max_inflight=1 << 20), dict(mode=7)])
+def test_queue_argument_checks(fake_env, kw):
+    with ctx_(sizes=(1,)) as c:
+        buf, base, n = _queue_arena()
+        mode = kw.pop("mode", lk.LK_SERVE_QUEUE)
+        rc, _ = lk.lk_serve(c, _reqs(1, [lk.LK_OP_COPY_I32], [16]), n_producers=4, budget_bytes=1 << 30,
+                            arena=base, arena_bytes=n, mode=mode, **kw)
+        assert rc == lk.LK_EINVAL
+
+
+def test_queue_needs_arena_for_its_state(fake_env):
+    with ctx_(sizes=(1,)) as c:
+        buf, base, n = _queue_arena()
+        rc, _ = lk.lk_serve(c, _reqs(1, [lk.LK_OP_COPY_I32], [16]), n_producers=4, budget_bytes=1 << 30,
+                            arena=base, arena_bytes=1024, mode=lk.LK_SERVE_QUEUE)
+        assert rc == lk.LK_ENOMEM
+
+
+def test_queue_device_error_ends_the_call(fake_env):
+    fake_env["LK_FAKE_FAIL_AFTER"] = "0"
+    with ctx_(sizes=(1,)) as c:
+        rc, res = _serve_q(c, _reqs(5, [lk.LK_OP_COPY_I32], [16]))
+        assert rc != lk.LK_OK
