@@ -309,6 +309,10 @@ def build_headline(d: dict, hbm: float) -> dict:
         "floor_over_nop_p50": round(d["pingpong_floor_us"]["p50"] / nop["lk"]["p50"], 3),
         "nop_device_p50_us": {k[:-3]: rnd1(v["p50"]) for k, v in nop["lk_device_phases"].items()
                               if k.endswith("_us")},
+        "tail": {"lk_max_item": d["tail_attribution"]["lk_top10"][0],
+                 "lk_device_pick_to_done_max_us": rnd1(d["tail_attribution"]["lk_device_pick_to_done_us"]["max"]),
+                 "items_over_25us_lk_vs_launch_sync": [d["tail_attribution"]["lk_items_over_25us"],
+                                                       d["tail_attribution"]["launch_sync_items_over_25us"]]},
         "small_us_p99_max": {"lk": [rnd1(small["lk_us"]["p99"]), rnd1(small["lk_us"]["max"])],
                              "launch_sync": [rnd1(small["launch_sync_us"]["p99"]),
                                              rnd1(small["launch_sync_us"]["max"])],
@@ -331,6 +335,25 @@ def build_headline(d: dict, hbm: float) -> dict:
                    "body_checks_bad": sum(v["parity"]["mismatches"] for v in bw.values()),
                    "batching_bad": bat["parity_mismatches"], "small_exact": small["bit_exact"]},
     }
+
+
+def item_device_us(items, log) -> np.ndarray:
+    """Device-side pick -> done (us) of each trace item, from one context's
+    execution log.  Each cluster's items were posted by one thread in
+    arrival order, so the k-th item of cluster c is its descriptor seq k+1."""
+    out = np.full(items.size, np.nan)
+    key = log["cluster"].astype(np.int64) << 40 | log["seq"].astype(np.int64)
+    last = log["t_done_ns"] > 0
+    dmap = dict(zip(key[last].tolist(), (log["t_done_ns"][last].astype(np.int64)
+                                          - log["t_pick_ns"][last].astype(np.int64)).tolist()))
+    for c in np.unique(items["cluster"]):
+        idx = np.nonzero(items["cluster"] == c)[0]
+        idx = idx[np.argsort(items["t_arrival_ns"][idx], kind="stable")]
+        for k, i in enumerate(idx):
+            v = dmap.get(int(c) << 40 | (k + 1))
+            if v is not None:
+                out[i] = v / 1000.0
+    return out
 
 
 def exec_log_phases(log) -> dict:
@@ -567,7 +590,7 @@ def main():
 
     # ---- timed region: K steps of (boot, trace, dispose) ---------------------------
     sizes = cfg["sizes"]
-    lat, lat_arr, kernel_ms = [], [], []
+    lat, lat_arr, kernel_ms, dev_us = [], [], [], []
     clocks = ClockSampler(dev)
     log_verdict = None
     for s in range(args.warmup + args.steps):
@@ -578,14 +601,18 @@ def main():
             t_timed = time.perf_counter()
         timed = s >= args.warmup
         last = s == args.warmup + args.steps - 1
-        ctx = lk.lk_init(sizes, device=dev, threads_per_cta=cfg["threads"], exec_log_cap=4096 if last else 0,
+        ctx = lk.lk_init(sizes, device=dev, threads_per_cta=cfg["threads"], exec_log_cap=4096,
                          idle_lease_ns=5_000_000_000)
         rc, res = lk.lk_run_trace(ctx, traces[s][0], n_threads=len(sizes), pin_cpu_base=pin)
         if rc != lk.LK_OK:
             raise RuntimeError(f"trace failed: {lk.lk_strerror(rc)}")
+        # the device's own pick -> done of every item (execution log; read
+        # after the trace, while the context idles)
+        log, dropped = lk.lk_exec_log(ctx)
+        if timed:
+            dev_us.append(item_device_us(traces[s][0], log))
         if last:
             last_res = res
-            log, dropped = lk.lk_exec_log(ctx)
             ops = traces[s][1]["op"]
             n_posted = [int(np.sum(np.arange(items_per_step) % 4 == c)) for c in range(4)]
             posted_op = np.concatenate([ops[np.arange(items_per_step) % 4 == c] for c in range(4)])
@@ -604,6 +631,8 @@ def main():
     wall = time.perf_counter() - t_timed
     lat = np.concatenate(lat)
     lat_arr = np.concatenate(lat_arr)
+    dev_us = np.concatenate(dev_us)
+    op_all = np.concatenate([traces[s][0]["op"] for s in range(args.warmup, args.warmup + args.steps)])
 
     # ---- parity: a seeded sample of the last step's items against the oracle -------
     it, meta = traces[-1]
@@ -633,6 +662,18 @@ def main():
             raise RuntimeError(f"baseline failed: {lk.lk_strerror(rc)}")
         base.append((res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0)
     base = np.concatenate(base)
+    top_lk = np.argsort(lat)[::-1][:10]
+    top_base = np.argsort(base)[::-1][:10]
+    nan2none = lambda x: None if not np.isfinite(x) else round(float(x), 2)
+    tail = {"lk_top10": [{"us": round(float(lat[i]), 2), "device_pick_to_done_us": nan2none(dev_us[i]),
+                          "op": lk.OP_NAMES.get(int(op_all[i]), str(int(op_all[i])))} for i in top_lk],
+            "launch_sync_top10": [{"us": round(float(base[i]), 2),
+                                   "op": lk.OP_NAMES.get(int(op_all[i]), str(int(op_all[i])))} for i in top_base],
+            "lk_items_over_25us": int(np.sum(lat > 25.0)), "launch_sync_items_over_25us": int(np.sum(base > 25.0)),
+            "lk_device_pick_to_done_us": lat_summary(dev_us[np.isfinite(dev_us)]),
+            "lk_items_without_device_stamp": int(np.sum(~np.isfinite(dev_us))),
+            "note": "device pick->done from the execution log (%globaltimer); the rest of an item's latency is "
+                    "host-side: posting, the descriptor's trip over the host link, completion observed"}
     # the occupancy-chosen grid: what an ordinary launch of the body picks on
     # its own (one CTA per SM at this shared-memory size, so every SM), for the
     # last timed step's trace
@@ -823,7 +864,8 @@ def main():
     arena = torch.empty(scfg["arena_bytes"], dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     serving = {"budget_bytes": scfg["budget_bytes"], "arena_bytes": scfg["arena_bytes"],
-               "part_bytes": scfg["part_bytes"], "window_units_per_cta": scfg["queue_window"],
+               "part_bytes": scfg["part_bytes"], "min_part_bytes": scfg["min_part_bytes"],
+               "window_units_per_cta": scfg["queue_window"],
                "producers": scfg["producers"], "seconds_per_rate": args.serve_seconds,
                "partition": "4 clusters x 37 SMs", "rates": {},
                "host_dispatcher": {"chunk_bytes": scfg["chunk_bytes"], "window": scfg["window"], "rates": {}},
@@ -831,17 +873,17 @@ def main():
                                              "coalesce_part_bytes": scfg["coalesce_part_bytes"], "rates": {}},
                "part_bytes_sweep_top_rate": {}}
     top = scfg["rates"][-3:]
-    runs = [("rates", r, dict(mode=lk.LK_SERVE_QUEUE, part_bytes=scfg["part_bytes"], window=scfg["queue_window"]))
-            for r in scfg["rates"]]
+    qkw = dict(mode=lk.LK_SERVE_QUEUE, part_bytes=scfg["part_bytes"], min_part_bytes=scfg["min_part_bytes"],
+               window=scfg["queue_window"])
+    runs = [("rates", r, qkw) for r in scfg["rates"]]
     runs += [("host_dispatcher", r, dict(mode=lk.LK_SERVE_CHUNKS, chunk_bytes=scfg["chunk_bytes"],
                                          window=scfg["window"])) for r in top]
     runs += [("host_dispatcher_coalesced", r, dict(mode=lk.LK_SERVE_CHUNKS, chunk_bytes=scfg["chunk_bytes"],
                                                    window=scfg["window"], coalesce_bytes=scfg["coalesce_bytes"],
                                                    coalesce_part_bytes=scfg["coalesce_part_bytes"]))
              for r in top[-1:]]
-    runs += [("part_bytes_sweep_top_rate", scfg["rates"][-1], dict(mode=lk.LK_SERVE_QUEUE, part_bytes=pb,
-                                                                   window=scfg["queue_window"]))
-             for pb in (1 << 20, 4 << 20, 8 << 20)]
+    runs += [("part_bytes_sweep_top_rate", scfg["rates"][-1], dict(qkw, part_bytes=pb))
+             for pb in (2 << 20, 4 << 20, 16 << 20)]
     with lk.lk_init(scfg["sizes"], device=dev, threads_per_cta=scfg["threads"], idle_lease_ns=30_000_000_000) as ctx:
         for where, rate, kw in runs:
             reqs, inb = wl.serving_requests(pools, seed, rate, args.serve_seconds)
@@ -1008,6 +1050,7 @@ def main():
         "latency_us": lat_summary(lat),
         "arrival_to_complete_us": lat_summary(lat_arr),
         "baseline_launch_sync_us": lat_summary(base),
+        "tail_attribution": tail,
         "baseline_occupancy_grid_us": dict(lat_summary(base_occ), grid=occ_grid,
                                            note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),
         "config_small": small,

@@ -298,7 +298,7 @@ int lk_baseline_graph(int device, const lk_batch_item* items, uint32_t count, in
  * hold (inputs, outputs, scratch) fit in a device-memory budget.  Two ways to
  * run what is admitted (lk_serve_params.mode):
  *   LK_SERVE_QUEUE (device-resident queue): each admitted request is split
- *     into work units of at most part_bytes of input, which the host
+ *     into work units (see the split rule below), which the host
  *     publishes into a ring in pinned host-mapped memory, one unit of each
  *     admitted request in turn (so a request that arrives while large ones
  *     run is interleaved with them), at most window x (CTAs) units ahead of
@@ -359,18 +359,29 @@ typedef struct {
   uint32_t mode;              /* LK_SERVE_CHUNKS or LK_SERVE_QUEUE                  */
   uint32_t max_inflight;      /* QUEUE: admitted, unfinished requests at most;     */
                               /* 0 -> 4096                                        */
-  uint64_t part_bytes;        /* QUEUE: input bytes per work unit (a request has   */
-                              /* at most 1024 units); 0 -> 2 MiB; >= 64 KiB         */
+  uint64_t part_bytes;        /* QUEUE: largest unit (input bytes); 0 -> 8 MiB     */
+  uint64_t min_part_bytes;    /* QUEUE: smallest unit when a request is spread      */
+                              /* wider; 0 -> 128 KiB; 64 KiB <= it <= part_bytes   */
 } lk_serve_params;
+
+/* How LK_SERVE_QUEUE splits a request of B input bytes into units (at most
+ * LK_SERVE_MAX_PARTS = 1024): at least ceil(B / part_bytes); a sum (whose
+ * float result depends on its split) exactly
+ *   max(ceil(B / part_bytes), min(32, ceil(B / min_part_bytes))),
+ * any other op as many as max(ceil(B / part_bytes), min(idle, ceil(B /
+ * min_part_bytes))), where idle = serving CTAs minus the units published and
+ * not finished when it is admitted (their results do not depend on the
+ * split), so a request spreads over the CTAs that are free. */
+#define LK_SERVE_SUM_WIDTH 32
 
 /* Device bytes the queue's state takes at the start of the arena
  * (LK_SERVE_QUEUE) for `max_inflight` request slots (0 -> 4096). */
 uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight);
 
 /* Run the requests through the context's clusters (all of one size) and
- * fill res[i] for each.  A request runs the same way whatever else is
- * served, so its result does not depend on the mix: QUEUE, as
- * ceil(input bytes / part_bytes) units (res.chunks = units); CHUNKS, as
+ * fill res[i] for each.  A request's result does not depend on the mix:
+ * QUEUE, as the units the split rule above gives (res.chunks = units);
+ * CHUNKS, as
  * chunks of at most chunk_bytes (one descriptor each, then one combine
  * descriptor for split sums and histograms), or, when it is at most
  * coalesce_bytes, as one item of a batch post split by coalesce_part_bytes

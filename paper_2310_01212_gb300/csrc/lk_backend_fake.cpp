@@ -149,8 +149,16 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       const uint64_t u = __atomic_fetch_add(&qs->head, 1ull, __ATOMIC_ACQ_REL);
       lk_qunit* e = qs->units + (u & qs->qmask);
       bool closed = false;
+      const uint64_t tag = ((u >> qs->qlog2) + 1) & 0xffffull;
+      uint64_t ew[6];
       int w = wait_for([&] {
-        if (ld_acq(&e->seq) == u + 1) return true;
+        for (int i = 0; i < 6; ++i) ew[i] = __atomic_load_n(&e->w[i], __ATOMIC_RELAXED);
+        bool cur = true;
+        for (int i = 0; i < 6; ++i) cur = cur && (ew[i] >> LK_TAG_SHIFT) == tag;
+        if (cur) {
+          __atomic_thread_fence(__ATOMIC_ACQUIRE);
+          return true;
+        }
         const uint64_t cl = ld_acq(qs->close);
         if ((cl >> 63) && u >= (cl & ~(1ull << 63))) {
           closed = true;
@@ -160,9 +168,8 @@ static void cluster_loop(lk_kargs a, int c, std::vector<int> ctas, std::vector<i
       });
       if (w) return w;
       if (closed) return 0;
-      const uint64_t meta = __atomic_load_n(&e->meta, __ATOMIC_RELAXED);
       st_rel(&e->ack, u + 1);
-      const uint32_t parts = (uint32_t)((meta >> 16) & 0xffffu), rslot = (uint32_t)(meta >> 32);
+      const uint32_t parts = (uint32_t)((ew[4] >> 16) & 0xffffu), rslot = (uint32_t)(ew[5] & 0xffffffffu);
       if (rslot >= qs->nslots || parts < 1) return (int)LK_DERR_BADDESC;
       if (stall) std::this_thread::sleep_for(std::chrono::nanoseconds(stall));
       lk_qslot* sl = qs->slots + rslot;

@@ -390,116 +390,25 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
   return ok ? 0 : LK_DERR_STAGING;
 }
 
-/* A batch (lk_submit_batch): the CTAs of the cluster claim work units from
- * the cluster's ticket until none is left.  Thread 0 claims and reads the
- * unit's 48-byte entry from the host-mapped unit table; the whole CTA runs
- * that part of that item.  Parts of a sum or histogram item combine through
- * per-item state: the last part to finish writes the item's output (sums in
- * binary64, in part order) and returns the state to zero.  Returns an
- * LK_DERR_* code or 0. */
-template <int MAXT, int P>
-__device__ __forceinline__ int run_batch(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
-                                         uint64_t* bars, uint32_t& phase, float* red) {
-  __shared__ uint64_t s_unit[6];
-  __shared__ unsigned long long s_u;
-  __shared__ float s_part;
-  __shared__ int s_lastp;
-  lk_bcluster* bc = a.bcl + c;
-  uint32_t* my_hist = a.cta_hist + (size_t)(a.cl_start[c] + r) * 256u;
-  const lk_unit* units = reinterpret_cast<const lk_unit*>(d.in0);
-  const uint64_t nunits = d.n;
-  const uint64_t rate = cta_rate(d.aux, a.cl_start[c + 1] - a.cl_start[c]);
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long u = atomicAdd(&bc->ticket, 1ull);
-      s_u = u;
-      if (u < nunits) {
-        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(units + u);
-        const ulonglong2 v0 = __ldcv(p), v1 = __ldcv(p + 1), v2 = __ldcv(p + 2);
-        s_unit[0] = v0.x; s_unit[1] = v0.y; s_unit[2] = v1.x;
-        s_unit[3] = v1.y; s_unit[4] = v2.x; s_unit[5] = v2.y;
-      }
-    }
-    __syncthreads();
-    if (s_u >= nunits) break;
-    const uint32_t op = (uint32_t)(s_unit[3] >> 56);
-    const uint32_t part = (uint32_t)(s_unit[4] & 0xffu);
-    const uint32_t parts = (uint32_t)((s_unit[4] >> 8) & 0xffu);
-    const uint64_t comb = s_unit[4] >> 16;
-    lk_slot it;
-    it.seq = d.seq;
-    it.cmd = LK_CMD_WORK + op;
-    it.flags = 0;
-    it.n = s_unit[3] & LK_LOW48;
-    it.in0 = s_unit[0];
-    it.in1 = s_unit[1];
-    it.out = s_unit[2];
-    it.aux = 0;
-    it.t_pick = 0;
-    const Pace deadline{gtime() + 2000000000ull, rate};
-    bool ok = true;
-    if (op == LK_OP_SUM_F32) {
-      float* pout = parts > 1 ? &bc->sums[comb - 1].partial[part] : &s_part;
-      ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
-      if (threadIdx.x == 0) {
-        if (parts == 1) {
-          *reinterpret_cast<float*>(it.out) = s_part;
-        } else {
-          lk_sum_state* st = &bc->sums[comb - 1];
-          __threadfence();
-          if (atomicAdd(&st->done, 1u) == parts - 1) {
-            __threadfence();
-            double sum = 0.0;
-            for (uint32_t q = 0; q < parts; ++q) sum += (double)__ldcg(&st->partial[q]);
-            *reinterpret_cast<float*>(it.out) = (float)sum;
-            st->done = 0;
-          }
-        }
-      }
-    } else if (op == LK_OP_HIST_U8) {
-      uint32_t* acc = parts > 1 ? bc->hists[comb - 1].bins : my_hist;
-      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, acc);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_lastp = 1;
-        if (parts > 1) {
-          __threadfence();
-          s_lastp = atomicAdd(&bc->hists[comb - 1].done, 1u) == parts - 1;
-          if (s_lastp) __threadfence();
-        }
-      }
-      __syncthreads();
-      if (s_lastp) {
-        combine_hist(it, acc);
-        if (parts > 1 && threadIdx.x == 0) bc->hists[comb - 1].done = 0;
-      }
-    } else {
-      const int e = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate,
-                                      (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
-      ok = (e == 0);
-    }
-    __syncthreads();   /* s_unit / s_u are rewritten by the next claim */
-    if (!ok) return LK_DERR_STAGING;
-  }
-  return 0;
-}
-
-/* Serving queue: thread 0 waits until unit u of the ring is published
- * (its seq word reads u + 1), or the host closed the queue below u.  The
- * entry is this CTA's alone (units are claimed once), so its probe delays
- * no other reader.  The entry's fields follow an acquire fence; the ack
- * tells the host the entry may be rewritten.  Returns 0 (w[0..4] = in0,
- * in1, out, n_op, meta), 1 (closed: no unit u) or an LK_DERR_* reason. */
-__device__ __noinline__ int serve_take(const lk_kargs& a, const lk_qstate* qs, lk_qunit* e, uint64_t u,
+/* Serving queue: thread 0 waits until unit u of the ring is published (all
+ * six words of entry u mod Q carry u's lap tag), or the host closed the
+ * queue below u.  The entry is this CTA's alone (units are claimed once), so
+ * its probe delays no other reader; one probe reads the whole entry, its
+ * last load an acquire.  The ack tells the host the entry may be rewritten.
+ * Returns 0 (w[0..5] = in0, in1, out, n, op/parts/part, slot, tags
+ * stripped), 1 (closed: no unit u) or an LK_DERR_* reason. */
+__device__ __noinline__ int serve_take(const lk_kargs& a, uint32_t qlog2, lk_qunit* e, uint64_t u,
                                        const uint64_t* close, uint64_t* w) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
   uint64_t close_v = 0, abort_v = 0, hb_v = hb;   /* loaded at one check, used at the next */
+  const uint64_t tag = ((u >> qlog2) + 1) & 0xffffull;
   for (uint32_t it = 1;; ++it) {
-    uint64_t sq;
-    asm volatile("ld.acquire.sys.u64 %0, [%1];" : "=l"(sq) : "l"(&e->seq) : "memory");
-    if (sq == u + 1) break;
+    ld_relaxed_sys_v2(&e->w[0], w[0], w[1]);
+    ld_relaxed_sys_v2(&e->w[2], w[2], w[3]);
+    asm volatile("ld.acquire.sys.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&e->w[4]) : "memory");
+    if (tags_match(w, tag)) break;
     if ((it & 15) == 0) {
       if ((close_v >> 63) && u >= (close_v & ~(1ull << 63))) return 1;
       close_v = ld_relaxed_sys(close);
@@ -517,55 +426,121 @@ __device__ __noinline__ int serve_take(const lk_kargs& a, const lk_qstate* qs, l
     }
     bo.pause();
   }
-  fence_acq_rel_sys();   /* nearly free after the acquire load (see probe()) */
-  ld_relaxed_sys_v2(&e->in0, w[0], w[1]);
-  ld_relaxed_sys_v2(&e->out, w[2], w[3]);
-  uint64_t ack;
-  ld_relaxed_sys_v2(&e->meta, w[4], ack);
+  for (int i = 0; i < 6; ++i) w[i] &= LK_LOW48;
   st_relaxed_sys(&e->ack, u + 1);
   return 0;
 }
 
-/* LK_OP_SERVE (lk_serve's device queue): the CTAs of every serving cluster
- * claim work units from one device counter until the queue closes.  A unit
- * is one part of one admitted request, run by this CTA with the body's
- * (part, parts) split, so a result depends only on the request and the
- * unit size.  Sum parts leave their partial in the request's slot and
- * histogram parts add into its bins; the last part to finish (an
- * acquire-release counter) writes the result (sums: binary64 in part order)
- * and returns the slot to zero; then, after a system-scope fence, the
- * request's slot id goes to the completion ring.  Returns an LK_DERR_* code
- * or 0. */
+/* Work units, claimed one at a time by each CTA of the cluster, for two
+ * descriptors (one loop, so the bodies are inlined once for both):
+ *   LK_OP_BATCH (lk_submit_batch): units from the batch's table in pinned
+ *     host-mapped memory, claimed with the cluster's ticket; the batch ends
+ *     when the table is exhausted.  Parts of a split sum or histogram
+ *     combine through per-item state in the cluster's batch state.
+ *   LK_OP_SERVE (lk_serve's device queue): the CTAs of every serving
+ *     cluster claim the next unit index from one device counter and wait
+ *     for that entry of the host-mapped unit ring (serve_take), until the
+ *     queue closes.  Parts combine through the request's slot; the last
+ *     part also appends the request to the completion ring, after a
+ *     system-scope fence.
+ * A unit is one part of one item or request, run by this CTA with the
+ * body's (part, parts) split, so a result depends only on the item and its
+ * parts.  The last part to finish (an acquire-release counter) writes a
+ * split result -- sums in binary64 by combine_sum, as a cluster of `parts`
+ * CTAs would, so a split sum is bit-identical to it -- and returns the
+ * state to zero.  Returns an LK_DERR_* code or 0. */
 template <int MAXT, int P>
-__device__ __forceinline__ int run_serve(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
+__device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, int c, int r, unsigned char* dsm,
                                          uint64_t* bars, uint32_t& phase, float* red) {
-  __shared__ uint64_t s_w[5];
-  __shared__ int s_take;
-  __shared__ float s_part;
+  __shared__ uint64_t s_w[5];                    /* in0, in1, out, op << 56 | n, unused */
+  __shared__ int s_take;                         /* 0 unit claimed, 1 none left, else LK_DERR_* */
+  __shared__ uint32_t s_part, s_parts;
+  __shared__ float* s_psum;                      /* per-part sums of a split item */
+  __shared__ uint32_t* s_pbins;                  /* accumulator of a split histogram */
+  __shared__ uint32_t* s_pdone;                  /* parts finished (split items) */
+  __shared__ uint32_t s_rslot;                   /* serve: the request's slot */
+  __shared__ float s_part_sum;
   __shared__ int s_lastp;
-  lk_qstate* qs = reinterpret_cast<lk_qstate*>(d.in0);
-  lk_qunit* units = reinterpret_cast<lk_qunit*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->units)));
-  uint64_t* cq = reinterpret_cast<uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->cq)));
-  const uint64_t* close = reinterpret_cast<const uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->close)));
-  lk_qslot* slots = reinterpret_cast<lk_qslot*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->slots)));
-  const uint64_t qmask = __ldcg(reinterpret_cast<const unsigned long long*>(&qs->qmask));
-  const uint32_t qlog2 = __ldcg(&qs->qlog2);
-  const uint32_t nslots = __ldcg(&qs->nslots);
+  const bool serve = d.cmd == LK_CMD_WORK + LK_OP_SERVE;
   uint32_t* my_hist = a.cta_hist + (size_t)(a.cl_start[c] + r) * 256u;
+  /* batch */
+  lk_bcluster* bc = a.bcl + c;
+  const lk_unit* units = reinterpret_cast<const lk_unit*>(d.in0);
+  const uint64_t nunits = d.n;
+  /* serve */
+  lk_qstate* qs = reinterpret_cast<lk_qstate*>(d.in0);
+  lk_qunit* qunits = nullptr;
+  uint64_t* cq = nullptr;
+  const uint64_t* qclose = nullptr;
+  lk_qslot* qslots = nullptr;
+  uint64_t qmask = 0;
+  uint32_t qlog2 = 0, nslots = 0;
+  if (serve) {
+    qunits = reinterpret_cast<lk_qunit*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->units)));
+    cq = reinterpret_cast<uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->cq)));
+    qclose = reinterpret_cast<const uint64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->close)));
+    qslots = reinterpret_cast<lk_qslot*>(__ldcg(reinterpret_cast<const unsigned long long*>(&qs->slots)));
+    qmask = __ldcg(reinterpret_cast<const unsigned long long*>(&qs->qmask));
+    qlog2 = __ldcg(&qs->qlog2);
+    nslots = __ldcg(&qs->nslots);
+  }
+  const uint64_t rate = serve ? 0 : cta_rate(d.aux, a.cl_start[c + 1] - a.cl_start[c]);
   for (;;) {
     if (threadIdx.x == 0) {
-      const unsigned long long u = atomicAdd(&qs->head, 1ull);
-      uint64_t w[5];
-      s_take = serve_take(a, qs, units + (u & qmask), u, close, w);
+      uint64_t w[5] = {0, 0, 0, 0, 0};
+      int take = 0;
+      uint32_t part = 0, parts = 1;
+      if (serve) {
+        const unsigned long long u = atomicAdd(&qs->head, 1ull);
+        uint64_t e[6];
+        take = serve_take(a, qlog2, qunits + (u & qmask), u, qclose, e);
+        part = (uint32_t)(e[4] & 0xffffu);
+        parts = (uint32_t)((e[4] >> 16) & 0xffffu);
+        const uint32_t rslot = (uint32_t)e[5];
+        w[0] = e[0];
+        w[1] = e[1];
+        w[2] = e[2];
+        w[3] = ((e[4] >> 32) & 0xffull) << 56 | e[3];   /* op << 56 | n, as a batch unit */
+        if (!take && (rslot >= nslots || parts < 1 || parts > LK_SERVE_MAX_PARTS || part >= parts))
+          take = LK_DERR_BADDESC;
+        if (!take) {
+          lk_qslot* sl = qslots + rslot;
+          s_psum = sl->partial;
+          s_pbins = sl->bins;
+          s_pdone = &sl->done;
+          s_rslot = rslot;
+        }
+      } else {
+        const unsigned long long u = atomicAdd(&bc->ticket, 1ull);
+        if (u < nunits) {
+          const ulonglong2* p = reinterpret_cast<const ulonglong2*>(units + u);
+          const ulonglong2 v0 = __ldcv(p), v1 = __ldcv(p + 1), v2 = __ldcv(p + 2);
+          w[0] = v0.x; w[1] = v0.y; w[2] = v1.x; w[3] = v1.y;
+          part = (uint32_t)(v2.x & 0xffu);
+          parts = (uint32_t)((v2.x >> 8) & 0xffu);
+          const uint64_t comb = v2.x >> 16;   /* combine slot + 1, 0 = none */
+          const uint32_t op = (uint32_t)(w[3] >> 56);
+          if (comb && op == LK_OP_SUM_F32) {
+            s_psum = bc->sums[comb - 1].partial;
+            s_pdone = &bc->sums[comb - 1].done;
+          } else if (comb && op == LK_OP_HIST_U8) {
+            s_pbins = bc->hists[comb - 1].bins;
+            s_pdone = &bc->hists[comb - 1].done;
+          }
+        } else {
+          take = 1;
+        }
+      }
       for (int i = 0; i < 5; ++i) s_w[i] = w[i];
+      s_part = part;
+      s_parts = parts;
+      s_take = take;
     }
     __syncthreads();
     const int take = s_take;   /* CTA-uniform */
     if (take) return take == 1 ? 0 : take;
     const uint32_t op = (uint32_t)(s_w[3] >> 56);
-    const uint32_t part = (uint32_t)(s_w[4] & 0xffffu);
-    const uint32_t parts = (uint32_t)((s_w[4] >> 16) & 0xffffu);
-    const uint32_t rslot = (uint32_t)(s_w[4] >> 32);
+    const uint32_t part = s_part, parts = s_parts;
     lk_slot it;
     it.seq = d.seq;
     it.cmd = LK_CMD_WORK + op;
@@ -576,47 +551,48 @@ __device__ __forceinline__ int run_serve(const lk_kargs& a, const lk_slot& d, in
     it.out = s_w[2];
     it.aux = 0;
     it.t_pick = 0;
+    const Pace deadline{gtime() + 2000000000ull, rate};
     bool ok = true;
-    if (rslot >= nslots || parts < 1 || parts > LK_SERVE_MAX_PARTS || part >= parts) return LK_DERR_BADDESC;
-    lk_qslot* sl = slots + rslot;
-    const Pace deadline{gtime() + 2000000000ull, 0};
     if (op == LK_OP_SUM_F32) {
-      float* pout = parts > 1 ? &sl->partial[part] : &s_part;
+      float* pout = parts > 1 ? s_psum + part : &s_part_sum;
       ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
     } else if (op == LK_OP_HIST_U8) {
-      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, parts > 1 ? sl->bins : my_hist);
+      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, parts > 1 ? s_pbins : my_hist);
     } else {
-      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, 0,
+      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate,
                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0) == 0;
     }
     __syncthreads();
-    /* the last part of the request (a single part always is) finishes it */
+    /* the last part of a split sum or histogram (a single part always is) finishes it */
+    const bool split = parts > 1 && (op == LK_OP_SUM_F32 || op == LK_OP_HIST_U8 || serve);
     if (threadIdx.x == 0) {
       s_lastp = 1;
-      if (parts > 1) {
+      if (split) {
         __threadfence();
-        s_lastp = atomicAdd(&sl->done, 1u) == parts - 1;
+        s_lastp = atomicAdd(s_pdone, 1u) == parts - 1;
         if (s_lastp) __threadfence();
       }
     }
     __syncthreads();
     if (s_lastp) {
       if (op == LK_OP_SUM_F32) {
-        if (parts > 1) combine_sum(it, sl->partial, (int)parts);
-        else if (threadIdx.x == 0) *reinterpret_cast<float*>(it.out) = s_part;
+        if (parts > 1) combine_sum(it, s_psum, (int)parts);
+        else if (threadIdx.x == 0) *reinterpret_cast<float*>(it.out) = s_part_sum;
       } else if (op == LK_OP_HIST_U8) {
-        combine_hist(it, parts > 1 ? sl->bins : my_hist);
+        combine_hist(it, parts > 1 ? s_pbins : my_hist);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
-        if (parts > 1) sl->done = 0;
-        /* every output write of the request before its completion entry */
-        fence_acq_rel_sys();
-        const unsigned long long pos = atomicAdd(&qs->cq_tail, 1ull);
-        st_relaxed_sys(cq + (pos & qmask), (((uint64_t)pos >> qlog2) + 1) << 32 | rslot);
+        if (split) *s_pdone = 0;
+        if (serve) {
+          /* every output write of the request before its completion entry */
+          fence_acq_rel_sys();
+          const unsigned long long pos = atomicAdd(&qs->cq_tail, 1ull);
+          st_relaxed_sys(cq + (pos & qmask), (((uint64_t)pos >> qlog2) + 1) << 32 | s_rslot);
+        }
       }
     }
-    __syncthreads();   /* s_w / s_take are rewritten by the next claim */
+    __syncthreads();   /* the shared claim words are rewritten by the next claim */
     if (!ok) return LK_DERR_STAGING;
   }
 }
@@ -738,7 +714,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     /* ---- descriptor k+1: from the ring, or from the master's relay ------ */
     if (tid == 0) {
       int err = 0;
-      lk_slot dsc;
+      lk_slot& dsc = s_desc;   /* written in place: no copy through local memory */
       const lk_wire* w = ring + (k & a.ring_mask);
       const uint64_t tag = lk_lap_tag(k, a.ring_log2);
       /* slot k mod D (relay copy, partials, histogram accumulator, arrival
@@ -788,7 +764,6 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
         }
         s_exit = 1;
       } else {
-        s_desc = dsc;
         s_exit = (dsc.cmd == LK_CMD_EXIT);
       }
       s_err = 0;
@@ -802,11 +777,10 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     /* ---- run this CTA's share ------------------------------------------ */
     const lk_slot d = s_desc;
     const uint32_t op = d.cmd - LK_CMD_WORK;
-    const int berr = op == LK_OP_BATCH   ? run_batch<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
-                     : op == LK_OP_SERVE ? run_serve<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
-                                         : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red,
-                                                             &dc->partial[slot][r], dc->hist[slot], cta_rate(d.aux, S),
-                                                             (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
+    const int berr = (op == LK_OP_BATCH || op == LK_OP_SERVE)
+                         ? run_units<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
+                         : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot],
+                                             cta_rate(d.aux, S), (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 

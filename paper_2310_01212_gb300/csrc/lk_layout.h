@@ -197,14 +197,17 @@ typedef struct __attribute__((aligned(LK_LINE))) {
  * request combines it (sums in part order, histograms) and appends the
  * request's slot to a completion ring in host-mapped memory.  The host only
  * admits, publishes and retires. */
+/* Unit u sits in entry u mod Q.  Like the mailbox ring, every word the host
+ * writes carries the lap tag (u >> log2 Q) + 1 in its top 16 bits, so the
+ * claimer reads the whole entry in one probe and accepts it when all six
+ * tags are current (unit indices below 2^32 per lk_serve call).
+ *   w0 = tag | in0      w3 = tag | n
+ *   w1 = tag | in1      w4 = tag | op << 32 | parts << 16 | part
+ *   w2 = tag | out      w5 = tag | request slot                          */
 typedef struct __attribute__((aligned(64))) {
-  uint64_t in0, in1, out;
-  uint64_t n_op;     /* op << 56 | n (n < 2^48)                                   */
-  uint64_t meta;     /* part (bits 0-15) | parts (16-31) | request slot (32-63)    */
+  uint64_t w[6];
   uint64_t ack;      /* device: u + 1 once the claimer has read the entry          */
   uint64_t pad;
-  uint64_t seq;      /* host: u + 1 once unit u's fields are written (stored last, */
-                     /* after a release fence)                                     */
 } lk_qunit;          /* 64 bytes */
 
 #define LK_SERVE_MAX_PARTS 1024   /* work units of one request           */

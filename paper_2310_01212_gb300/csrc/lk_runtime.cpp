@@ -899,6 +899,12 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
     uint64_t deadline = t0 + timeout_ns;
     /* pending handles in submission order per cluster (completion is FIFO per cluster) */
     std::vector<std::vector<std::pair<uint64_t, size_t>>> pend(ctx->C);
+    /* no allocation inside the timed loop: room for every item up front */
+    {
+      std::vector<size_t> per_cluster(ctx->C, 0);
+      for (size_t k = 0; k < v.size(); ++k) per_cluster[items[v[k]].cluster]++;
+      for (int c = 0; c < ctx->C; ++c) pend[c].reserve(per_cluster[c]);
+    }
     std::vector<size_t> head(ctx->C, 0);
     size_t next = 0, finished = 0;
     while (finished < v.size()) {
@@ -1060,24 +1066,27 @@ extern "C" uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight) {
 
 /* lk_serve, LK_SERVE_QUEUE: the device-resident queue (see lk.h).  The
  * host admits requests, publishes their units round-robin into the
- * host-mapped unit ring while fewer than `window` x CTAs published units are
- * unclaimed, and retires requests from the completion ring.  Units are
- * claimed in index order, so the claimed count is tracked by walking the
- * entries' acknowledgements in order. */
+ * host-mapped unit ring (lap-tagged words, as lk_qunit describes) while
+ * fewer than `window` x CTAs published units are unclaimed, and retires
+ * requests from the completion ring.  Units are claimed in index order, so
+ * the claimed count is tracked by walking the entries' acknowledgements in
+ * order; unit indices stay below 2^32 per call. */
 static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const lk_serve_params* p,
                        lk_request_result* res) {
   if (!ctx->qn || ctx->mailbox) return LK_EINVAL;   /* live ring-mode contexts only */
   const uint32_t nslots = p->max_inflight ? p->max_inflight : 4096u;
-  const uint64_t part_bytes = p->part_bytes ? p->part_bytes : (2ull << 20);
+  const uint64_t part_bytes = p->part_bytes ? p->part_bytes : (8ull << 20);
+  const uint64_t min_part = p->min_part_bytes ? p->min_part_bytes : (128ull << 10);
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
   const int window = p->window > 0 ? p->window : 2;
   const uint64_t W = std::min<uint64_t>((uint64_t)window * (uint64_t)ctx->total, ctx->qn / 2);
-  if (nslots > ctx->qn || part_bytes < 65536 || ((uintptr_t)p->arena & 255u) || !p->arena) return LK_EINVAL;
+  if (nslots > ctx->qn || min_part < 65536 || part_bytes < min_part || ((uintptr_t)p->arena & 255u) || !p->arena)
+    return LK_EINVAL;
   const uint64_t sbytes = queue_state_bytes(nslots);
   if (p->arena_bytes < sbytes) return LK_ENOMEM;
   struct QReq {
     uint64_t in_bytes = 0, out_bytes = 0, held = 0, out_off = 0;
-    uint32_t parts = 1, published = 0, slot = 0;
+    uint32_t parts = 1, published = 0, slot = 0, base_parts = 1, wide_parts = 1;
     bool arena_out = false;
     void* out = nullptr;
   };
@@ -1095,8 +1104,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
                   : r.op == LK_OP_SUM_F32                        ? 16
                   : r.op == LK_OP_HIST_U8                        ? 1024
                                                                  : 16384 * r.n;
-    const uint64_t want = std::max<uint64_t>(1, (q.in_bytes + part_bytes - 1) / part_bytes);
-    q.parts = (uint32_t)std::min<uint64_t>(want, LK_SERVE_MAX_PARTS);
+    /* at least this many units; a sum gets exactly its fixed width now,
+     * other ops may spread wider at admission (split_wide) */
+    q.base_parts = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (q.in_bytes + part_bytes - 1) / part_bytes),
+                                                LK_SERVE_MAX_PARTS);
+    q.wide_parts = (uint32_t)std::min<uint64_t>((q.in_bytes + min_part - 1) / min_part, LK_SERVE_MAX_PARTS);
+    if (r.op == LK_OP_GEMM64_F32) q.wide_parts = (uint32_t)std::min<uint64_t>(q.wide_parts, r.n);   /* whole tiles */
+    q.parts = r.op == LK_OP_SUM_F32 ? std::max(q.base_parts, std::min<uint32_t>(LK_SERVE_SUM_WIDTH, q.wide_parts))
+                                    : q.base_parts;
     q.arena_out = r.out == nullptr;
     q.held = q.in_bytes + q.out_bytes;
     if (q.held > p->budget_bytes || (q.arena_out && q.out_bytes + 256 > p->arena_bytes - sbytes)) return LK_ENOMEM;
@@ -1175,6 +1190,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   std::deque<size_t> waiting;    /* arrived, not admitted (FIFO) */
   std::deque<size_t> active;     /* admitted with units left to publish (round-robin) */
   uint64_t held = 0, next_u = 0, acked = 0, cq_head = 0, last_beat = t0;
+  uint64_t unfinished_units = 0;   /* units of admitted, unfinished requests */
   size_t finished = 0;
   int first_err = LK_OK;
   char* const out_base = (char*)p->arena + sbytes;
@@ -1217,6 +1233,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       free_slots.pop_back();
       slot_req[q.slot] = i;
       held += q.held;
+      if (reqs[i].op != LK_OP_SUM_F32) {
+        /* spread over the CTAs no published, unfinished unit holds */
+        const uint64_t busy = unfinished_units;
+        const uint64_t idle = busy < (uint64_t)ctx->total ? (uint64_t)ctx->total - busy : 0;
+        q.parts = std::max<uint32_t>(q.base_parts, (uint32_t)std::min<uint64_t>(idle, q.wide_parts));
+      }
+      unfinished_units += q.parts;
+      res[i].chunks = q.parts;
       res[i].t_admit_ns = now_ns() - t0;
       active.push_back(i);
       waiting.pop_front();
@@ -1230,12 +1254,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       QReq& q = st[i];
       const lk_request& r = reqs[i];
       lk_qunit* e = &ctx->q_units_h[next_u & (ctx->qn - 1)];
-      st_rlx(&e->in0, (uint64_t)(uintptr_t)r.in0);
-      st_rlx(&e->in1, (uint64_t)(uintptr_t)r.in1);
-      st_rlx(&e->out, (uint64_t)(uintptr_t)q.out);
-      st_rlx(&e->n_op, ((uint64_t)r.op << 56) | (r.n & LK_LOW48));
-      st_rlx(&e->meta, (uint64_t)q.published | ((uint64_t)q.parts << 16) | ((uint64_t)q.slot << 32));
-      st_rel(&e->seq, next_u + 1);   /* the fields before the seq word */
+      const uint64_t tag = (((next_u >> ctx->qlog2) + 1) & 0xffffull) << LK_TAG_SHIFT;
+      __atomic_thread_fence(__ATOMIC_RELEASE);   /* earlier host writes before the entry's words */
+      st_rlx(&e->w[0], tag | ((uint64_t)(uintptr_t)r.in0 & LK_LOW48));
+      st_rlx(&e->w[1], tag | ((uint64_t)(uintptr_t)r.in1 & LK_LOW48));
+      st_rlx(&e->w[2], tag | ((uint64_t)(uintptr_t)q.out & LK_LOW48));
+      st_rlx(&e->w[3], tag | (r.n & LK_LOW48));
+      st_rlx(&e->w[4], tag | ((uint64_t)r.op << 32) | ((uint64_t)q.parts << 16) | (uint64_t)q.published);
+      st_rlx(&e->w[5], tag | (uint64_t)q.slot);
       ++next_u;
       if (++q.published < q.parts) active.push_back(i);
     }
@@ -1256,6 +1282,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       res[i].out = q.out;
       if (q.arena_out) arena.release(q.out_off, q.out_bytes);
       held -= q.held;
+      unfinished_units -= q.parts;
       free_slots.push_back(slot);
       ++finished;
     }

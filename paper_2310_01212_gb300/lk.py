@@ -94,7 +94,7 @@ class lk_serve_params(ctypes.Structure):
                 ("budget_bytes", ctypes.c_uint64), ("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_uint64),
                 ("timeout_ns", ctypes.c_uint64), ("coalesce_bytes", ctypes.c_uint64), ("coalesce_max", ctypes.c_uint32),
                 ("coalesce_part_bytes", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
-                ("part_bytes", ctypes.c_uint64)]
+                ("part_bytes", ctypes.c_uint64), ("min_part_bytes", ctypes.c_uint64)]
 
 
 TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op", "<u4"), ("n", "<u8"),
@@ -512,7 +512,7 @@ def lk_baseline_graph(items: np.ndarray, max_ctas: int, threads: int = 256, reps
 def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int, arena=None, arena_bytes: int = 0,
              window: int = 0, chunk_bytes: int = 0, timeout_ns: int = 0, coalesce_bytes: int = 0,
              coalesce_max: int = 0, coalesce_part_bytes: int = 0, mode: int = LK_SERVE_CHUNKS,
-             max_inflight: int = 0, part_bytes: int = 0):
+             max_inflight: int = 0, part_bytes: int = 0, min_part_bytes: int = 0):
     """Serve REQUEST_DTYPE requests; returns (rc, REQUEST_RES_DTYPE results).
     mode LK_SERVE_QUEUE runs them through the device-resident queue (the
     arena's first lk_serve_queue_state_bytes(max_inflight) bytes hold its
@@ -520,7 +520,8 @@ def lk_serve(ctx: Context, reqs: np.ndarray, n_producers: int, budget_bytes: int
     reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
     res = np.zeros(reqs.size, dtype=REQUEST_RES_DTYPE)
     prm = lk_serve_params(n_producers, window, chunk_bytes, budget_bytes, _ptr(arena) or None, arena_bytes, timeout_ns,
-                          coalesce_bytes, coalesce_max, coalesce_part_bytes, mode, max_inflight, part_bytes)
+                          coalesce_bytes, coalesce_max, coalesce_part_bytes, mode, max_inflight, part_bytes,
+                          min_part_bytes)
     rc = ctx.lib.lk_serve(ctx.ptr, reqs.ctypes.data if reqs.size else None, reqs.size, ctypes.byref(prm),
                           res.ctypes.data if reqs.size else None)
     return rc, res

@@ -20,7 +20,8 @@ Configurations (all seeded):
              requests/s, request sizes log-uniform 4 KB..256 MB over the four
              bodies (a GEMM request of S bytes is floor(S / 48 KB) >= 1 tiles),
              admission by a 64 GB budget, 148 SMs as 4 clusters of 37; the
-             device-resident queue splits requests into 2 MiB work units.
+             device-resident queue splits requests into units of at most 8 MiB, spread
+             over idle CTAs down to 128 KiB units.
   isolation  a critical cluster of 16 SMs releases an FP32 sum over 1 MB
              (262,144 N(0,1) values) every 1 ms, waiting for each; a
              best-effort cluster of 132 SMs runs int32 copies of 4 GiB and
@@ -44,7 +45,8 @@ FULL_CHIP = dict(sizes=[37, 37, 37, 37], threads=256, rate_per_s=20_000.0, n_add
 BATCHING = dict(max_count=4096, n_lo=1024, n_hi=16_777_216, seed=0)
 SERVING = dict(sizes=[37, 37, 37, 37], threads=256, producers=8, rates=(5_000, 10_000, 20_000, 50_000, 100_000, 200_000),
                s_lo=4096, s_hi=256 << 20, budget_bytes=64 << 30, arena_bytes=24 << 30, chunk_bytes=64 << 20, window=2,
-               coalesce_bytes=4 << 20, coalesce_part_bytes=256 << 10, part_bytes=2 << 20, queue_window=2,
+               coalesce_bytes=4 << 20, coalesce_part_bytes=256 << 10, part_bytes=8 << 20, min_part_bytes=128 << 10,
+               queue_window=2,
                seed=0)
 ISOLATION = dict(sizes=[16, 132], threads=256, period_ns=1_000_000, crit_n=262_144, copy_n=1 << 30,
                  hist_n=256 << 20, seed=0)

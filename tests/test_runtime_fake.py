@@ -690,6 +690,7 @@ def _serve_q(c, reqs, **kw):
     buf, base, n = _queue_arena(max_inflight=kw.get("max_inflight", 64))
     kw.setdefault("max_inflight", 64)
     kw.setdefault("part_bytes", 1 << 20)
+    kw.setdefault("min_part_bytes", kw["part_bytes"])   # no spreading unless a test asks for it
     rc, res = lk.lk_serve(c, reqs, n_producers=4, budget_bytes=kw.pop("budget_bytes", 1 << 34), arena=base,
                           arena_bytes=n, mode=lk.LK_SERVE_QUEUE, **kw)
     del buf
@@ -712,6 +713,24 @@ def test_queue_serves_every_request_with_its_units(fake_env):
         assert np.all(res["out"] % 256 == 0)
         # the context serves ordinary descriptors again afterwards
         assert lk.lk_wait(c, lk.lk_submit(c, 1, lk.LK_OP_NOP, 0)) == lk.LK_OK
+
+
+def test_queue_split_rule(fake_env):
+    """A sum gets exactly max(ceil(B / part), min(32, ceil(B / min_part)))
+    units, whatever else runs; another op spreads over the idle CTAs (here
+    all six, nothing else is admitted at once), never below ceil(B / part)."""
+    with ctx_(sizes=(2, 2, 2)) as c:
+        ops = [lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_COPY_I32, lk.LK_OP_COPY_I32,
+               lk.LK_OP_HIST_U8, lk.LK_OP_GEMM64_F32]
+        ns = [1 << 10, 1 << 18, 9 << 20, 1 << 18, 9 << 20, 1 << 20, 3]
+        reqs = _reqs(len(ops), ops, ns, gap_ns=3_000_000, out=A)
+        rc, res = _serve_q(c, reqs, part_bytes=4 << 20, min_part_bytes=64 << 10)
+        assert rc == lk.LK_OK
+        got = res["chunks"].tolist()
+        # sums: 4 KiB -> 1; 1 MiB -> min(32, 16) = 16; 36 MiB -> max(9, 32) = 32
+        # copy 1 MiB -> min(6 idle, 16) = 6; copy 36 MiB -> max(9, min(6, ...)) = 9
+        # hist 1 MiB -> 6; gemm 3 tiles (96 KiB) -> min(6, 2, 3 tiles) = 2
+        assert got == [1, 16, 32, 6, 9, 6, 2], got
 
 
 def test_queue_serves_twice_and_empty(fake_env):
