@@ -517,15 +517,19 @@ def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, th
     }
     # the block size is a context parameter: the histogram, bound by shared-
     # memory reductions, is also timed at 512 threads per CTA
-    runs = [(name, case, threads) for name, case in cases.items()]
-    runs.append(("hist_u8_512_threads", cases["hist_u8"], 512))
+    runs = [(name, case, threads, 0) for name, case in cases.items()]
+    runs.append(("hist_u8_512_threads", cases["hist_u8"], 512, 0))
+    # the float32 FFMA path of the GEMM tile (what split row blocks and two
+    # CTAs per SM run), at the same size
+    runs.append(("gemm64_f32_ffma", cases["gemm64_f32"], threads, lk.LK_INIT_GEMM_FFMA))
     res = {}
-    for name, (op, cnt, a, b, o, nbytes), t_cta in runs:
+    for name, (op, cnt, a, b, o, nbytes), t_cta, fl in runs:
         ms = []
         for _ in range(reps):
             t, _log = lk.lk_run_finite([n_sms], [(op, cnt)] * per_launch, [0] * per_launch,
                                        in0=[a] * per_launch, in1=[b] * per_launch if b is not None else None,
-                                       out=[o] * per_launch, threads_per_cta=t_cta, exec_log_cap=per_launch + 1)
+                                       out=[o] * per_launch, threads_per_cta=t_cta, exec_log_cap=per_launch + 1,
+                                       flags=fl)
             ms.append(t)
         avg = float(np.mean(ms))
         torch.cuda.synchronize()
@@ -534,7 +538,7 @@ def body_bandwidth(pools, lk, n_sms: int, reps: int = 5, per_launch: int = 3, th
             raise RuntimeError(f"body bandwidth leg {name}: {chk['mismatches']} mismatches against the oracle")
         res[name] = {"gbs": nbytes * per_launch / (avg * 1e-3) / 1e9, "launch_ms": avg, "bytes_per_launch":
                      nbytes * per_launch, "descriptors_per_launch": per_launch, "threads_per_cta": t_cta,
-                     "parity": chk}
+                     "parity": chk, "flags": fl}
         if op == lk.LK_OP_GEMM64_F32:
             res[name]["tflops"] = 524288.0 * cnt * per_launch / (avg * 1e-3) / 1e12
     return res

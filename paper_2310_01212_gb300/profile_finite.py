@@ -6,6 +6,7 @@ replay it.  The inputs are allocated here and sized by --log2n, so that a
 capture stays small (a few GB on the device at most).
 
   python -m paper_2310_01212_gb300.profile_finite --op add_i32 --log2n 26 [--sms N] [--threads 256] [--launches 1]
+                                                  [--ffma]   (GEMM tiles on the FFMA path)
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ def main():
     ap.add_argument("--threads", type=int, default=256)
     ap.add_argument("--per-launch", type=int, default=1, help="descriptors per launch")
     ap.add_argument("--launches", type=int, default=1)
+    ap.add_argument("--ffma", action="store_true", help="LK_INIT_GEMM_FFMA: GEMM tiles on the FFMA path")
     args = ap.parse_args()
 
     import torch
@@ -59,7 +61,7 @@ def main():
         ms, _log = lk.lk_run_finite([sms], [(op, cnt)] * k, [0] * k, in0=[in0] * k if in0 is not None else None,
                                     in1=[in1] * k if in1 is not None else None,
                                     out=[out] * k if out is not None else None, threads_per_cta=args.threads,
-                                    exec_log_cap=k + 1)
+                                    exec_log_cap=k + 1, flags=lk.LK_INIT_GEMM_FFMA if args.ffma else 0)
         print(f"{args.op} n=2^{args.log2n} x{k} on {sms} SMs, {args.threads} threads: {ms:.4f} ms")
 
 

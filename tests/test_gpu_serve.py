@@ -94,7 +94,12 @@ def test_each_result_same_alone_and_in_the_mix(served):
             one["out"] = alone_out.data_ptr()
             rc1, r1 = lk.lk_serve(c, one, n_producers=1, budget_bytes=1 << 30, arena=arena, arena_bytes=arena.numel(),
                                   **kw)
-            assert rc1 == lk.LK_OK and r1["chunks"][0] == res["chunks"][i]
+            assert rc1 == lk.LK_OK
+            # the split is fixed per request for sums (their float result
+            # depends on it) and in the host dispatcher's modes; the queue
+            # spreads other ops over idle CTAs, which cannot change them
+            if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32 or kw["mode"] == lk.LK_SERVE_CHUNKS:
+                assert r1["chunks"][0] == res["chunks"][i]
             a, m = host(alone_out), host(outs[i])
             if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32:
                 a, m = a[:1], m[:1]   # the result; the rest of the 16-byte slot is padding
