@@ -594,7 +594,7 @@ def main():
 
     # ---- timed region: K steps of (boot, trace, dispose) ---------------------------
     sizes = cfg["sizes"]
-    lat, lat_arr, kernel_ms, dev_us = [], [], [], []
+    lat, lat_arr, kernel_ms, dev_us, sub_ms, step_of = [], [], [], [], [], []
     clocks = ClockSampler(dev)
     log_verdict = None
     for s in range(args.warmup + args.steps):
@@ -628,6 +628,8 @@ def main():
         ctx.dispose()
         if timed:
             lat.append((res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0)
+            sub_ms.append(res["t_submit_ns"] / 1e6)
+            step_of.append(np.full(res.size, s - args.warmup))
             lat_arr.append((res["t_complete_ns"] - traces[s][0]["t_arrival_ns"]) / 1000.0)
             kernel_ms.append(ctx.kernel_ms)
     torch.cuda.synchronize()
@@ -636,6 +638,8 @@ def main():
     lat = np.concatenate(lat)
     lat_arr = np.concatenate(lat_arr)
     dev_us = np.concatenate(dev_us)
+    sub_ms = np.concatenate(sub_ms)
+    step_of = np.concatenate(step_of)
     op_all = np.concatenate([traces[s][0]["op"] for s in range(args.warmup, args.warmup + args.steps)])
 
     # ---- parity: a seeded sample of the last step's items against the oracle -------
@@ -670,7 +674,8 @@ def main():
     top_base = np.argsort(base)[::-1][:10]
     nan2none = lambda x: None if not np.isfinite(x) else round(float(x), 2)
     tail = {"lk_top10": [{"us": round(float(lat[i]), 2), "device_pick_to_done_us": nan2none(dev_us[i]),
-                          "op": lk.OP_NAMES.get(int(op_all[i]), str(int(op_all[i])))} for i in top_lk],
+                          "op": lk.OP_NAMES.get(int(op_all[i]), str(int(op_all[i]))),
+                          "step": int(step_of[i]), "submit_ms": round(float(sub_ms[i]), 3)} for i in top_lk],
             "launch_sync_top10": [{"us": round(float(base[i]), 2),
                                    "op": lk.OP_NAMES.get(int(op_all[i]), str(int(op_all[i])))} for i in top_base],
             "lk_items_over_25us": int(np.sum(lat > 25.0)), "launch_sync_items_over_25us": int(np.sum(base > 25.0)),

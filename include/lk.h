@@ -365,14 +365,14 @@ typedef struct {
 } lk_serve_params;
 
 /* How LK_SERVE_QUEUE splits a request of B input bytes into units (at most
- * LK_SERVE_MAX_PARTS = 1024): at least ceil(B / part_bytes); a sum (whose
- * float result depends on its split) exactly
- *   max(ceil(B / part_bytes), min(32, ceil(B / min_part_bytes))),
- * any other op as many as max(ceil(B / part_bytes), min(idle, ceil(B /
- * min_part_bytes))), where idle = serving CTAs minus the units published and
- * not finished when it is admitted (their results do not depend on the
- * split), so a request spreads over the CTAs that are free. */
-#define LK_SERVE_SUM_WIDTH 32
+ * 1024): at least ceil(B / part_bytes); a sum (whose float result depends
+ * on its split) exactly
+ *   max(ceil(B / part_bytes), min(S, ceil(B / min_part_bytes))),
+ * S = the context's CTAs, so it is the same whatever else is served; any
+ * other op as many as max(ceil(B / part_bytes), min(idle, ceil(B /
+ * min_part_bytes))), where idle = S minus the units of admitted, unfinished
+ * requests when it is admitted (their results do not depend on the split),
+ * so a request spreads over the CTAs that are free. */
 
 /* Device bytes the queue's state takes at the start of the arena
  * (LK_SERVE_QUEUE) for `max_inflight` request slots (0 -> 4096). */

@@ -69,9 +69,9 @@ __device__ __forceinline__ bool tags_match(const uint64_t* w, uint64_t tag) {
 /* One probe of a ring slot: three vector loads in flight together, the last
  * an acquire.  When every tag is current, that acquire load has read a word
  * the host stored after its release fence, so it synchronises with the
- * host's post; the fence the caller issues next is then nearly free
- * (measured on GB300: a system-scope fence after relaxed system-scope loads
- * cost 0.48 us of a host round trip, after an acquire load nothing). */
+ * host's post and no system-scope fence is needed (measured on GB300: a
+ * system-scope fence after relaxed system-scope loads cost 0.48 us of a
+ * host round trip; an acquire load in the probe, nothing). */
 __device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
   ld_relaxed_sys_v2(&s->w[0], w[0], w[1]);
   ld_relaxed_sys_v2(&s->w[2], w[2], w[3]);
@@ -86,9 +86,9 @@ __device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
  * successful probe pairs with the host's release fence before its stores.
  * Each probe also loads *pre (device memory, relaxed, in flight beside the
  * probe, so it costs no extra time) into *pre_val: the completion word the
- * caller gates on next, read while it waits anyway; the same fence makes
- * that load an acquire.  Returns 0 or an LK_DERR_* reason (lease ran out,
- * abort). */
+ * caller gates on next, read while it waits anyway; the GPU-scope fence
+ * after success makes that load an acquire.  Returns 0 or an LK_DERR_*
+ * reason (lease ran out, abort). */
 __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, uint64_t tag, uint64_t seq,
                                            lk_slot& out, const uint64_t* pre, uint64_t* pre_val) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
@@ -100,8 +100,10 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, 
     uint64_t pv;
     asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(pv) : "l"(pre) : "memory");
     probe(s, w);
-    *pre_val = pv;
-    if (tags_match(w, tag)) break;
+    if (tags_match(w, tag)) {
+      *pre_val = pv;
+      break;
+    }
     if ((it & 63) == 0) {
       if (abort_v) return LK_DERR_ABORT;
       const uint64_t now = gtime();
@@ -115,7 +117,10 @@ __device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, 
     }
     bo.pause();
   }
-  fence_acq_rel_sys();
+  /* the probe's acquire load synchronised with the host's post; this
+   * GPU-scope fence orders the prefetched completion word (a relaxed load)
+   * before everything this CTA does next, the relay included */
+  fence_acq_rel_gpu();
   lk_wire_decode(w, seq, &out);
   return 0;
 }
@@ -604,6 +609,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   __shared__ int32_t s_cl, s_rank, s_size, s_exit, s_err;
   __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag (mailbox mode) */
   __shared__ int32_t s_last;           /* this CTA arrived last on the descriptor's slot */
+  __shared__ uint64_t s_slot_seen;     /* the slot's completion word, read while probing */
   __shared__ float s_red[32];
   __shared__ __align__(8) uint64_t s_bars[LK_ALL_BARS];
   __shared__ uint64_t s_tstart;
@@ -720,13 +726,13 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       /* slot k mod D (relay copy, partials, histogram accumulator, arrival
        * counter) is free once descriptor k+1-D, its previous user, finished */
       const uint64_t need = k + 1 > LK_BCAST_DEPTH ? k + 1 - LK_BCAST_DEPTH : 0;
-      uint64_t slot_seen = 0;
+      s_slot_seen = 0;   /* shared, not local: the probe functions are out of line */
       if (master && mailbox) {
         err = take_from_mailbox(a, c, k, dsc);
         if (!err) dsc.t_pick = gtime();
-        slot_seen = known_done;   /* the mailbox master completes each descriptor itself */
+        s_slot_seen = known_done;   /* the mailbox master completes each descriptor itself */
       } else if (!relay || master) {
-        err = take_from_ring(a, w, tag, k + 1, dsc, &dc->slot_done[slot], &slot_seen);
+        err = take_from_ring(a, w, tag, k + 1, dsc, &dc->slot_done[slot], &s_slot_seen);
         if (!err) dsc.t_pick = gtime();
       } else {
         err = take_from_relay(a, dc, &dc->relay[slot], k, dsc);
@@ -737,7 +743,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
        * the master wrote it), or, with LK_INIT_DIRECT, every CTA for itself
        * (EXIT uses no slot there). */
       const bool self_gate = relay ? master : (!err && dsc.cmd != LK_CMD_EXIT);
-      if (!err && self_gate && need && slot_seen < need) {
+      if (!err && self_gate && need && s_slot_seen < need) {
         const int ww = wait_word(a, &dc->slot_done[slot], need, false);
         err = ww < 0 ? LK_DERR_STALL : ww;
       }

@@ -1110,7 +1110,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
                                                 LK_SERVE_MAX_PARTS);
     q.wide_parts = (uint32_t)std::min<uint64_t>((q.in_bytes + min_part - 1) / min_part, LK_SERVE_MAX_PARTS);
     if (r.op == LK_OP_GEMM64_F32) q.wide_parts = (uint32_t)std::min<uint64_t>(q.wide_parts, r.n);   /* whole tiles */
-    q.parts = r.op == LK_OP_SUM_F32 ? std::max(q.base_parts, std::min<uint32_t>(LK_SERVE_SUM_WIDTH, q.wide_parts))
+    q.parts = r.op == LK_OP_SUM_F32 ? std::max(q.base_parts, std::min<uint32_t>((uint32_t)ctx->total, q.wide_parts))
                                     : q.base_parts;
     q.arena_out = r.out == nullptr;
     q.held = q.in_bytes + q.out_bytes;

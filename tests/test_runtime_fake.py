@@ -716,7 +716,7 @@ def test_queue_serves_every_request_with_its_units(fake_env):
 
 
 def test_queue_split_rule(fake_env):
-    """A sum gets exactly max(ceil(B / part), min(32, ceil(B / min_part)))
+    """A sum gets exactly max(ceil(B / part), min(CTAs, ceil(B / min_part)))
     units, whatever else runs; another op spreads over the idle CTAs (here
     all six, nothing else is admitted at once), never below ceil(B / part)."""
     with ctx_(sizes=(2, 2, 2)) as c:
@@ -727,10 +727,10 @@ def test_queue_split_rule(fake_env):
         rc, res = _serve_q(c, reqs, part_bytes=4 << 20, min_part_bytes=64 << 10)
         assert rc == lk.LK_OK
         got = res["chunks"].tolist()
-        # sums: 4 KiB -> 1; 1 MiB -> min(32, 16) = 16; 36 MiB -> max(9, 32) = 32
+        # sums (6 CTAs): 4 KiB -> 1; 1 MiB -> min(6, 16) = 6; 36 MiB -> max(9, 6) = 9
         # copy 1 MiB -> min(6 idle, 16) = 6; copy 36 MiB -> max(9, min(6, ...)) = 9
         # hist 1 MiB -> 6; gemm 3 tiles (96 KiB) -> min(6, 2, 3 tiles) = 2
-        assert got == [1, 16, 32, 6, 9, 6, 2], got
+        assert got == [1, 6, 9, 6, 9, 6, 2], got
 
 
 def test_queue_serves_twice_and_empty(fake_env):
