@@ -308,7 +308,7 @@ def build_headline(d: dict, hbm: float) -> dict:
                        "ring_1sm": rnd1(d["paper_mailbox_vs_ring"]["ring_1sm_nop_us"]["p50"])},
         "floor_over_nop_p50": round(d["pingpong_floor_us"]["p50"] / nop["lk"]["p50"], 3),
         "nop_device_p50_us": {k[:-3]: rnd1(v["p50"]) for k, v in nop["lk_device_phases"].items()
-                              if k.endswith("_us")},
+                              if k.endswith("_us") and "p50" in v},
         "tail": {"lk_max_item": d["tail_attribution"]["lk_top10"][0],
                  "lk_device_pick_to_done_max_us": rnd1(d["tail_attribution"]["lk_device_pick_to_done_us"]["max"]),
                  "items_over_25us_lk_vs_launch_sync": [d["tail_attribution"]["lk_items_over_25us"],
@@ -344,8 +344,11 @@ def item_device_us(items, log) -> np.ndarray:
     out = np.full(items.size, np.nan)
     key = log["cluster"].astype(np.int64) << 40 | log["seq"].astype(np.int64)
     last = log["t_done_ns"] > 0
-    dmap = dict(zip(key[last].tolist(), (log["t_done_ns"][last].astype(np.int64)
-                                          - log["t_pick_ns"][last].astype(np.int64)).tolist()))
+    # first pickup of each descriptor (the master's, when it relays)
+    uk, inv = np.unique(key, return_inverse=True)
+    first = np.full(uk.size, np.iinfo(np.int64).max, np.int64)
+    np.minimum.at(first, inv, log["t_pick_ns"].astype(np.int64))
+    dmap = dict(zip(key[last].tolist(), (log["t_done_ns"][last].astype(np.int64) - first[inv[last]]).tolist()))
     for c in np.unique(items["cluster"]):
         idx = np.nonzero(items["cluster"] == c)[0]
         idx = idx[np.argsort(items["t_arrival_ns"][idx], kind="stable")]
@@ -363,11 +366,12 @@ def exec_log_phases(log) -> dict:
     and p99 in us over the descriptors."""
     key = log["cluster"].astype(np.int64) << 40 | log["seq"].astype(np.int64)
     uk, inv = np.unique(key, return_inverse=True)
-    pick = np.zeros(uk.size, np.int64)
+    pick = np.full(uk.size, np.iinfo(np.int64).max, np.int64)
     start = np.zeros(uk.size, np.int64)
     end = np.zeros(uk.size, np.int64)
     done = np.zeros(uk.size, np.int64)
-    pick[inv] = log["t_pick_ns"].astype(np.int64)
+    # the descriptor's first pickup (the master's, when it relays)
+    np.minimum.at(pick, inv, log["t_pick_ns"].astype(np.int64))
     np.maximum.at(start, inv, log["t_start_ns"].astype(np.int64))
     np.maximum.at(end, inv, log["t_end_ns"].astype(np.int64))
     np.maximum.at(done, inv, log["t_done_ns"].astype(np.int64))
@@ -377,16 +381,17 @@ def exec_log_phases(log) -> dict:
                     ("last_end_to_done", done - end), ("pick_to_done", done - pick)):
         v = v[ok] / 1000.0
         out[name + "_us"] = {"p50": pct(v, 0.5), "p99": pct(v, 0.99)}
-    # per CTA: median of its own start - pick (who is late to see the relay)
+    # per CTA: median of its own pickup - the descriptor's first pickup
+    # (how late each CTA sees the relay, or the host's post with LK_INIT_DIRECT)
     rk = log["cluster"].astype(np.int64) << 20 | log["rank"].astype(np.int64)
     per = {}
-    d = (log["t_start_ns"].astype(np.int64) - log["t_pick_ns"].astype(np.int64)) / 1000.0
+    d = (log["t_pick_ns"].astype(np.int64) - pick[inv]) / 1000.0
     for key in np.unique(rk):
         m = rk == key
         per[int(key)] = (float(np.median(d[m])), int(log["smid"][m][0]), int(key & 0xfffff))
     meds = np.array([v[0] for v in per.values()])
     worst = sorted(per.values(), reverse=True)[:5]
-    out["per_cta_pick_to_start_us"] = {"min": float(meds.min()), "p50": float(np.median(meds)),
+    out["per_cta_first_pick_to_own_pick_us"] = {"min": float(meds.min()), "p50": float(np.median(meds)),
                                        "max": float(meds.max()),
                                        "worst5_us_smid_rank": [[round(a, 3), b, c] for a, b, c in worst]}
     return out

@@ -199,7 +199,8 @@ typedef struct {
   uint32_t smid;       /* %smid read by the CTA when it wrote this record          */
   uint32_t op;         /* the operation it ran                                     */
   uint64_t order;      /* how many descriptors this CTA ran before this one        */
-  uint64_t t_pick_ns;  /* %globaltimer: master took the descriptor from the ring   */
+  uint64_t t_pick_ns;  /* %globaltimer: this CTA took the descriptor (from the     */
+                       /* ring or mailbox, or a relayed member from the relay)    */
   uint64_t t_start_ns; /* %globaltimer: this CTA started its share                 */
   uint64_t t_end_ns;   /* %globaltimer: this CTA finished its share                */
   uint64_t t_done_ns;  /* %globaltimer of the completion store if this CTA was the */

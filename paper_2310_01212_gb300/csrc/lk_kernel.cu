@@ -193,9 +193,10 @@ __device__ __noinline__ int take_from_mailbox(const lk_kargs& a, int c, uint64_t
 
 /* Relay (the default delivery): the master copies descriptor k into relay slot
  * k mod D as six lap-tagged words (the host ring's format, tag = relay lap),
- * after the acquire-release fence that followed its ring probe, so members
- * need no separate generation word: they probe the slot in L2 (one round
- * trip) and issue a GPU-scope acquire fence when every tag is current. */
+ * after the fence that followed its ring probe, so members need no separate
+ * generation word: they probe the slot in L2 (one round trip, the last load
+ * an acquire) and accept it when every tag is current.  No timestamp rides
+ * in the slot: reading %globaltimer is slow, so no store waits on one. */
 __device__ __forceinline__ void relay_publish(lk_wire* rs, uint64_t k, const lk_slot& d) {
   const uint64_t tag = ((k / LK_BCAST_DEPTH + 1) & 0xffffull) << LK_TAG_SHIFT;
   const uint64_t v[6] = {tag | ((uint64_t)(d.flags & 0xffffu) << 16) | (d.cmd & 0xffffu), tag | (d.n & LK_LOW48),
@@ -203,18 +204,15 @@ __device__ __forceinline__ void relay_publish(lk_wire* rs, uint64_t k, const lk_
                          tag | (d.aux & LK_LOW48)};
 #pragma unroll
   for (int i = 0; i < 6; ++i) asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[i]), "l"(v[i]) : "memory");
-  /* the pickup time (for the execution log), tagged too: its low 48 bits */
-  asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&rs->w[6]), "l"(tag | (d.t_pick & LK_LOW48)) : "memory");
 }
 
-/* One probe of a relay slot: four vector loads, the last an acquire (when
+/* One probe of a relay slot: three vector loads, the last an acquire (when
  * every tag is current it read a word the master stored after its fence,
  * so it synchronises with the master; no separate fence follows). */
 __device__ __forceinline__ void relay_probe(const lk_wire* rs, uint64_t* w) {
   asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(&rs->w[0]) : "memory");
   asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[2]), "=l"(w[3]) : "l"(&rs->w[2]) : "memory");
-  asm volatile("ld.relaxed.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
-  asm volatile("ld.acquire.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[6]), "=l"(w[7]) : "l"(&rs->w[6]) : "memory");
+  asm volatile("ld.acquire.gpu.v2.u64 {%0, %1}, [%2];" : "=l"(w[4]), "=l"(w[5]) : "l"(&rs->w[4]) : "memory");
 }
 
 /* A relayed member waits for descriptor k in relay slot rs (L2).  One probe
@@ -231,10 +229,10 @@ __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster
   uint64_t t_last = gtime();
   const uint64_t limit = a.lease_ns + 1000000000ull;
   uint64_t abort_v = 0, gen_v = 0, hb_v = hb;
-  uint64_t w[8];
+  uint64_t w[6];
   for (uint32_t it = 1;; ++it) {
     relay_probe(rs, w);
-    if (tags_match(w, tag) && (w[6] >> LK_TAG_SHIFT) == tag) break;
+    if (tags_match(w, tag)) break;
     if ((it & 127) == 0) {
       /* act on the words loaded one check ago, then load them again */
       if (abort_v) return LK_DERR_ABORT;
@@ -252,11 +250,6 @@ __device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster
     bo.pause();
   }
   lk_wire_decode(w, k + 1, &out);
-  /* the master's pickup time: its low 48 bits under this reader's high bits */
-  const uint64_t now = gtime();
-  uint64_t tp = (now & ~LK_LOW48) | (w[6] & LK_LOW48);
-  if (tp > now) tp -= (1ull << 48);
-  out.t_pick = tp;
   return 0;
 }
 
@@ -610,9 +603,9 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
   __shared__ volatile int s_found;     /* rank 0: a warp saw every rank's flag (mailbox mode) */
   __shared__ int32_t s_last;           /* this CTA arrived last on the descriptor's slot */
   __shared__ uint64_t s_slot_seen;     /* the slot's completion word, read while probing */
+  __shared__ uint64_t s_tpick, s_tstart; /* thread 0's stamps, for the execution log */
   __shared__ float s_red[32];
   __shared__ __align__(8) uint64_t s_bars[LK_ALL_BARS];
-  __shared__ uint64_t s_tstart;
   const uint32_t tid = threadIdx.x;
 
   /* ---- boot: read %smid, exchange, join a cluster --------------------- */
@@ -729,14 +722,13 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       s_slot_seen = 0;   /* shared, not local: the probe functions are out of line */
       if (master && mailbox) {
         err = take_from_mailbox(a, c, k, dsc);
-        if (!err) dsc.t_pick = gtime();
         s_slot_seen = known_done;   /* the mailbox master completes each descriptor itself */
       } else if (!relay || master) {
         err = take_from_ring(a, w, tag, k + 1, dsc, &dc->slot_done[slot], &s_slot_seen);
-        if (!err) dsc.t_pick = gtime();
       } else {
         err = take_from_relay(a, dc, &dc->relay[slot], k, dsc);
       }
+      const uint64_t t_pick = gtime();   /* read now, stored below (the read is slow) */
       /* Who gates: the CTA that reads the ring or mailbox for the cluster --
        * the master, which relays descriptor k only once slot k mod D is free
        * (so a relayed member needs no check: the slot it reads was free when
@@ -775,6 +767,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       s_err = 0;
       s_found = 0;
       s_last = 0;
+      s_tpick = t_pick;
       s_tstart = gtime();
     }
     __syncthreads();
@@ -865,7 +858,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       rec->smid = smid();
       rec->op = op;
       rec->order = k;
-      rec->t_pick_ns = d.t_pick;
+      rec->t_pick_ns = s_tpick;
       rec->t_start_ns = s_tstart;
       rec->t_end_ns = t_end;
       rec->t_done_ns = t_done;
