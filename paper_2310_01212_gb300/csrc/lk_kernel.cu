@@ -89,8 +89,8 @@ __device__ __forceinline__ void probe(const lk_wire* s, uint64_t* w) {
  * caller gates on next, read while it waits anyway; the GPU-scope fence
  * after success makes that load an acquire.  Returns 0 or an LK_DERR_*
  * reason (lease ran out, abort). */
-__device__ __noinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, uint64_t tag, uint64_t seq,
-                                           lk_slot& out, const uint64_t* pre, uint64_t* pre_val) {
+__device__ __forceinline__ int take_from_ring(const lk_kargs& a, const lk_wire* s, uint64_t tag, uint64_t seq,
+                                              lk_slot& out, const uint64_t* pre, uint64_t* pre_val) {
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
   uint64_t t_last = gtime();
@@ -221,8 +221,8 @@ __device__ __forceinline__ void relay_probe(const lk_wire* rs, uint64_t* w) {
  * (abort word, master stop, lease) read their words without waiting on
  * them: each check uses the values loaded at the previous one.  Returns 0,
  * -1 (the master stopped) or an LK_DERR_* reason. */
-__device__ __noinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster* dc, const lk_wire* rs, uint64_t k,
-                                            lk_slot& out) {
+__device__ __forceinline__ int take_from_relay(const lk_kargs& a, const lk_dcluster* dc, const lk_wire* rs, uint64_t k,
+                                               lk_slot& out) {
   const uint64_t tag = (k / LK_BCAST_DEPTH + 1) & 0xffffull;
   Backoff bo(a.backoff_base_ns, a.backoff_cap_ns);
   uint64_t hb = ld_relaxed_sys(&a.ctrl->heartbeat);
