@@ -359,6 +359,18 @@ def item_device_us(items, log) -> np.ndarray:
     return out
 
 
+def e2e_parts(res) -> dict:
+    """Split end-to-end trace latencies into copy in / dispatch / copy out."""
+    cin = (res["t_post_ns"].astype(np.int64) - res["t_submit_ns"].astype(np.int64)) / 1000.0
+    dis = (res["t_observed_ns"].astype(np.int64) - res["t_post_ns"].astype(np.int64)) / 1000.0
+    cout = (res["t_complete_ns"].astype(np.int64) - res["t_observed_ns"].astype(np.int64)) / 1000.0
+    tot = (res["t_complete_ns"].astype(np.int64) - res["t_submit_ns"].astype(np.int64)) / 1000.0
+    top = np.argsort(tot)[::-1][: max(1, tot.size // 100)]   # the slowest 1 %: where their time went
+    return {"copy_in": lat_summary(cin), "dispatch": lat_summary(dis), "copy_out": lat_summary(cout),
+            "slowest_1pct_mean": {"copy_in": float(np.mean(cin[top])), "dispatch": float(np.mean(dis[top])),
+                                  "copy_out": float(np.mean(cout[top]))}}
+
+
 def exec_log_phases(log) -> dict:
     """Per descriptor, from one context's execution log (device %globaltimer,
     32 ns ticks): pick -> last CTA start (relay), last start -> last end
@@ -1080,7 +1092,10 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"latency_us": lat_summary(e2e), "launch_sync_e2e_us": lat_summary(e2e_base),
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy"},
+                "parts_us": {"lk": e2e_parts(re), "launch_sync": e2e_parts(rb)},
+                "how": "per item: pinned host->device input copies, lk submit, wait, device->host output copy; "
+                       "parts: copy in (submit -> post), dispatch (post -> completion observed), copy out "
+                       "(observed -> complete), host clock"},
         "paper_phases": phases,
         "batching": batching,
         "serving": serving,
@@ -1105,7 +1120,9 @@ def main():
                      if k in ("bound", "achieved", "peak", "unit", "frac", "traffic")},
         "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None,
         "e2e": {"value": pct(e2e, 0.99), "unit": "us", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "launch_sync_p99": rnd1(pct(e2e_base, 0.99))},
+                "launch_sync_p99": rnd1(pct(e2e_base, 0.99)),
+                "p99_copy_in_dispatch_copy_out_us": [rnd1(detail["e2e"]["parts_us"]["lk"][k]["p99"])
+                                                     for k in ("copy_in", "dispatch", "copy_out")]},
         "gpu_launches": args.steps,
         "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "detail_file": os.path.basename(args.detail),

@@ -502,7 +502,11 @@ typedef struct {
                           /* copy finished)                                          */
   int32_t status;         /* LK_OK or the error the item hit                        */
   int32_t thread;         /* host thread that handled it                            */
-} lk_trace_result;
+  uint64_t t_post_ns;     /* the work was posted or launched (E2E: after the input  */
+                          /* copy)                                                  */
+  uint64_t t_observed_ns; /* its completion was observed (E2E: before the output    */
+                          /* copy); E2E latency = copy in + dispatch + copy out     */
+} lk_trace_result;        /* 40 bytes */
 
 #define LK_TRACE_OPEN   0  /* release on arrival; several items in flight per cluster */
 #define LK_TRACE_CLOSED 1  /* a thread releases its next item after the previous one finished */

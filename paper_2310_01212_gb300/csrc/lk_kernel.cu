@@ -1246,7 +1246,7 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
     if (ctas_of_slot[s] < 1 || ctas_of_slot[s] > LK_MAX_CTAS) return LK_EINVAL;
   for (size_t i = 0; i < count; ++i) {
     if (items[i].cluster < 0 || items[i].cluster >= n_slots || items[i].op >= LK_OP_COUNT) return LK_EINVAL;
-    res[i] = lk_trace_result{0, 0, LK_PENDING, -1};
+    res[i] = lk_trace_result{0, 0, LK_PENDING, -1, 0, 0};
   }
   if (cudaSetDevice(device) != cudaSuccess) return LK_EDEVICE;
   preload_all();
@@ -1297,8 +1297,10 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
             e = cudaMemcpyAsync((void*)it.in1, it.h_in1, it.in1_bytes, cudaMemcpyHostToDevice, st[s]);
           if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
         }
+        const uint64_t tp = now_ns();
         if (e == cudaSuccess) e = launch_ordinary(d, ctas_of_slot[s], threads, sc[s], st[s]);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
+        const uint64_t to = now_ns();
         if (e == cudaSuccess && e2e && it.out_bytes && it.h_out) {
           e = cudaMemcpyAsync(it.h_out, it.out, it.out_bytes, cudaMemcpyDeviceToHost, st[s]);
           if (e == cudaSuccess) e = cudaStreamSynchronize(st[s]);
@@ -1306,6 +1308,8 @@ extern "C" int lk_baseline_run_trace(int device, const lk_trace_item* items, siz
         const uint64_t tc = now_ns();
         res[i].t_submit_ns = ts - t0;
         res[i].t_complete_ns = tc - t0;
+        res[i].t_post_ns = tp - t0;
+        res[i].t_observed_ns = to - t0;
         res[i].thread = w;
         res[i].status = e == cudaSuccess ? LK_OK : LK_EDEVICE;
         if (e != cudaSuccess) {

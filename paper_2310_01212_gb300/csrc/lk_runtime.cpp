@@ -876,7 +876,7 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
     lk_desc d{it.op, 0, it.n, 0};
     int rc = validate(&d, it.in0, it.in1, op_inputs(it.op), it.out);
     if (rc != LK_OK) return rc;
-    res[i] = lk_trace_result{0, 0, LK_PENDING, -1};
+    res[i] = lk_trace_result{0, 0, LK_PENDING, -1, 0, 0};
   }
   if (!ctx_alive(ctx)) return LK_ESTATE;
   /* per thread: its items in arrival order */
@@ -938,6 +938,7 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
         while (rc == LK_EAGAIN && e2e) rc = post(ctx, it.cluster, LK_CMD_WORK + it.op, &d, it.in0, it.in1, it.out, &seq);
         if (rc == LK_OK) {
           res[v[next]].t_submit_ns = ts - t0;
+          res[v[next]].t_post_ns = now_ns() - t0;
           res[v[next]].thread = w;
           pend[it.cluster].push_back({seq, v[next]});
           ++next;
@@ -968,6 +969,7 @@ int lk_run_trace(lk_ctx* ctx, const lk_trace_item* items, size_t count, int n_th
         while (head[c] < pq.size() && pq[head[c]].first <= done) {
           const size_t idx = pq[head[c]].second;
           int st = LK_OK;
+          res[idx].t_observed_ns = tc;
           if (e2e && items[idx].out_bytes && items[idx].h_out) {
             /* Copyout (Sec. III) */
             st = lkb_memcpy_async(stream, items[idx].h_out, items[idx].out, items[idx].out_bytes, 0);

@@ -102,8 +102,8 @@ TRACE_ITEM_DTYPE = np.dtype([("t_arrival_ns", "<u8"), ("cluster", "<i4"), ("op",
                              ("h_out", "<u8"), ("in0_bytes", "<u8"), ("in1_bytes", "<u8"), ("out_bytes", "<u8")])
 LK_TRACE_OPEN, LK_TRACE_CLOSED, LK_TRACE_E2E = 0, 1, 2
 TRACE_RES_DTYPE = np.dtype([("t_submit_ns", "<u8"), ("t_complete_ns", "<u8"), ("status", "<i4"),
-                            ("thread", "<i4")])
-assert TRACE_ITEM_DTYPE.itemsize == 96 and TRACE_RES_DTYPE.itemsize == 24
+                            ("thread", "<i4"), ("t_post_ns", "<u8"), ("t_observed_ns", "<u8")])
+assert TRACE_ITEM_DTYPE.itemsize == 96 and TRACE_RES_DTYPE.itemsize == 40
 
 # ---- library loading -------------------------------------------------------------
 _libs: dict = {}
