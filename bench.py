@@ -572,8 +572,9 @@ def main():
                     help="critical periods (1 ms each) of the disjoint-layout isolation run, alone and loaded")
     ap.add_argument("--iso-sweep-periods", type=int, default=2000,
                     help="critical periods of each co-resident and rate-capped isolation run")
-    ap.add_argument("--batch-items", type=int, default=100_000,
-                    help="descriptors of the batching stream's seeded prefix (whole batches)")
+    ap.add_argument("--batch-items", type=int, default=1_000_000,
+                    help="descriptors of the batching stream to run (whole batches; 1,000,000 = the whole "
+                         "stream, about 13.8 TB)")
     ap.add_argument("--graph-batches", type=int, default=8,
                     help="batches of that prefix also timed as CUDA graphs of ordinary launches")
     ap.add_argument("--detail", default="bench_detail.json",
@@ -878,8 +879,9 @@ def main():
                 "items_per_batch": [len(it) for it, _ in bbat],
                 "tuned": tuned, "cluster": f"{n_sms} SMs as one cluster",
                 "parity_mismatches": batch_bad, "parity_items": int(len(par_items)),
-                "sample": f"seeded prefix: {len(bbat)} batches ({all_count} descriptors) of the 1M-descriptor "
-                          f"stream, batch b+1 posted while batch b runs"}
+                "sample": f"{len(bbat)} batches ({all_count} descriptors) of the seeded 1M-descriptor stream "
+                          f"(the whole stream once the count reaches 1,000,000), batch b+1 posted while batch b "
+                          f"runs"}
 
     # ---- serving: continuous admission under open-loop arrivals, per rate ----------
     # the device-resident queue at every rate (the clusters' CTAs claim work
