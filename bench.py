@@ -302,6 +302,8 @@ def build_headline(d: dict, hbm: float) -> dict:
         "launch_sync_us_p50_p99_max": trio(d["baseline_launch_sync_us"]),
         "occupancy_grid_us_p50_p99_max": trio(d["baseline_occupancy_grid_us"]),
         "arrival_to_complete_us_p50_p99_max": trio(d["arrival_to_complete_us"]),
+        "by_op_us_p50_p99_max": {k: {"lk": v["lk"], "launch_sync": v["launch_sync"]}
+                                 for k, v in d.get("latency_by_op_us_p50_p99_max", {}).items()},
         "floor_p50_us": rnd1(d["pingpong_floor_us"]["p50"]),
         "nop_p50_us": {"relay": rnd1(nop["lk"]["p50"]), "direct": rnd1(nop["lk_direct"]["p50"]),
                        "mailbox": rnd1(nop["lk_mailbox"]["p50"]), "launch_sync": rnd1(nop["launch_sync"]["p50"]),
@@ -323,7 +325,10 @@ def build_headline(d: dict, hbm: float) -> dict:
                       "loaded_p999_us": rnd1(iso["loaded_us"]["p999"]),
                       "inflation_p999": round(iso["inflation_p999"], 2),
                       "inflation_max": round(iso["inflation_max"], 2),
-                      "cap_2tbs_inflation_p999": round(iso["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2)},
+                      "cap_2tbs_inflation_p999": round(iso["best_effort_rate_cap_gbs"]["2000"]["inflation_p999"], 2),
+                      "yield": {"inflation_p999": round(iso["best_effort_yield"]["inflation_p999"], 2),
+                                "best_effort_gbs": round(iso["best_effort_yield"]["best_effort_gbs"]),
+                                "unyielded_best_effort_gbs": round(iso["best_effort_gbs"])}},
         "batching_gbs": {"lk_prefix": round(bat["lk_gbs"]), "prefix_items": bat["items"],
                          "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
         "serving_saturation_gbs": {"device_queue": round(sat["throughput_gbs"]),
@@ -688,6 +693,15 @@ def main():
             raise RuntimeError(f"baseline failed: {lk.lk_strerror(rc)}")
         base.append((res["t_complete_ns"] - res["t_submit_ns"]) / 1000.0)
     base = np.concatenate(base)
+    # per body: which op sets the p99 (the device's own pick -> done beside it)
+    by_op = {}
+    for o in np.unique(op_all):
+        m = op_all == o
+        dv = dev_us[m][np.isfinite(dev_us[m])]
+        by_op[lk.OP_NAMES.get(int(o), str(int(o)))] = {
+            "lk": [rnd1(np.percentile(lat[m], q)) for q in (50, 99)] + [rnd1(lat[m].max())],
+            "launch_sync": [rnd1(np.percentile(base[m], q)) for q in (50, 99)] + [rnd1(base[m].max())],
+            "device_pick_to_done": [rnd1(np.percentile(dv, q)) for q in (50, 99)] if dv.size else None}
     top_lk = np.argsort(lat)[::-1][:10]
     top_base = np.argsort(base)[::-1][:10]
     nan2none = lambda x: None if not np.isfinite(x) else round(float(x), 2)
@@ -884,6 +898,7 @@ def main():
                           f"runs"}
 
     # ---- serving: continuous admission under open-loop arrivals, per rate ----------
+    hbm_serv = float(measured_peaks()[0].get("hbm_gbs", FALLBACK_HBM))
     # the device-resident queue at every rate (the clusters' CTAs claim work
     # units themselves); the host dispatcher (chunks posted per cluster) and
     # its coalesced variant at the top rates for comparison; unit sizes swept
@@ -928,6 +943,13 @@ def main():
                      "throughput_gbs": float(inb.sum()) / span / 1e9,
                      "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
                      "units_or_chunks": int(res["chunks"].sum())}
+            # the slowest requests, each against its own bytes at the measured HBM peak
+            top = np.argsort(lat_s)[::-1][:5]
+            out_b = np.where(reqs["op"] == lk.LK_OP_ADD_I32, inb / 2, np.where(reqs["op"] == lk.LK_OP_GEMM64_F32,
+                                                                             inb / 2, 0.0))
+            entry["slowest"] = [{"op": lk.OP_NAMES[int(reqs["op"][i])], "mb": rnd1((inb[i] + out_b[i]) / 1e6),
+                                 "units": int(res["chunks"][i]), "us": rnd1(lat_s[i]), "admit_us": rnd1(wait_s[i]),
+                                 "hbm_us": rnd1((inb[i] + out_b[i]) / (hbm_serv * 1e3))} for i in top]
             if where == "rates":
                 serving["rates"][str(rate)] = entry
             elif where == "part_bytes_sweep_top_rate":
@@ -944,9 +966,10 @@ def main():
     hist_in = pools.u8[: iso["hist_n"]]
     hist_out = torch.zeros(256, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
-    def iso_run(init_kw, periods, be_rate=0, alone=True):
+    def iso_run(init_kw, periods, be_rate=0, alone=True, roles=False):
         """`periods` critical periods alone, then under best-effort load, on one
-        layout; be_rate caps the best-effort cluster's loads (bytes/us, 0 = none)."""
+        layout; be_rate caps the best-effort cluster's loads (bytes/us, 0 = none);
+        roles makes cluster 0 critical and cluster 1 yield to it (lk_set_role)."""
         out = {"periods": periods}
         for loaded in ((False, True) if alone else (True,)):
             be_items = 0
@@ -964,6 +987,9 @@ def main():
             with lk.lk_init(init_kw["sizes"], device=dev, threads_per_cta=iso["threads"], idle_lease_ns=5_000_000_000,
                             **{k: v for k, v in init_kw.items() if k != "sizes"}) as ctx:
                 lk.lk_set_rate(ctx, 1, be_rate)
+                if roles:
+                    lk.lk_set_role(ctx, 0, lk.LK_ROLE_CRITICAL)
+                    lk.lk_set_role(ctx, 1, lk.LK_ROLE_YIELD)
                 rc, rr = lk.lk_run_trace(ctx, tr, n_threads=2, closed_loop=True, timeout_ns=600_000_000_000,
                                          pin_cpu_base=pin)
             if rc != lk.LK_OK:
@@ -1004,6 +1030,12 @@ def main():
         paced[str(cap_gbs)] = {"loaded_us": pr["loaded_us"], "best_effort_gbs": pr["best_effort_gbs"],
                                "inflation_p999": pr["loaded_us"]["p999"] / iso_res["alone_us"]["p999"],
                                "load_covered_critical_run": pr["load_covered_critical_run"]}
+    # load yielding: the best-effort cluster holds its loads while a critical
+    # descriptor runs (lk_set_role), instead of a standing cap
+    yr = iso_run({"sizes": iso["sizes"]}, args.iso_sweep_periods, alone=False, roles=True)
+    iso_res["best_effort_yield"] = {"loaded_us": yr["loaded_us"], "best_effort_gbs": yr["best_effort_gbs"],
+                                    "inflation_p999": yr["loaded_us"]["p999"] / iso_res["alone_us"]["p999"],
+                                    "load_covered_critical_run": yr["load_covered_critical_run"]}
     iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
     iso_res["inflation_max"] = iso_res["loaded_us"]["max"] / iso_res["alone_us"]["max"]
     iso_res["coresident"] = co
@@ -1078,6 +1110,7 @@ def main():
         "latency_us": lat_summary(lat),
         "arrival_to_complete_us": lat_summary(lat_arr),
         "baseline_launch_sync_us": lat_summary(base),
+        "latency_by_op_us_p50_p99_max": by_op,
         "tail_attribution": tail,
         "baseline_occupancy_grid_us": dict(lat_summary(base_occ), grid=occ_grid,
                                            note="one step's trace; grid from the occupancy API (1 CTA/SM x all SMs)"),

@@ -238,6 +238,21 @@ int lk_submit(lk_ctx* ctx, int cluster, const lk_desc* d, const void* const* in,
  * Errors: LK_EINVAL (ctx, cluster, rate). */
 int lk_set_rate(lk_ctx* ctx, int cluster, uint64_t bytes_per_us);
 
+/* Not in the paper: load yielding between clusters, for isolation.  While a
+ * cluster with role LK_ROLE_CRITICAL has a descriptor running (from its
+ * pickup to its last CTA's completion), every cluster with role
+ * LK_ROLE_YIELD stops issuing new input loads in its streaming bodies (add,
+ * copy, sum, histogram; the loads already in flight complete, and one wait
+ * lasts at most 1 ms), so a critical task meets less memory traffic while
+ * the yielding work keeps full speed in between.  Roles apply to
+ * descriptors posted after the call; a cluster may also keep a rate cap
+ * (lk_set_rate).  role: LK_ROLE_NONE, LK_ROLE_CRITICAL or LK_ROLE_YIELD.
+ * Errors: LK_EINVAL (ctx, cluster, role). */
+#define LK_ROLE_NONE     0
+#define LK_ROLE_CRITICAL 1
+#define LK_ROLE_YIELD    2
+int lk_set_role(lk_ctx* ctx, int cluster, int role);
+
 /* Wait (Sec. III), non-blocking: LK_OK if h finished, LK_PENDING if not.
  * Errors: LK_EINVAL (bad handle), LK_EDEVICE (the cluster stopped on a device
  * error before finishing h), LK_ESTATE (context gone before h finished). */

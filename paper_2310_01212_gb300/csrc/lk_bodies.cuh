@@ -87,6 +87,7 @@ struct SmemCfg {
 struct Pace {
   uint64_t deadline;
   uint64_t rate;
+  const int32_t* gate;   /* non-null: yield to critical descriptors (lk_set_role) */
 };
 
 /* Thread 0: sleep until `due` (%globaltimer ns); bounded by `due` itself. */
@@ -96,6 +97,40 @@ __device__ __forceinline__ void sleep_until(uint64_t due) {
     __nanosleep(left > 2000u ? 2000u : (uint32_t)left);
   }
 }
+
+/* Load yielding of one issuing thread (lk_set_role): before each refill of
+ * a stage it holds while the count of running critical descriptors is
+ * positive.  The count tested is the one loaded at the previous refill (the
+ * load's round trip overlaps the stage wait in between, so a refill never
+ * waits on L2 for it); one hold lasts at most LK_YIELD_HOLD_NS and a body's
+ * holds together at most LK_YIELD_BUDGET_NS, by which its stage deadline is
+ * extended.  The count is a hint: a stale value only shifts a hold by one
+ * stage. */
+#define LK_YIELD_HOLD_NS 1000000ull
+#define LK_YIELD_BUDGET_NS 8000000ull
+struct Yield {
+  const int32_t* gate;
+  int32_t seen;
+  uint64_t end;
+  __device__ __forceinline__ explicit Yield(const int32_t* g) : gate(g), seen(0), end(0) {
+    if (gate) {
+      end = gtime() + LK_YIELD_BUDGET_NS;
+      seen = ld_relaxed_gpu_s32(gate);
+    }
+  }
+  __device__ __forceinline__ void hold() {
+    if (!gate) return;
+    if (seen > 0) {
+      uint64_t now = gtime();
+      const uint64_t lim = now + LK_YIELD_HOLD_NS < end ? now + LK_YIELD_HOLD_NS : end;
+      while (now < lim && ld_relaxed_gpu_s32(gate) > 0) {
+        __nanosleep(256);
+        now = gtime();
+      }
+    }
+    seen = ld_relaxed_gpu_s32(gate);
+  }
+};
 
 /* Stream the 16-byte vectors [beg, end) of NIN inputs through the stages.
  * consume(v0, nv, s0, s1) runs on every thread for each chunk: vectors
@@ -114,8 +149,10 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
   const uint64_t nch = (total + stage_vec - 1) / stage_vec;
   if (nch == 0) return true;
   constexpr uint64_t chunk_bytes = (uint64_t)stage_vec * 16u * NIN;
-  const uint64_t deadline = pace.rate ? pace.deadline + total * 16u * NIN * 1000u / pace.rate : pace.deadline;
+  const uint64_t deadline = (pace.rate ? pace.deadline + total * 16u * NIN * 1000u / pace.rate : pace.deadline) +
+                            (pace.gate ? LK_YIELD_BUDGET_NS : 0u);
   const uint64_t t_first = pace.rate && threadIdx.x == 0 ? gtime() : 0;
+  Yield yield(threadIdx.x == 0 ? pace.gate : nullptr);
   auto sbuf = [&](uint32_t st, int which) {
     return reinterpret_cast<uint4*>(stage_mem + ((size_t)st * NIN + which) * stage_vec * 16u);
   };
@@ -134,6 +171,7 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
     if (NIN > 1) bulk_g2s(sbuf(st, 1), in1 + v0, nv * 16u, &bars[st]);
   };
   if (threadIdx.x == 0) {
+    yield.hold();
     fence_proxy_async_global();   /* earlier generic writes before these async reads */
     fence_proxy_async_smem();     /* earlier generic shared accesses before async writes */
     for (uint64_t ch = 0; ch < nch && ch < LK_STAGES; ++ch) issue(ch);
@@ -156,6 +194,7 @@ __device__ __forceinline__ bool stream(const uint4* in0, const uint4* in1, uint6
     /* every thread has finished chunk ch-1: refill its stage */
     if (threadIdx.x == 0 && ch >= 1 && ch - 1 + LK_STAGES < nch) {
       if (pace.rate) sleep_until(t_first + ch * chunk_bytes * 1000u / pace.rate);
+      yield.hold();
       if (STORE) bulk_wait_read_all();
       fence_proxy_async_smem();
       issue(ch - 1 + LK_STAGES);
@@ -446,8 +485,10 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
   const uint64_t nch = (total + stage_vec - 1) / stage_vec;
   /* the warp's rate: the CTA's, split evenly over its warps */
   const uint64_t rate = pace.rate ? (pace.rate / W ? pace.rate / W : 1) : 0;
-  const uint64_t deadline = rate ? pace.deadline + total * 16u * 1000u / rate : pace.deadline;
+  const uint64_t deadline =
+      (rate ? pace.deadline + total * 16u * 1000u / rate : pace.deadline) + (pace.gate ? LK_YIELD_BUDGET_NS : 0u);
   const uint64_t t_first = rate && lane == 0 ? gtime() : 0;
+  Yield yield(lane == 0 && nch ? pace.gate : nullptr);
   auto parity = [&](uint64_t ch) {
     return ((phase >> (LK_NUM_BARS + (uint32_t)(ch % LK_STAGES))) & 1u) ^ ((uint32_t)(ch / LK_STAGES) & 1u);
   };
@@ -463,6 +504,7 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
     bulk_g2s(ring + (size_t)st * stage_vec, in + v0, nv * 16u, &wb[st]);
   };
   if (lane == 0 && nch) {
+    yield.hold();
     fence_proxy_async_global();   /* earlier generic writes before these async reads */
     fence_proxy_async_smem();     /* earlier generic shared accesses before async writes */
     for (uint64_t ch = 0; ch < nch && ch < LK_STAGES; ++ch) issue(ch);
@@ -495,6 +537,7 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
       /* token bucket as deep as the ring: chunk k >= LK_STAGES no earlier
        * than t_first + (k - LK_STAGES + 1) chunks' worth of time */
       if (rate) sleep_until(t_first + (ch + 1) * (uint64_t)stage_vec * 16u * 1000u / rate);
+      yield.hold();
       fence_proxy_async_smem();
       issue(ch + LK_STAGES);
     }

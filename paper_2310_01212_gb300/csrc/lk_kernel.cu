@@ -362,9 +362,9 @@ __device__ __forceinline__ uint64_t cta_rate(uint64_t cluster_rate, int S) {
 template <int MAXT, int P>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
                                         uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc,
-                                        uint64_t rate, bool tc = true) {
+                                        uint64_t rate, const int32_t* gate, bool tc = true) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
-  const Pace deadline{gtime() + 2000000000ull, rate};
+  const Pace deadline{gtime() + 2000000000ull, rate, gate};
   bool ok = true;
   switch (op) {
     case LK_OP_ADD_I32: ok = body_add<P, (MAXT <= 256 && P == 1)>(d, r, S, dsm, bars, phase, deadline); break;
@@ -483,6 +483,7 @@ __device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, in
     nslots = __ldcg(&qs->nslots);
   }
   const uint64_t rate = serve ? 0 : cta_rate(d.aux, a.cl_start[c + 1] - a.cl_start[c]);
+  const int32_t* gate = (d.flags & LK_DFLAG_YIELD) ? a.crit_active : nullptr;
   for (;;) {
     if (threadIdx.x == 0) {
       uint64_t w[5] = {0, 0, 0, 0, 0};
@@ -549,7 +550,7 @@ __device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, in
     it.out = s_w[2];
     it.aux = 0;
     it.t_pick = 0;
-    const Pace deadline{gtime() + 2000000000ull, rate};
+    const Pace deadline{gtime() + 2000000000ull, rate, gate};
     bool ok = true;
     if (op == LK_OP_SUM_F32) {
       float* pout = parts > 1 ? s_psum + part : &s_part_sum;
@@ -557,7 +558,7 @@ __device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, in
     } else if (op == LK_OP_HIST_U8) {
       ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, parts > 1 ? s_pbins : my_hist);
     } else {
-      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate,
+      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate, gate,
                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0) == 0;
     }
     __syncthreads();
@@ -749,6 +750,10 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
           err = ww < 0 ? LK_DERR_STALL : ww;
         }
       }
+      /* a critical descriptor (lk_set_role) counts as running from here to
+       * its last CTA's completion; yielding clusters read the count */
+      if (!err && master && (dsc.flags & LK_DFLAG_CRITICAL) && dsc.cmd != LK_CMD_EXIT)
+        red_relaxed_gpu_add_s32(a.crit_active, 1);
       if (relay && master) {
         if (!err) relay_publish(&dc->relay[slot], k, dsc);
         else st_release_gpu(&dc->gen, LK_GEN_STOP);
@@ -779,7 +784,8 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     const int berr = (op == LK_OP_BATCH || op == LK_OP_SERVE)
                          ? run_units<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
                          : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot],
-                                             cta_rate(d.aux, S), (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
+                                             cta_rate(d.aux, S), (d.flags & LK_DFLAG_YIELD) ? a.crit_active : nullptr,
+                                             (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
     __syncthreads();
 
@@ -807,6 +813,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
             asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(&dc->slot_done[slot]), "l"(k + 1) : "memory");
             known_done = k + 1;
             st_relaxed_sys(&a.cword[c].status, LK_ST_FINISHED);   /* the host re-arms */
+            if (d.flags & LK_DFLAG_CRITICAL) red_relaxed_gpu_add_s32(a.crit_active, -1);
             t_done = gtime();
           }
         }
@@ -846,6 +853,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
           if (S > 1) dc->arrive[slot].count = 0;
           if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every CTA has left the claim loop */
           st_release_gpu(&dc->slot_done[slot], k + 1);
+          if (d.flags & LK_DFLAG_CRITICAL) red_relaxed_gpu_add_s32(a.crit_active, -1);
           t_done = gtime();
         }
       }
@@ -921,7 +929,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist, 0);
+  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist, 0, nullptr);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -240,6 +240,11 @@ typedef struct __attribute__((aligned(LK_LINE))) {
 #define LK_KFLAG_FINITE 4u       /* finite mode: ring pre-filled in device memory      */
 #define LK_KFLAG_GEMM_FFMA 8u    /* GEMM tiles on the FFMA path only                   */
 
+/* Descriptor flag bits the host sets in the posted wire (never user-set:
+ * lk_desc.flags must be 0): the cluster's lk_set_role. */
+#define LK_DFLAG_CRITICAL 1u      /* marks crit_active while it runs              */
+#define LK_DFLAG_YIELD    2u      /* its loads wait while crit_active is non-zero */
+
 typedef struct {
   lk_wire* ring;                 /* [C][R]; host-mapped (live) or device (finite mode)  */
   lk_cword* cword;               /* [C] host-mapped                                     */
@@ -257,6 +262,7 @@ typedef struct {
   uint64_t* log_count;           /* [G] device: records written per CTA                 */
   lk_bcluster* bcl;              /* [C] device: batch tickets and combine state         */
   uint32_t* cta_hist;            /* [total][256] device: single-part histogram bins     */
+  int32_t* crit_active;          /* device: critical descriptors running (lk_set_role)  */
   int32_t num_clusters;
   int32_t grid;
   int32_t total;                 /* CTAs that join clusters (= sum of sizes)            */

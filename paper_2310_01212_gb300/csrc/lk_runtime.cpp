@@ -86,6 +86,7 @@ struct lk_ctx {
   Tail* rearmed = nullptr;       /* [C] descriptors whose FINISHED the host consumed */
 
   Tail* rate = nullptr;          /* [C] default load-rate cap (bytes/us), 0 = none */
+  Tail* role = nullptr;          /* [C] lk_set_role value                         */
 
   /* batches: per cluster LK_BATCH_BUFFERS unit tables in host-mapped memory */
   uint32_t max_units = 0;
@@ -224,13 +225,16 @@ static int post_mailbox(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, cons
 }
 
 /* Ticket + publish.  Returns LK_OK / LK_EAGAIN.  A descriptor without its
- * own rate cap carries the cluster's default (lk_set_rate) in `aux`. */
+ * own rate cap carries the cluster's default (lk_set_rate) in `aux`, and
+ * every descriptor the cluster's role (lk_set_role) in its flag bits. */
 static int post(lk_ctx* ctx, int c, uint32_t cmd, const lk_desc* d, const void* in0, const void* in1,
                 void* out, uint64_t* seq_out) {
   lk_desc paced;
-  if (d && !d->aux) {
+  const uint64_t role = ctx->role[c].t.load(std::memory_order_relaxed);
+  if (d && (!d->aux || role)) {
     paced = *d;
-    paced.aux = ctx->rate[c].t.load(std::memory_order_relaxed);
+    if (!paced.aux) paced.aux = ctx->rate[c].t.load(std::memory_order_relaxed);
+    paced.flags |= role == LK_ROLE_CRITICAL ? LK_DFLAG_CRITICAL : role == LK_ROLE_YIELD ? LK_DFLAG_YIELD : 0u;
     d = &paced;
   }
   if (ctx->mailbox) return post_mailbox(ctx, c, cmd, d, in0, in1, out, seq_out);
@@ -347,7 +351,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
     for (int c = 0; c < ctx->C; ++c) ctx->mbox_h[c].to_gpu = LK_CMD_NOP;   /* idle */
   }
 
-  /* device block: [ring (finite only)] dcl[C] cl_start rd_off pin_smid boot_smid boot_count log_count log */
+  /* device block: [ring (finite only)] dcl[C] cl_start rd_off pin_smid boot_smid boot_count crit_active
+   * log_count bcl chist log */
   size_t d_ring = 0;
   size_t d_dcl = live ? 0 : align_up(ring_bytes, LK_LINE);
   size_t d_start = align_up(d_dcl + ctx->C * sizeof(lk_dcluster), LK_LINE);
@@ -355,7 +360,8 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   size_t d_pin = align_up(d_rdoff + ctx->C * sizeof(int32_t), LK_LINE);
   size_t d_bsm = align_up(d_pin + (p->smids ? ctx->total : 0) * sizeof(int32_t), LK_LINE);
   size_t d_bcnt = align_up(d_bsm + ctx->G * sizeof(int32_t), LK_LINE);
-  size_t d_lcnt = align_up(d_bcnt + sizeof(uint32_t), LK_LINE);
+  size_t d_crit = align_up(d_bcnt + sizeof(uint32_t), LK_LINE);
+  size_t d_lcnt = align_up(d_crit + sizeof(int32_t), LK_LINE);
   size_t d_bcl = align_up(d_lcnt + ctx->G * sizeof(uint64_t), LK_LINE);
   size_t d_chist = align_up(d_bcl + ctx->C * sizeof(lk_bcluster), LK_LINE);
   size_t d_log = align_up(d_chist + (size_t)ctx->total * 256 * sizeof(uint32_t), LK_LINE);
@@ -390,6 +396,7 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   a.log = ctx->log_cap ? (lk_exec_rec*)(db + d_log) : nullptr;
   a.bcl = (lk_bcluster*)(db + d_bcl);
   a.cta_hist = (uint32_t*)(db + d_chist);
+  a.crit_active = (int32_t*)(db + d_crit);
   a.num_clusters = ctx->C;
   a.grid = ctx->G;
   a.total = ctx->total;
@@ -409,8 +416,9 @@ static int setup(lk_ctx* ctx, const lk_init_params* p, bool live, uint32_t ring_
   ctx->tail = new (std::nothrow) Tail[ctx->C];
   ctx->rearmed = new (std::nothrow) Tail[ctx->C];
   ctx->rate = new (std::nothrow) Tail[ctx->C];
+  ctx->role = new (std::nothrow) Tail[ctx->C];
   ctx->batch = new (std::nothrow) lk_ctx::BatchState[ctx->C];
-  if (!ctx->tail || !ctx->rearmed || !ctx->rate || !ctx->batch) return LK_ENOMEM;
+  if (!ctx->tail || !ctx->rearmed || !ctx->rate || !ctx->role || !ctx->batch) return LK_ENOMEM;
   return LK_OK;
 }
 
@@ -421,6 +429,7 @@ static void teardown(lk_ctx* ctx) {
   delete[] ctx->tail;
   delete[] ctx->rearmed;
   delete[] ctx->rate;
+  delete[] ctx->role;
   delete[] ctx->batch;
   delete ctx;
 }
@@ -535,6 +544,13 @@ int lk_set_rate(lk_ctx* ctx, int cluster, uint64_t bytes_per_us) {
   if (!ctx || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
   if (bytes_per_us >= (1ull << 40) || (bytes_per_us != 0 && bytes_per_us < LK_RATE_MIN)) return LK_EINVAL;
   ctx->rate[cluster].t.store(bytes_per_us, std::memory_order_relaxed);
+  return LK_OK;
+}
+
+int lk_set_role(lk_ctx* ctx, int cluster, int role) {
+  if (!ctx || cluster < 0 || cluster >= ctx->C) return LK_EINVAL;
+  if (role != LK_ROLE_NONE && role != LK_ROLE_CRITICAL && role != LK_ROLE_YIELD) return LK_EINVAL;
+  ctx->role[cluster].t.store((uint64_t)role, std::memory_order_relaxed);
   return LK_OK;
 }
 

@@ -37,6 +37,7 @@ LK_OP_SPIN = 8
 LK_OP_BATCH = 9
 LK_OP_SERVE = 10
 LK_SERVE_CHUNKS, LK_SERVE_QUEUE = 0, 1
+LK_ROLE_NONE, LK_ROLE_CRITICAL, LK_ROLE_YIELD = 0, 1, 2
 (LK_DERR_NONE, LK_DERR_LEASE, LK_DERR_ABORT, LK_DERR_BOOT, LK_DERR_STALL, LK_DERR_BADDESC, LK_DERR_STAGING,
  LK_DERR_BOUNDS) = range(8)
 OP_INPUTS = {LK_OP_NOP: 0, LK_OP_ADD_I32: 2, LK_OP_HIST_U8: 1, LK_OP_SUM_F32: 1, LK_OP_GEMM64_F32: 2,
@@ -135,6 +136,7 @@ def load(fake: bool = False, bounds: bool = False) -> ctypes.CDLL:
             "lk_sync": (I, [P, U64]),
             "lk_heartbeat": (I, [P]),
             "lk_set_rate": (I, [P, I, U64]),
+            "lk_set_role": (I, [P, I, I]),
             "lk_dispose": (I, [P, U64]),
             "lk_dispose_timed": (I, [P, U64, ctypes.POINTER(ctypes.c_float)]),
             "lk_cluster_info": (I, [P, I, ctypes.POINTER(I), I]),
@@ -331,6 +333,13 @@ def lk_set_rate(ctx: Context, cluster: int, bytes_per_us: int) -> None:
     rc = ctx.lib.lk_set_rate(ctx.ptr, cluster, bytes_per_us)
     if rc != LK_OK:
         raise LkError(rc, "lk_set_rate")
+
+
+def lk_set_role(ctx: Context, cluster: int, role: int) -> None:
+    """Role of `cluster` for load yielding: LK_ROLE_CRITICAL, LK_ROLE_YIELD or LK_ROLE_NONE."""
+    rc = ctx.lib.lk_set_role(ctx.ptr, cluster, role)
+    if rc != LK_OK:
+        raise LkError(rc, "lk_set_role")
 
 
 def lk_dispose(ctx: Context, timeout_ns: int = 20_000_000_000) -> int:

@@ -671,6 +671,33 @@ def test_rate_caps_are_checked(fake_env):
         assert lk.lk_wait(c, h) == lk.LK_OK
 
 
+# ---- load yielding (lk_set_role) -----------------------------------------------------
+def test_roles_are_checked(fake_env):
+    with ctx_() as c:
+        for cl, role in ((0, lk.LK_ROLE_CRITICAL), (1, lk.LK_ROLE_YIELD), (1, lk.LK_ROLE_NONE)):
+            lk.lk_set_role(c, cl, role)
+        for cl, role in ((0, 3), (0, -1), (2, lk.LK_ROLE_YIELD), (-1, lk.LK_ROLE_CRITICAL)):
+            with pytest.raises(lk.LkError) as e:
+                lk.lk_set_role(c, cl, role)
+            assert e.value.code == lk.LK_EINVAL
+
+
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX])
+def test_role_bits_ride_the_wire(fake_env, flags):
+    """The role travels as flag bits of the posted descriptor next to a rate
+    cap: every delivery mode still carries and completes such descriptors,
+    batches included."""
+    with ctx_(flags=flags) as c:
+        lk.lk_set_role(c, 0, lk.LK_ROLE_CRITICAL)
+        lk.lk_set_role(c, 1, lk.LK_ROLE_YIELD)
+        lk.lk_set_rate(c, 1, 5000)
+        for i in range(12):   # one at a time: the mailbox holds one descriptor per cluster
+            assert lk.lk_wait(c, lk.lk_submit(c, i % 2, lk.LK_OP_COPY_I32, 64, (A,), A)) == lk.LK_OK
+        for cl in (0, 1):
+            items = lk.batch_items([(lk.LK_OP_COPY_I32, 64, (A,), A)] * 3)
+            assert lk.lk_wait(c, lk.lk_submit_batch(c, cl, items)) == lk.LK_OK
+
+
 def test_gemm_ffma_flag_accepted(fake_env):
     with ctx_(flags=lk.LK_INIT_GEMM_FFMA | lk.LK_INIT_MAILBOX) as c:
         assert lk.lk_wait(c, lk.lk_submit(c, 0, lk.LK_OP_NOP, 0)) == lk.LK_OK
