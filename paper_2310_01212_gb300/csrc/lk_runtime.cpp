@@ -1208,7 +1208,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   std::deque<size_t> waiting;    /* arrived, not admitted (FIFO) */
   std::deque<size_t> active;     /* admitted with units left to publish (round-robin) */
   uint64_t held = 0, next_u = 0, acked = 0, cq_head = 0, last_beat = t0;
-  uint64_t unfinished_units = 0;   /* units of admitted, unfinished requests */
+  uint64_t unpublished = 0;   /* units of admitted requests not yet published */
   size_t finished = 0;
   int first_err = LK_OK;
   char* const out_base = (char*)p->arena + sbytes;
@@ -1252,12 +1252,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       slot_req[q.slot] = i;
       held += q.held;
       if (reqs[i].op != LK_OP_SUM_F32) {
-        /* spread over the CTAs no published, unfinished unit holds */
-        const uint64_t busy = unfinished_units;
-        const uint64_t idle = busy < (uint64_t)ctx->total ? (uint64_t)ctx->total - busy : 0;
+        /* spread over the CTAs that no queued unit waits for: the backlog is
+         * every admitted unit no CTA has claimed yet (published or not);
+         * units already running do not count, their CTAs free up first */
+        const uint64_t backlog = unpublished + (next_u - acked);
+        const uint64_t idle = backlog < (uint64_t)ctx->total ? (uint64_t)ctx->total - backlog : 0;
         q.parts = std::max<uint32_t>(q.base_parts, (uint32_t)std::min<uint64_t>(idle, q.wide_parts));
       }
-      unfinished_units += q.parts;
+      unpublished += q.parts;
       res[i].chunks = q.parts;
       res[i].t_admit_ns = now_ns() - t0;
       active.push_back(i);
@@ -1281,6 +1283,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       st_rlx(&e->w[4], tag | ((uint64_t)r.op << 32) | ((uint64_t)q.parts << 16) | (uint64_t)q.published);
       st_rlx(&e->w[5], tag | (uint64_t)q.slot);
       ++next_u;
+      --unpublished;
       if (++q.published < q.parts) active.push_back(i);
     }
     /* retire completed requests */
@@ -1300,7 +1303,6 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       res[i].out = q.out;
       if (q.arena_out) arena.release(q.out_off, q.out_bytes);
       held -= q.held;
-      unfinished_units -= q.parts;
       free_slots.push_back(slot);
       ++finished;
     }

@@ -744,8 +744,9 @@ def test_queue_serves_every_request_with_its_units(fake_env):
 
 def test_queue_split_rule(fake_env):
     """A sum gets exactly max(ceil(B / part), min(CTAs, ceil(B / min_part)))
-    units, whatever else runs; another op spreads over the idle CTAs (here
-    all six, nothing else is admitted at once), never below ceil(B / part)."""
+    units, whatever else runs; another op spreads over the CTAs no unclaimed
+    unit waits for (here all six: nothing else is queued at once), never
+    below ceil(B / part)."""
     with ctx_(sizes=(2, 2, 2)) as c:
         ops = [lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_COPY_I32, lk.LK_OP_COPY_I32,
                lk.LK_OP_HIST_U8, lk.LK_OP_GEMM64_F32]
