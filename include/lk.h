@@ -385,12 +385,14 @@ typedef struct {
  * on its split) exactly
  *   max(ceil(B / part_bytes), min(S, ceil(B / min_part_bytes))),
  * S = the context's CTAs, so it is the same whatever else is served; any
- * other op as many as max(ceil(B / part_bytes), min(idle, ceil(B /
- * min_part_bytes))), where idle = S minus the backlog when it is admitted:
- * the admitted units no CTA has claimed yet (units already running do not
- * count).  Their results do not depend on the split, so a request spreads
- * over the CTAs that no queued unit waits for, and under a backlog (the
- * queue saturated) takes the large units. */
+ * other op as many as max(ceil(B / f), min(idle, ceil(B /
+ * min_part_bytes))), where idle = S minus the backlog when it is admitted
+ * (the admitted units no CTA has claimed yet; units already running do not
+ * count) and f = part_bytes while that backlog holds at least S x
+ * part_bytes / 2 input bytes (the queue is saturated), else
+ * max(min_part_bytes, part_bytes / 8).  Their results do not depend on the
+ * split, so a request spreads over the CTAs that no queued unit waits for,
+ * in units of at most f. */
 
 /* Device bytes the queue's state takes at the start of the arena
  * (LK_SERVE_QUEUE) for `max_inflight` request slots (0 -> 4096). */

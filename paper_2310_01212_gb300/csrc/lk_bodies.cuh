@@ -1036,6 +1036,59 @@ __device__ __forceinline__ bool body_gemm_tc(const lk_slot& d, int r, int S, uns
   return ok;
 }
 
+/* FFMA micro-tiles of one row block: `rows` rows of A (row-major, 64 k
+ * each) times the 64 x 64 B tile, both in shared memory, into C (row-major,
+ * 64 floats a row).  Thread t takes micro-tiles of MR rows x MC columns, t
+ * and t + T ...; every output accumulates its 64 products in k order with
+ * one fused multiply-add each, whatever the micro-tile shape, so a tile's
+ * result does not depend on how it was split into row blocks. */
+template <int MR, int MC, bool FULL_UNROLL>
+__device__ __forceinline__ void ffma_block(const float* sA, const float* sB, float* cblk, uint32_t rows, bool store_ok) {
+  constexpr uint32_t ncg = 64u / MC;
+  const uint32_t nmt = rows / MR * ncg;
+  for (uint32_t mt = threadIdx.x; mt < nmt; mt += blockDim.x) {
+    const uint32_t r0 = mt / ncg * MR, c0 = mt % ncg * MC;
+    float c[MR][MC];
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+      for (int j = 0; j < MC; ++j) c[i][j] = 0.f;
+#pragma unroll(FULL_UNROLL ? 16 : 2)
+    for (uint32_t k = 0; k < 64; k += 4) {
+      float av[MR][4], bv[4][MC];
+#pragma unroll
+      for (int i = 0; i < MR; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(sA + (r0 + i) * 64 + k);
+        av[i][0] = q.x; av[i][1] = q.y; av[i][2] = q.z; av[i][3] = q.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (MC == 4) {
+          const float4 b = *reinterpret_cast<const float4*>(sB + (k + q) * 64 + c0);
+          bv[q][0] = b.x; bv[q][1] = b.y; bv[q][MC > 2 ? 2 : 0] = b.z; bv[q][MC > 3 ? 3 : 0] = b.w;
+        } else {
+          const float2 b = *reinterpret_cast<const float2*>(sB + (k + q) * 64 + c0);
+          bv[q][0] = b.x; bv[q][1] = b.y;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+          for (int j = 0; j < MC; ++j) c[i][j] = fmaf(av[i][q], bv[q][j], c[i][j]);
+    }
+    if (store_ok && LK_INB(r0 + MR <= rows && c0 + MC <= 64u, LK_OOB_GEMM_STORE)) {
+#pragma unroll
+      for (int i = 0; i < MR; ++i) {
+        float* crow = cblk + (r0 + i) * 64 + c0;
+        if (MC == 4) *reinterpret_cast<float4*>(crow) = make_float4(c[i][0], c[i][1], c[i][MC > 2 ? 2 : 0], c[i][MC > 3 ? 3 : 0]);
+        else *reinterpret_cast<float2*>(crow) = make_float2(c[i][0], c[i][1]);
+      }
+    }
+  }
+}
+
 /* Returns false if a staging copy did not complete before the deadline.
  * `phase` holds one parity bit per stage and persists across descriptors;
  * `pace` paces the tile loads as in stream().  Whole tiles at 256 threads
@@ -1057,7 +1110,6 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
   const float* A = reinterpret_cast<const float*>(d.in0);
   const float* B = reinterpret_cast<const float*>(d.in1);
   float* C = reinterpret_cast<float*>(d.out);
-  const uint32_t T = blockDim.x;
   constexpr uint32_t nstages = SmemCfg<P>::gemm_stages;
   const uint64_t unit_bytes = rows * 256u + 16384u;
   const uint64_t deadline = pace.rate ? pace.deadline + (end - beg) * unit_bytes * 1000u / pace.rate : pace.deadline;
@@ -1115,41 +1167,14 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
     const float* sB = sA + 4096;
     const uint64_t tile = u / U;
     const uint32_t rb = (uint32_t)(u % U);
-    const uint32_t nmt = rows * 4;   /* 4x4 micro-tiles: rows/4 row groups x 16 column groups */
-    for (uint32_t mt = threadIdx.x; mt < nmt; mt += T) {
-      const uint32_t r0 = (mt >> 4) << 2, c0 = (mt & 15u) << 2;
-      float c[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
-#pragma unroll(FULL_UNROLL ? 16 : 2)
-      for (uint32_t k = 0; k < 64; k += 4) {
-        float av[4][4], bv[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 q = *reinterpret_cast<const float4*>(sA + (r0 + i) * 64 + k);
-          av[i][0] = q.x; av[i][1] = q.y; av[i][2] = q.z; av[i][3] = q.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 b = *reinterpret_cast<const float4*>(sB + (k + q) * 64 + c0);
-          bv[q][0] = b.x; bv[q][1] = b.y; bv[q][2] = b.z; bv[q][3] = b.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) c[i][j] = fmaf(av[i][q], bv[q][j], c[i][j]);
-      }
-      float* crow = C + tile * 4096 + (uint64_t)(rb * rows + r0) * 64 + c0;
-      if (LK_INB(tile < tiles && rb * rows + r0 + 4u <= 64u && c0 + 4u <= 64u, LK_OOB_GEMM_STORE)) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          *reinterpret_cast<float4*>(crow + i * 64) = make_float4(c[i][0], c[i][1], c[i][2], c[i][3]);
-      }
-    }
+    float* cblk = C + tile * 4096 + (uint64_t)rb * rows * 64;
+    const bool cblk_ok = LK_INB(tile < tiles && (uint64_t)(rb + 1) * rows <= 64u, LK_OOB_GEMM_STORE);
+    /* every thread takes a micro-tile: the smaller the row block, the fewer
+     * outputs each (a one-tile item split 8 ways keeps all threads busy) */
+    if (rows >= 64) ffma_block<4, 4, FULL_UNROLL>(sA, sB, cblk, rows, cblk_ok);
+    else if (rows >= 32) ffma_block<2, 4, FULL_UNROLL>(sA, sB, cblk, rows, cblk_ok);
+    else if (rows >= 16) ffma_block<2, 2, FULL_UNROLL>(sA, sB, cblk, rows, cblk_ok);
+    else ffma_block<1, 2, FULL_UNROLL>(sA, sB, cblk, rows, cblk_ok);
   }
   __syncthreads();          /* every stage is free for the next body */
   return ok;

@@ -1095,6 +1095,8 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   const uint32_t nslots = p->max_inflight ? p->max_inflight : 4096u;
   const uint64_t part_bytes = p->part_bytes ? p->part_bytes : (8ull << 20);
   const uint64_t min_part = p->min_part_bytes ? p->min_part_bytes : (128ull << 10);
+  /* unit size floor of a non-sum request while the queue is not saturated */
+  const uint64_t fine_part = std::max<uint64_t>(min_part, part_bytes / 8);
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
   const int window = p->window > 0 ? p->window : 2;
   const uint64_t W = std::min<uint64_t>((uint64_t)window * (uint64_t)ctx->total, ctx->qn / 2);
@@ -1104,7 +1106,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   if (p->arena_bytes < sbytes) return LK_ENOMEM;
   struct QReq {
     uint64_t in_bytes = 0, out_bytes = 0, held = 0, out_off = 0;
-    uint32_t parts = 1, published = 0, slot = 0, base_parts = 1, wide_parts = 1;
+    uint32_t parts = 1, published = 0, slot = 0, base_parts = 1, fine_parts = 1, wide_parts = 1;
     bool arena_out = false;
     void* out = nullptr;
   };
@@ -1126,8 +1128,13 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
      * other ops may spread wider at admission (split_wide) */
     q.base_parts = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (q.in_bytes + part_bytes - 1) / part_bytes),
                                                 LK_SERVE_MAX_PARTS);
+    q.fine_parts = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (q.in_bytes + fine_part - 1) / fine_part),
+                                                LK_SERVE_MAX_PARTS);
     q.wide_parts = (uint32_t)std::min<uint64_t>((q.in_bytes + min_part - 1) / min_part, LK_SERVE_MAX_PARTS);
-    if (r.op == LK_OP_GEMM64_F32) q.wide_parts = (uint32_t)std::min<uint64_t>(q.wide_parts, r.n);   /* whole tiles */
+    if (r.op == LK_OP_GEMM64_F32) {   /* whole tiles */
+      q.fine_parts = (uint32_t)std::min<uint64_t>(q.fine_parts, r.n);
+      q.wide_parts = (uint32_t)std::min<uint64_t>(q.wide_parts, r.n);
+    }
     q.parts = r.op == LK_OP_SUM_F32 ? std::max(q.base_parts, std::min<uint32_t>((uint32_t)ctx->total, q.wide_parts))
                                     : q.base_parts;
     q.arena_out = r.out == nullptr;
@@ -1208,7 +1215,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   std::deque<size_t> waiting;    /* arrived, not admitted (FIFO) */
   std::deque<size_t> active;     /* admitted with units left to publish (round-robin) */
   uint64_t held = 0, next_u = 0, acked = 0, cq_head = 0, last_beat = t0;
-  uint64_t unpublished = 0;   /* units of admitted requests not yet published */
+  uint64_t unpublished = 0;         /* units of admitted requests not yet published */
+  uint64_t unpublished_bytes = 0;   /* and their input bytes */
+  uint64_t pub_bytes = 0;           /* input bytes of every published unit */
+  /* input bytes published through unit u, at u mod qn: the bytes of the
+   * published units no CTA has claimed yet are cum(next_u) - cum(acked) */
+  std::vector<uint64_t> cum(ctx->qn, 0);
+  /* saturated: the unclaimed backlog holds at least half a part per CTA */
+  const uint64_t sat_bytes = (uint64_t)ctx->total * part_bytes / 2;
   size_t finished = 0;
   int first_err = LK_OK;
   char* const out_base = (char*)p->arena + sbytes;
@@ -1256,10 +1270,14 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
          * every admitted unit no CTA has claimed yet (published or not);
          * units already running do not count, their CTAs free up first */
         const uint64_t backlog = unpublished + (next_u - acked);
+        const uint64_t claimed_bytes = acked ? cum[(acked - 1) & (ctx->qn - 1)] : 0;
+        const uint64_t backlog_bytes = unpublished_bytes + (pub_bytes - claimed_bytes);
+        const uint32_t floor_parts = backlog_bytes >= sat_bytes ? q.base_parts : q.fine_parts;
         const uint64_t idle = backlog < (uint64_t)ctx->total ? (uint64_t)ctx->total - backlog : 0;
-        q.parts = std::max<uint32_t>(q.base_parts, (uint32_t)std::min<uint64_t>(idle, q.wide_parts));
+        q.parts = std::max<uint32_t>(floor_parts, (uint32_t)std::min<uint64_t>(idle, q.wide_parts));
       }
       unpublished += q.parts;
+      unpublished_bytes += q.in_bytes;
       res[i].chunks = q.parts;
       res[i].t_admit_ns = now_ns() - t0;
       active.push_back(i);
@@ -1282,8 +1300,13 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
       st_rlx(&e->w[3], tag | (r.n & LK_LOW48));
       st_rlx(&e->w[4], tag | ((uint64_t)r.op << 32) | ((uint64_t)q.parts << 16) | (uint64_t)q.published);
       st_rlx(&e->w[5], tag | (uint64_t)q.slot);
+      /* this unit's share of the input bytes, the request's split exactly */
+      const uint64_t ub = q.in_bytes * (q.published + 1) / q.parts - q.in_bytes * q.published / q.parts;
+      pub_bytes += ub;
+      cum[next_u & (ctx->qn - 1)] = pub_bytes;
       ++next_u;
       --unpublished;
+      unpublished_bytes -= ub;
       if (++q.published < q.parts) active.push_back(i);
     }
     /* retire completed requests */

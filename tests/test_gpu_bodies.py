@@ -169,6 +169,28 @@ def test_gemm_ffma_flag(torch_ready, oracle_lib, S):
             assert np.all(np.abs(got - B) <= 2.0 ** -16 * np.abs(B))
 
 
+def test_gemm_row_blocks_bit_identical(torch_ready, oracle_lib):
+    """On the FFMA path a tile's result does not depend on its split into row
+    blocks: one tile on 1, 2, 3 and 8 CTAs (blocks of 64, 32, 16 and 8 rows,
+    each with its own micro-tile shape) gives the same bits, within the
+    per-element bound of the oracle."""
+    torch = torch_ready
+    A = synth.normal_f32(16, 1, 4096).reshape(1, 64, 64)
+    B = synth.normal_f32(16, 2, 4096).reshape(1, 64, 64)
+    dA, dB = to_dev(A), to_dev(B)
+    sizes = [1, 2, 3, 8]
+    outs = [torch.zeros((1, 64, 64), device="cuda") for _ in sizes]
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init(sizes, idle_lease_ns=5_000_000_000, flags=lk.LK_INIT_GEMM_FFMA) as c:
+        hs = [lk.lk_submit(c, i, lk.LK_OP_GEMM64_F32, 1, (dA, dB), o) for i, o in enumerate(outs)]
+        for h in hs:
+            assert lk.lk_wait(c, h) == lk.LK_OK
+    got = [host(o) for o in outs]
+    assert gemm_ok(got[0], A, B, oracle_lib)
+    for g in got[1:]:
+        assert np.array_equal(g, got[0])
+
+
 def test_misaligned_pointers_rejected_on_host(torch_ready):
     torch = torch_ready
     x = torch.zeros(1024, dtype=torch.int32, device="cuda")

@@ -745,8 +745,8 @@ def test_queue_serves_every_request_with_its_units(fake_env):
 def test_queue_split_rule(fake_env):
     """A sum gets exactly max(ceil(B / part), min(CTAs, ceil(B / min_part)))
     units, whatever else runs; another op spreads over the CTAs no unclaimed
-    unit waits for (here all six: nothing else is queued at once), never
-    below ceil(B / part)."""
+    unit waits for (here all six: nothing else is queued at once), and with
+    the queue not saturated never takes units above max(min_part, part / 8)."""
     with ctx_(sizes=(2, 2, 2)) as c:
         ops = [lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_SUM_F32, lk.LK_OP_COPY_I32, lk.LK_OP_COPY_I32,
                lk.LK_OP_HIST_U8, lk.LK_OP_GEMM64_F32]
@@ -756,9 +756,10 @@ def test_queue_split_rule(fake_env):
         assert rc == lk.LK_OK
         got = res["chunks"].tolist()
         # sums (6 CTAs): 4 KiB -> 1; 1 MiB -> min(6, 16) = 6; 36 MiB -> max(9, 6) = 9
-        # copy 1 MiB -> min(6 idle, 16) = 6; copy 36 MiB -> max(9, min(6, ...)) = 9
+        # copy 1 MiB -> max(2, min(6 idle, 16)) = 6; copy 36 MiB -> units of at
+        # most 512 KiB (part / 8): max(72, min(6, 576)) = 72
         # hist 1 MiB -> 6; gemm 3 tiles (96 KiB) -> min(6, 2, 3 tiles) = 2
-        assert got == [1, 6, 9, 6, 9, 6, 2], got
+        assert got == [1, 6, 9, 6, 72, 6, 2], got
 
 
 def test_queue_serves_twice_and_empty(fake_env):
