@@ -68,6 +68,22 @@ def submitter_cpus(local_rank: int, n: int = 4) -> int:
     return base if set(range(base, base + n)) <= allowed else -1
 
 
+def keep_off_submitter_cores(local_rank: int, n: int = 4):
+    """Move this process's own threads, and every thread or process it starts
+    from now on, off the cores that submitter_cpus reserves; the submitting
+    threads pin themselves there.  Returns (first submitter core or -1, the
+    affinity to restore for the CPU baseline, or None)."""
+    base = submitter_cpus(local_rank, n)
+    if base < 0:
+        return -1, None
+    allowed = os.sched_getaffinity(0)
+    rest = allowed - set(range(base, base + n))
+    if not rest:
+        return base, None
+    os.sched_setaffinity(0, rest)
+    return base, allowed
+
+
 def lat_summary(us):
     return {"p50": pct(us, 0.50), "p99": pct(us, 0.99), "p999": pct(us, 0.999), "max": pct(us, 1.0),
             "mean": float(np.mean(us)) if len(us) else None, "count": int(len(us))}
@@ -588,6 +604,10 @@ def main():
     ap.add_argument("--phase-runs", type=int, default=100, help="runs of the paper's life-cycle measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    full_mask = None
+    if args.impl != "reference":
+        # before torch and the CUDA driver start their threads
+        pin, full_mask = keep_off_submitter_cores(int(os.environ.get("LOCAL_RANK", "0")))
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)
@@ -606,7 +626,6 @@ def main():
     cfg = dict(wl.FULL_CHIP)
     seed = cfg["seed"] + 7919 * dist.rank
     items_per_step = args.items
-    pin = submitter_cpus(dist.local)
 
     # dispatch floor (no context alive)
     rtt = lk.lk_pingpong(20_000, device=dev)[1000:] / 1000.0
@@ -1084,6 +1103,8 @@ def main():
         import oracle as _o
 
         _o.build()
+        if full_mask:
+            os.sched_setaffinity(0, full_mask)   # the oracle may use every core
         sample = oracle_sample(424242, 400)
         us = time_oracle(sample, budget_s=15.0)
         names = ["add_i32", "hist_u8", "sum_f32", "gemm64_f32"]   # the sample cycles through the bodies

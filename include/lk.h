@@ -389,7 +389,7 @@ typedef struct {
  * min_part_bytes))), where idle = S minus the backlog when it is admitted
  * (the admitted units no CTA has claimed yet; units already running do not
  * count) and f = part_bytes while that backlog holds at least S x
- * part_bytes / 2 input bytes (the queue is saturated), else
+ * part_bytes input bytes (the queue is saturated), else
  * max(min_part_bytes, part_bytes / 8).  Their results do not depend on the
  * split, so a request spreads over the CTAs that no queued unit waits for,
  * in units of at most f. */

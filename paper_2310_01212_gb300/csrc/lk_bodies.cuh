@@ -462,7 +462,7 @@ __device__ __forceinline__ uint32_t hist_row_readout(const uint32_t* sh, uint32_
  * ring per CTA, warps stalled about a fifth of their cycles at the per-chunk
  * barrier: random bytes make their counting times uneven).  Returns false,
  * on every thread alike, if a stage did not arrive before the deadline. */
-template <int P>
+template <int P, bool YIELD>
 __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg, uint64_t end, unsigned char* dsm,
                                                   uint64_t* bars, uint32_t& phase, uint32_t lane_addr, Pace pace) {
   static_assert(P == 1, "the counter rows take the whole 64 KB work region of one CTA per SM");
@@ -486,9 +486,11 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
   /* the warp's rate: the CTA's, split evenly over its warps */
   const uint64_t rate = pace.rate ? (pace.rate / W ? pace.rate / W : 1) : 0;
   const uint64_t deadline =
-      (rate ? pace.deadline + total * 16u * 1000u / rate : pace.deadline) + (pace.gate ? LK_YIELD_BUDGET_NS : 0u);
+      (rate ? pace.deadline + total * 16u * 1000u / rate : pace.deadline) + (YIELD ? LK_YIELD_BUDGET_NS : 0u);
   const uint64_t t_first = rate && lane == 0 ? gtime() : 0;
-  Yield yield(lane == 0 && nch ? pace.gate : nullptr);
+  /* compiled apart from the plain loop: its state would cost the counting
+   * loop registers */
+  Yield yield(YIELD && lane == 0 && nch ? pace.gate : nullptr);
   auto parity = [&](uint64_t ch) {
     return ((phase >> (LK_NUM_BARS + (uint32_t)(ch % LK_STAGES))) & 1u) ^ ((uint32_t)(ch / LK_STAGES) & 1u);
   };
@@ -504,7 +506,7 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
     bulk_g2s(ring + (size_t)st * stage_vec, in + v0, nv * 16u, &wb[st]);
   };
   if (lane == 0 && nch) {
-    yield.hold();
+    if (YIELD) yield.hold();
     fence_proxy_async_global();   /* earlier generic writes before these async reads */
     fence_proxy_async_smem();     /* earlier generic shared accesses before async writes */
     for (uint64_t ch = 0; ch < nch && ch < LK_STAGES; ++ch) issue(ch);
@@ -537,7 +539,7 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
       /* token bucket as deep as the ring: chunk k >= LK_STAGES no earlier
        * than t_first + (k - LK_STAGES + 1) chunks' worth of time */
       if (rate) sleep_until(t_first + (ch + 1) * (uint64_t)stage_vec * 16u * 1000u / rate);
-      yield.hold();
+      if (YIELD) yield.hold();
       fence_proxy_async_smem();
       issue(ch + LK_STAGES);
     }
@@ -599,7 +601,10 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
       const uint32_t lane_addr = smem_addr(sh) + ((threadIdx.x >> 5) & 1u) * 128u + lane * 4u;
       hist_zero(sh, 256u * 64u);
       __syncthreads();
-      ok = hist_warp_streams<P>(reinterpret_cast<const uint4*>(d.in0), beg, end, dsm, bars, phase, lane_addr, pace);
+      ok = pace.gate ? hist_warp_streams<P, true>(reinterpret_cast<const uint4*>(d.in0), beg, end, dsm, bars, phase,
+                                                  lane_addr, pace)
+                     : hist_warp_streams<P, false>(reinterpret_cast<const uint4*>(d.in0), beg, end, dsm, bars, phase,
+                                                   lane_addr, pace);
       if (tail)
         for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T)
           asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + ((uint32_t)xb[j] << 8))

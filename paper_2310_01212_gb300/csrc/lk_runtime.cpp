@@ -1221,8 +1221,8 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   /* input bytes published through unit u, at u mod qn: the bytes of the
    * published units no CTA has claimed yet are cum(next_u) - cum(acked) */
   std::vector<uint64_t> cum(ctx->qn, 0);
-  /* saturated: the unclaimed backlog holds at least half a part per CTA */
-  const uint64_t sat_bytes = (uint64_t)ctx->total * part_bytes / 2;
+  /* saturated: the unclaimed backlog holds at least a part per CTA */
+  const uint64_t sat_bytes = (uint64_t)ctx->total * part_bytes;
   size_t finished = 0;
   int first_err = LK_OK;
   char* const out_base = (char*)p->arena + sbytes;
