@@ -221,6 +221,10 @@ int lk_init(lk_ctx** out, const lk_init_params* p);
  *   Every non-null pointer must be 16-byte aligned and below 2^48; n must
  *   be at most 2^40 (HIST: below 2^31, GEMM: at most 2^28 tiles).  No CUDA call is made:
  *   the descriptor reaches the device through the mailbox ring only.
+ *   Outputs are written while the descriptor runs (a histogram's bins are
+ *   cleared by the cluster's first CTA and accumulated by every CTA), so an
+ *   output must not be read, nor written by another descriptor, until this
+ *   one has finished.
  * On success *h names the descriptor.
  * Errors: LK_EINVAL (cluster, op, n_in, alignment, n too large),
  * LK_EAGAIN (ring full, or with LK_INIT_MAILBOX the mailbox not idle yet:

@@ -557,9 +557,40 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
   return !__syncthreads_or(failed);
 }
 
+/* Where a histogram's counts go.  With `zero` null, every CTA adds its
+ * counts into `acc` (zero at rest) and a combine copies it out afterwards
+ * (split parts, ordinary launches).  With `zero` set (a descriptor on a
+ * cluster), rank 0 clears the output itself and release-stores `seq` into
+ * *zero, and every CTA adds its counts straight into the output once it has
+ * acquired that word: no combine, and no CTA waits for another at the end. */
+struct HistSink {
+  uint32_t* acc;
+  uint64_t* zero;
+  uint64_t seq;
+};
+
+/* Thread 0 waits for rank 0's cleared output (with a sink that has one),
+ * then the whole CTA synchronises; false, on every thread, if the word did
+ * not arrive by `deadline`. */
+__device__ __forceinline__ bool hist_out_ready(const HistSink& sink, uint64_t deadline) {
+  __shared__ int s_ready;
+  if (threadIdx.x == 0) {
+    int ready = 1;
+    if (sink.zero)
+      for (uint32_t it = 0; ld_acquire_gpu(sink.zero) < sink.seq; ++it)
+        if ((it & 63u) == 63u && gtime() > deadline) {
+          ready = 0;
+          break;
+        }
+    s_ready = ready;
+  }
+  __syncthreads();
+  return s_ready != 0;
+}
+
 template <int P>
 __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                          uint32_t& phase, Pace pace, uint32_t* acc) {
+                                          uint32_t& phase, Pace pace, HistSink sink) {
   const uint64_t nv = d.n >> 4;
   uint64_t beg, end;
   share(nv, r, S, beg, end);
@@ -570,6 +601,16 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   const uint8_t* xb = reinterpret_cast<const uint8_t*>(d.in0);
   bool ok = true;
   const uint64_t total = end - beg;
+  uint32_t* acc = sink.acc;
+  if (sink.zero) {
+    acc = reinterpret_cast<uint32_t*>(d.out);
+    if (r == 0) {
+      /* the counters' targets start at zero; the others add once they see it */
+      for (uint32_t v = threadIdx.x; v < 256; v += T) acc[v] = 0;
+      __syncthreads();
+      if (threadIdx.x == 0) st_release_gpu(sink.zero, sink.seq);
+    }
+  }
   if (total * 16 < LK_HIST_SMALL_BYTES) {
     hist_zero(sh, W * 256);
     __syncthreads();
@@ -586,13 +627,13 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
                           });
     if (tail)
       for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T) atomicAdd(&bins[xb[j]], 1u);
-    __syncthreads();
-    for (uint32_t v = threadIdx.x; v < 256; v += T) {
+    const bool ready = hist_out_ready(sink, pace.deadline);
+    for (uint32_t v = threadIdx.x; ready && v < 256; v += T) {
       uint32_t s = 0;
       for (uint32_t w = 0; w < W; ++w) s += sh[w * 256 + v];
       if (s) atomicAdd(&acc[v], s);
     }
-    return ok;
+    return ok && ready;
   }
   if constexpr (P == 1) {
     if (total * 16 >= LK_HIST_WARP_BYTES) {
@@ -609,12 +650,12 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
         for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T)
           asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + ((uint32_t)xb[j] << 8))
                        : "memory");
-      __syncthreads();
-      for (uint32_t v = threadIdx.x; v < 256; v += T) {
+      const bool ready = hist_out_ready(sink, pace.deadline);
+      for (uint32_t v = threadIdx.x; ready && v < 256; v += T) {
         const uint32_t tot = hist_row_readout(sh, v);
         if (tot) atomicAdd(&acc[v], tot);
       }
-      return ok;
+      return ok && ready;
     }
   }
   /* medium share, or two CTAs per SM: one ring for the CTA; lane-private
@@ -654,12 +695,12 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
   if (tail)
     for (uint64_t j = nv * 16 + threadIdx.x; j < d.n; j += T)
       asm volatile("red.relaxed.cta.shared::cta.add.u32 [%0], 1;" ::"r"(lane_addr + ((uint32_t)xb[j] << 7)) : "memory");
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < 256; v += T) {
+  const bool ready = hist_out_ready(sink, pace.deadline);
+  for (uint32_t v = threadIdx.x; ready && v < 256; v += T) {
     const uint32_t tot = hist_readout<P>(sh, v);
     if (tot) atomicAdd(&acc[v], tot);
   }
-  return ok;
+  return ok && ready;
 }
 
 /* Rank 0: copy the accumulator out and return it to zero for reuse. */

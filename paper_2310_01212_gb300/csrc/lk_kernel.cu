@@ -361,7 +361,7 @@ __device__ __forceinline__ uint64_t cta_rate(uint64_t cluster_rate, int S) {
  * tensor cores. */
 template <int MAXT, int P>
 __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned char* dsm, uint64_t* bars,
-                                        uint32_t& phase, float* red, float* partial_out, uint32_t* hist_acc,
+                                        uint32_t& phase, float* red, float* partial_out, HistSink hist,
                                         uint64_t rate, const int32_t* gate, bool tc = true) {
   const uint32_t op = d.cmd - LK_CMD_WORK;
   const Pace deadline{gtime() + 2000000000ull, rate, gate};
@@ -372,7 +372,7 @@ __device__ __forceinline__ int run_body(const lk_slot& d, int r, int S, unsigned
     case LK_OP_SUM_F32:
       ok = body_sum<P, (MAXT <= 256 && P == 1)>(d, r, S, dsm, bars, phase, deadline, red, partial_out);
       break;
-    case LK_OP_HIST_U8: ok = body_hist<P>(d, r, S, dsm, bars, phase, deadline, hist_acc); break;
+    case LK_OP_HIST_U8: ok = body_hist<P>(d, r, S, dsm, bars, phase, deadline, hist); break;
     case LK_OP_GEMM64_F32:
       ok = body_gemm<(MAXT <= 256 && P == 1), P>(d, r, S, reinterpret_cast<float*>(dsm), bars, phase, deadline, tc);
       break;
@@ -556,9 +556,10 @@ __device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, in
       float* pout = parts > 1 ? s_psum + part : &s_part_sum;
       ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
     } else if (op == LK_OP_HIST_U8) {
-      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline, parts > 1 ? s_pbins : my_hist);
+      ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline,
+                        HistSink{parts > 1 ? s_pbins : my_hist, nullptr, 0});
     } else {
-      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, nullptr, rate, gate,
+      ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, HistSink{}, rate, gate,
                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0) == 0;
     }
     __syncthreads();
@@ -783,7 +784,8 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     const uint32_t op = d.cmd - LK_CMD_WORK;
     const int berr = (op == LK_OP_BATCH || op == LK_OP_SERVE)
                          ? run_units<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
-                         : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r], dc->hist[slot],
+                         : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r],
+                                             HistSink{nullptr, &dc->hzero[slot], d.seq},
                                              cta_rate(d.aux, S), (d.flags & LK_DFLAG_YIELD) ? a.crit_active : nullptr,
                                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
@@ -793,7 +795,7 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     if (tid == 0) t_end = gtime();
     if (mailbox) {
       /* ---- finish, one-deep mailbox: rank 0 gathers every rank's flag,
-       * combines, and answers THREAD_FINISHED ---------------------------- */
+       * combines a sum, and answers THREAD_FINISHED ---------------------- */
       if (tid == 0 && S > 1) st_release_gpu(&dc->flag[r], k + 1);   /* orders this CTA's writes (after the barrier) */
       if (master) {
         if (S > 1) {
@@ -803,7 +805,6 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
         __syncthreads();
         if (!s_err) {
           if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
-          else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
           __syncthreads();
           if (tid == 0) {
             if (op == LK_OP_BATCH) a.bcl[c].ticket = 0;   /* every rank has left the claim loop */
@@ -822,20 +823,20 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       /* ---- finish, ring modes: every CTA publishes its own completion
        * word (the paper's per-SM from_GPU mailbox); the host takes the
        * minimum over the cluster's words, so nothing between the last CTA's
-       * end and the host waits on another CTA.  A sum, histogram or batch
-       * needs one CTA to finish the descriptor's shared state first: each
-       * CTA arrives on the slot's counter before publishing, and the last
-       * arriver combines (the host's minimum includes its word, published
-       * after the combine).  Other ops arrive after publishing, off the
-       * host's path; their arrivals only pick the CTA that frees the slot. */
-      const bool comb = op == LK_OP_SUM_F32 || op == LK_OP_HIST_U8 || op == LK_OP_BATCH;
+       * end and the host waits on another CTA.  A sum or batch needs one
+       * CTA to finish the descriptor's shared state first: each CTA arrives
+       * on the slot's counter before publishing, and the last arriver
+       * combines (the host's minimum includes its word, published after the
+       * combine).  Other ops -- a histogram too: every CTA adds its counts
+       * into the output itself -- arrive after publishing, off the host's
+       * path; their arrivals only pick the CTA that frees the slot. */
+      const bool comb = op == LK_OP_SUM_F32 || op == LK_OP_BATCH;
       if (comb) {
         if (tid == 0 && !s_err)
           s_last = S == 1 || atom_add_acq_rel_gpu(&dc->arrive[slot].count, 1u) == (uint32_t)(S - 1);
         __syncthreads();
         if (s_last) {   /* CTA-uniform after the barrier */
           if (op == LK_OP_SUM_F32) combine_sum(d, dc->partial[slot], S);
-          else if (op == LK_OP_HIST_U8) combine_hist(d, dc->hist[slot]);
           __syncthreads();   /* the combine's writes before thread 0's fence */
         }
       }
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], sc->hist, 0, nullptr);
+  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], HistSink{sc->hist, nullptr, 0}, 0, nullptr);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -134,8 +134,8 @@ typedef struct {
  * rank 0 gathers the flags and completes each descriptor).  In the ring
  * modes every CTA publishes its own completion word to the host instead;
  * descriptor k (0-based) uses slot k mod D of the relay ring, the partials
- * and the histogram accumulators, and its last CTA to arrive on
- * arrive[k mod D] (the one that also combines a sum or histogram) resets
+ * and the histogram-clear word, and its last CTA to arrive on
+ * arrive[k mod D] (the one that also combines a sum) resets
  * the counter and release-stores slot_done[k mod D] = k + 1, which gates the
  * slot's reuse by descriptor k + D. */
 typedef struct __attribute__((aligned(LK_LINE))) {
@@ -151,7 +151,8 @@ typedef struct __attribute__((aligned(LK_LINE))) {
   lk_line_counter arrive[LK_BCAST_DEPTH]; /* CTAs that finished the slot's descriptor   */
   uint64_t flag[LK_MAX_CTAS];            /* per-rank finished count (mailbox mode)      */
   lk_wire relay[LK_BCAST_DEPTH];         /* relay ring (lap-tagged like the host ring)  */
-  uint32_t hist[LK_BCAST_DEPTH][256];    /* histogram accumulators, zero at rest        */
+  uint64_t hzero[LK_BCAST_DEPTH];        /* seq whose histogram output rank 0 cleared   */
+  uint8_t pad2[LK_LINE - 8 * LK_BCAST_DEPTH];
   float partial[LK_BCAST_DEPTH][LK_MAX_CTAS]; /* per-rank partial sums                  */
 } lk_dcluster;
 
