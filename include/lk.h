@@ -223,8 +223,9 @@ int lk_init(lk_ctx** out, const lk_init_params* p);
  *   the descriptor reaches the device through the mailbox ring only.
  *   Outputs are written while the descriptor runs (a histogram's bins are
  *   cleared by the cluster's first CTA and accumulated by every CTA), so an
- *   output must not be read, nor written by another descriptor, until this
- *   one has finished.
+ *   output must not be read until the descriptor has finished.  Descriptors
+ *   posted to one cluster that write the same output leave the last one's
+ *   result when they have the same n (histograms: always).
  * On success *h names the descriptor.
  * Errors: LK_EINVAL (cluster, op, n_in, alignment, n too large),
  * LK_EAGAIN (ring full, or with LK_INIT_MAILBOX the mailbox not idle yet:

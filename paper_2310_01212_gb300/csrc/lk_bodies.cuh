@@ -562,11 +562,17 @@ __device__ __forceinline__ bool hist_warp_streams(const uint4* in, uint64_t beg,
  * (split parts, ordinary launches).  With `zero` set (a descriptor on a
  * cluster), rank 0 clears the output itself and release-stores `seq` into
  * *zero, and every CTA adds its counts straight into the output once it has
- * acquired that word: no combine, and no CTA waits for another at the end. */
+ * acquired that word: no combine, and no CTA waits for another at the end.
+ * Rank 0 clears only once the cluster's previous descriptor has finished on
+ * every CTA (*prev_done >= seq - 1; null when there is none, or the cluster
+ * runs one descriptor at a time), so a CTA still writing the same buffer
+ * for an earlier descriptor cannot land after the clear: the output ends as
+ * the last descriptor's result, as if the descriptors ran one by one. */
 struct HistSink {
   uint32_t* acc;
   uint64_t* zero;
   uint64_t seq;
+  const uint64_t* prev_done;
 };
 
 /* Thread 0 waits for rank 0's cleared output (with a sink that has one),
@@ -606,6 +612,10 @@ __device__ __forceinline__ bool body_hist(const lk_slot& d, int r, int S, unsign
     acc = reinterpret_cast<uint32_t*>(d.out);
     if (r == 0) {
       /* the counters' targets start at zero; the others add once they see it */
+      if (sink.prev_done && !hist_out_ready(HistSink{nullptr, const_cast<uint64_t*>(sink.prev_done), sink.seq - 1,
+                                                     nullptr},
+                                            pace.deadline))
+        return false;
       for (uint32_t v = threadIdx.x; v < 256; v += T) acc[v] = 0;
       __syncthreads();
       if (threadIdx.x == 0) st_release_gpu(sink.zero, sink.seq);

@@ -557,7 +557,7 @@ __device__ __forceinline__ int run_units(const lk_kargs& a, const lk_slot& d, in
       ok = body_sum<P, (MAXT <= 256 && P == 1)>(it, (int)part, (int)parts, dsm, bars, phase, deadline, red, pout);
     } else if (op == LK_OP_HIST_U8) {
       ok = body_hist<P>(it, (int)part, (int)parts, dsm, bars, phase, deadline,
-                        HistSink{parts > 1 ? s_pbins : my_hist, nullptr, 0});
+                        HistSink{parts > 1 ? s_pbins : my_hist, nullptr, 0, nullptr});
     } else {
       ok = run_body<MAXT, P>(it, (int)part, (int)parts, dsm, bars, phase, red, nullptr, HistSink{}, rate, gate,
                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0) == 0;
@@ -785,7 +785,9 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
     const int berr = (op == LK_OP_BATCH || op == LK_OP_SERVE)
                          ? run_units<MAXT, P>(a, d, c, r, dsm, s_bars, phase, s_red)
                          : run_body<MAXT, P>(d, r, S, dsm, s_bars, phase, s_red, &dc->partial[slot][r],
-                                             HistSink{nullptr, &dc->hzero[slot], d.seq},
+                                             HistSink{nullptr, &dc->hzero[slot], d.seq,
+                                                      k > 0 && !mailbox ? &dc->slot_done[(k - 1) % LK_BCAST_DEPTH]
+                                                                        : nullptr},
                                              cta_rate(d.aux, S), (d.flags & LK_DFLAG_YIELD) ? a.crit_active : nullptr,
                                              (a.flags & LK_KFLAG_GEMM_FFMA) == 0);
     if (berr && tid == 0) s_err = berr;
@@ -930,7 +932,7 @@ __global__ void __launch_bounds__(MAXT) lk_ordinary(const lk_slot d, lk_scratch*
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], HistSink{sc->hist, nullptr, 0}, 0, nullptr);
+  run_body<MAXT, 1>(d, r, S, dsm, s_bars, phase, s_red, &sc->partial[r], HistSink{sc->hist, nullptr, 0, nullptr}, 0, nullptr);
   if (op != LK_OP_SUM_F32 && op != LK_OP_HIST_U8) return;
   __syncthreads();
   if (threadIdx.x == 0) {

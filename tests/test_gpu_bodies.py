@@ -169,6 +169,31 @@ def test_gemm_ffma_flag(torch_ready, oracle_lib, S):
             assert np.all(np.abs(got - B) <= 2.0 ** -16 * np.abs(B))
 
 
+@pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX], ids=["relay", "direct", "mailbox"])
+def test_histograms_into_one_output_leave_the_last(torch_ready, oracle_lib, flags):
+    """Histogram descriptors posted back to back into one output (sizes from a
+    few KB to 16 MiB, so the CTAs of one run behind the next) leave exactly
+    the last one's bins: rank 0 clears the output only after the previous
+    descriptor finished everywhere."""
+    torch = torch_ready
+    sizes = [1 << 24, 4099, 1 << 20, 123_457, 1 << 24, 77, 3 << 20]
+    xs = [synth.bytes_uniform(17, i, n) for i, n in enumerate(sizes)]
+    dx = [to_dev(x) for x in xs]
+    out = torch.zeros(256, dtype=torch.int32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    with lk.lk_init([37], flags=flags, idle_lease_ns=5_000_000_000) as c:
+        for rep in range(3):
+            hs = []
+            for x, d in zip(xs, dx):
+                h = None
+                while h is None:   # the one-deep mailbox takes one descriptor at a time
+                    h = lk.lk_submit(c, 0, lk.LK_OP_HIST_U8, x.size, (d,), out)
+                hs.append(h)
+            for h in hs:
+                assert lk.lk_wait(c, h) == lk.LK_OK
+            assert np.array_equal(host(out).astype(np.int64), oracle_lib.hist_u8(xs[-1])), rep
+
+
 def test_gemm_row_blocks_bit_identical(torch_ready, oracle_lib):
     """On the FFMA path a tile's result does not depend on its split into row
     blocks: one tile on 1, 2, 3 and 8 CTAs (blocks of 64, 32, 16 and 8 rows,
