@@ -349,7 +349,8 @@ def build_headline(d: dict, hbm: float) -> dict:
                          "lk_vs_graph": [round(gcmp["lk_gbs"]), round(gcmp["graph_gbs"])]},
         "serving_saturation_gbs": {"device_queue": round(sat["throughput_gbs"]),
                                    "host_dispatcher": round(sat_h["throughput_gbs"]) if sat_h else None,
-                                   "host_coalesced": round(sat_c["throughput_gbs"]) if sat_c else None},
+                                   "host_coalesced": round(sat_c["throughput_gbs"]) if sat_c else None,
+                                   "device_queue_hbm_traffic_frac": round(sat["traffic_gbs"] / hbm, 3)},
         "serving_lowest_rate_us_p50_p99": [rnd1(low["latency_us"]["p50"]), rnd1(low["latency_us"]["p99"])],
         "parity": {"sampled_items_bad": d["parity"]["mismatches"],
                    "exec_log_violations": d["parity"]["exec_log"]["violations"],
@@ -954,18 +955,21 @@ def main():
             if rc != lk.LK_OK:
                 raise RuntimeError(f"serving ({where}) at {rate}/s failed: {lk.lk_strerror(rc)}")
             lat_s = (res["t_complete_ns"] - reqs["t_arrival_ns"]) / 1000.0
+            out_b = np.where(reqs["op"] == lk.LK_OP_ADD_I32, inb / 2, np.where(reqs["op"] == lk.LK_OP_GEMM64_F32,
+                                                                             inb / 2, 0.0))
             wait_s = (res["t_admit_ns"] - reqs["t_arrival_ns"]) / 1000.0
             span = float(res["t_complete_ns"].max()) / 1e9
             entry = {"requests": int(reqs.size), "latency_us": lat_summary(lat_s),
                      "admission_wait_us": lat_summary(wait_s),
                      "throughput_req_per_s": reqs.size / span,
                      "throughput_gbs": float(inb.sum()) / span / 1e9,
+                     # HBM traffic: the inputs plus the outputs (an add writes half its input
+                     # bytes, a GEMM tile 16 KB per 32 KB read; sums and histograms ~0)
+                     "traffic_gbs": float(inb.sum() + out_b.sum()) / span / 1e9,
                      "offered_gbs": float(inb.sum()) / (float(reqs["t_arrival_ns"].max()) / 1e9) / 1e9,
                      "units_or_chunks": int(res["chunks"].sum())}
             # the slowest requests, each against its own bytes at the measured HBM peak
             top = np.argsort(lat_s)[::-1][:5]
-            out_b = np.where(reqs["op"] == lk.LK_OP_ADD_I32, inb / 2, np.where(reqs["op"] == lk.LK_OP_GEMM64_F32,
-                                                                             inb / 2, 0.0))
             entry["slowest"] = [{"op": lk.OP_NAMES[int(reqs["op"][i])], "mb": rnd1((inb[i] + out_b[i]) / 1e6),
                                  "units": int(res["chunks"][i]), "us": rnd1(lat_s[i]), "admit_us": rnd1(wait_s[i]),
                                  "hbm_us": rnd1((inb[i] + out_b[i]) / (hbm_serv * 1e3))} for i in top]
