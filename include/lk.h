@@ -399,6 +399,16 @@ typedef struct {
  * split, so a request spreads over the CTAs that no queued unit waits for,
  * in units of at most f. */
 
+/* The rule above as a function: the units LK_SERVE_QUEUE gives a request of
+ * `op` (ADD, HIST, SUM, GEMM or COPY) over n elements (bytes, tiles) on a
+ * context of `ctas` CTAs, admitted while `backlog_units` units of
+ * `backlog_bytes` input bytes wait unclaimed; part_bytes and
+ * min_part_bytes as in lk_serve_params (0 -> the defaults).  Host-only:
+ * no device or context is touched.  Returns 0 for an op outside that set,
+ * ctas = 0 or parts sizes lk_serve would refuse. */
+uint32_t lk_serve_parts(uint32_t op, uint64_t n, uint32_t ctas, uint64_t backlog_units, uint64_t backlog_bytes,
+                        uint64_t part_bytes, uint64_t min_part_bytes);
+
 /* Device bytes the queue's state takes at the start of the arena
  * (LK_SERVE_QUEUE) for `max_inflight` request slots (0 -> 4096). */
 uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight);

@@ -1078,6 +1078,39 @@ static uint64_t queue_state_bytes(uint32_t nslots) {
   return align_up(sizeof(lk_qstate), 256) + align_up((uint64_t)nslots * sizeof(lk_qslot), 256);
 }
 
+/* The queue's split rule (see lk.h, lk_serve_parts): units of a request of
+ * op over n elements, given the context's CTAs and the backlog of admitted
+ * units no CTA has claimed yet (count and input bytes). */
+static uint32_t split_parts(uint32_t op, uint64_t n, uint64_t ctas, uint64_t backlog_units, uint64_t backlog_bytes,
+                            uint64_t part_bytes, uint64_t min_part) {
+  const uint64_t B = item_input_bytes(op, n);
+  const uint64_t fine_part = std::max<uint64_t>(min_part, part_bytes / 8);
+  auto ceil_parts = [&](uint64_t unit) {
+    return std::min<uint64_t>(std::max<uint64_t>(1, (B + unit - 1) / unit), LK_SERVE_MAX_PARTS);
+  };
+  const uint64_t base = ceil_parts(part_bytes);
+  uint64_t fine = ceil_parts(fine_part);
+  uint64_t wide = std::min<uint64_t>((B + min_part - 1) / min_part, LK_SERVE_MAX_PARTS);
+  if (op == LK_OP_GEMM64_F32) {   /* whole tiles */
+    fine = std::min<uint64_t>(fine, n);
+    wide = std::min<uint64_t>(wide, n);
+  }
+  /* a sum's float result depends on its split: a function of B and the CTAs alone */
+  if (op == LK_OP_SUM_F32) return (uint32_t)std::max(base, std::min(ctas, wide));
+  const uint64_t floor_parts = backlog_bytes >= ctas * part_bytes ? base : fine;   /* saturated? */
+  const uint64_t idle = backlog_units < ctas ? ctas - backlog_units : 0;
+  return (uint32_t)std::max(floor_parts, std::min(idle, wide));
+}
+
+extern "C" uint32_t lk_serve_parts(uint32_t op, uint64_t n, uint32_t ctas, uint64_t backlog_units,
+                                   uint64_t backlog_bytes, uint64_t part_bytes, uint64_t min_part_bytes) {
+  if (op < LK_OP_ADD_I32 || op > LK_OP_COPY_I32 || ctas == 0) return 0;
+  const uint64_t part = part_bytes ? part_bytes : (8ull << 20);
+  const uint64_t min_part = min_part_bytes ? min_part_bytes : (128ull << 10);
+  if (min_part < 65536 || part < min_part) return 0;
+  return split_parts(op, n, ctas, backlog_units, backlog_bytes, part, min_part);
+}
+
 extern "C" uint64_t lk_serve_queue_state_bytes(uint32_t max_inflight) {
   return queue_state_bytes(max_inflight ? max_inflight : 4096u);
 }
@@ -1095,8 +1128,6 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   const uint32_t nslots = p->max_inflight ? p->max_inflight : 4096u;
   const uint64_t part_bytes = p->part_bytes ? p->part_bytes : (8ull << 20);
   const uint64_t min_part = p->min_part_bytes ? p->min_part_bytes : (128ull << 10);
-  /* unit size floor of a non-sum request while the queue is not saturated */
-  const uint64_t fine_part = std::max<uint64_t>(min_part, part_bytes / 8);
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
   const int window = p->window > 0 ? p->window : 2;
   const uint64_t W = std::min<uint64_t>((uint64_t)window * (uint64_t)ctx->total, ctx->qn / 2);
@@ -1106,7 +1137,7 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   if (p->arena_bytes < sbytes) return LK_ENOMEM;
   struct QReq {
     uint64_t in_bytes = 0, out_bytes = 0, held = 0, out_off = 0;
-    uint32_t parts = 1, published = 0, slot = 0, base_parts = 1, fine_parts = 1, wide_parts = 1;
+    uint32_t parts = 1, published = 0, slot = 0;
     bool arena_out = false;
     void* out = nullptr;
   };
@@ -1124,19 +1155,8 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
                   : r.op == LK_OP_SUM_F32                        ? 16
                   : r.op == LK_OP_HIST_U8                        ? 1024
                                                                  : 16384 * r.n;
-    /* at least this many units; a sum gets exactly its fixed width now,
-     * other ops may spread wider at admission (split_wide) */
-    q.base_parts = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (q.in_bytes + part_bytes - 1) / part_bytes),
-                                                LK_SERVE_MAX_PARTS);
-    q.fine_parts = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (q.in_bytes + fine_part - 1) / fine_part),
-                                                LK_SERVE_MAX_PARTS);
-    q.wide_parts = (uint32_t)std::min<uint64_t>((q.in_bytes + min_part - 1) / min_part, LK_SERVE_MAX_PARTS);
-    if (r.op == LK_OP_GEMM64_F32) {   /* whole tiles */
-      q.fine_parts = (uint32_t)std::min<uint64_t>(q.fine_parts, r.n);
-      q.wide_parts = (uint32_t)std::min<uint64_t>(q.wide_parts, r.n);
-    }
-    q.parts = r.op == LK_OP_SUM_F32 ? std::max(q.base_parts, std::min<uint32_t>((uint32_t)ctx->total, q.wide_parts))
-                                    : q.base_parts;
+    /* a sum's unit count is fixed now; other ops are split at admission */
+    q.parts = split_parts(r.op, r.n, (uint64_t)ctx->total, 0, 0, part_bytes, min_part);
     q.arena_out = r.out == nullptr;
     q.held = q.in_bytes + q.out_bytes;
     if (q.held > p->budget_bytes || (q.arena_out && q.out_bytes + 256 > p->arena_bytes - sbytes)) return LK_ENOMEM;
@@ -1221,8 +1241,6 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   /* input bytes published through unit u, at u mod qn: the bytes of the
    * published units no CTA has claimed yet are cum(next_u) - cum(acked) */
   std::vector<uint64_t> cum(ctx->qn, 0);
-  /* saturated: the unclaimed backlog holds at least a part per CTA */
-  const uint64_t sat_bytes = (uint64_t)ctx->total * part_bytes;
   size_t finished = 0;
   int first_err = LK_OK;
   char* const out_base = (char*)p->arena + sbytes;
@@ -1272,9 +1290,8 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
         const uint64_t backlog = unpublished + (next_u - acked);
         const uint64_t claimed_bytes = acked ? cum[(acked - 1) & (ctx->qn - 1)] : 0;
         const uint64_t backlog_bytes = unpublished_bytes + (pub_bytes - claimed_bytes);
-        const uint32_t floor_parts = backlog_bytes >= sat_bytes ? q.base_parts : q.fine_parts;
-        const uint64_t idle = backlog < (uint64_t)ctx->total ? (uint64_t)ctx->total - backlog : 0;
-        q.parts = std::max<uint32_t>(floor_parts, (uint32_t)std::min<uint64_t>(idle, q.wide_parts));
+        q.parts = split_parts(reqs[i].op, reqs[i].n, (uint64_t)ctx->total, backlog, backlog_bytes, part_bytes,
+                              min_part);
       }
       unpublished += q.parts;
       unpublished_bytes += q.in_bytes;

@@ -137,6 +137,7 @@ def load(fake: bool = False, bounds: bool = False) -> ctypes.CDLL:
             "lk_heartbeat": (I, [P]),
             "lk_set_rate": (I, [P, I, U64]),
             "lk_set_role": (I, [P, I, I]),
+            "lk_serve_parts": (ctypes.c_uint32, [ctypes.c_uint32, U64, ctypes.c_uint32, U64, U64, U64, U64]),
             "lk_dispose": (I, [P, U64]),
             "lk_dispose_timed": (I, [P, U64, ctypes.POINTER(ctypes.c_float)]),
             "lk_cluster_info": (I, [P, I, ctypes.POINTER(I), I]),
@@ -566,3 +567,13 @@ def lk_baseline_phase_run(sms: int, iters: int, runs: int, threads: int = 256, o
     if rc != LK_OK:
         raise LkError(rc, "lk_baseline_phase_run")
     return res
+
+
+def lk_serve_parts(op: int, n: int, ctas: int, backlog_units: int = 0, backlog_bytes: int = 0,
+                   part_bytes: int = 0, min_part_bytes: int = 0) -> int:
+    """Units the device queue gives a request (the split rule of include/lk.h); 0 if refused."""
+    try:
+        lib = load()
+    except OSError:
+        lib = load(True)
+    return int(lib.lk_serve_parts(op, n, ctas, backlog_units, backlog_bytes, part_bytes, min_part_bytes))

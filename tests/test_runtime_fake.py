@@ -742,6 +742,33 @@ def test_queue_serves_every_request_with_its_units(fake_env):
         assert lk.lk_wait(c, lk.lk_submit(c, 1, lk.LK_OP_NOP, 0)) == lk.LK_OK
 
 
+def test_serve_parts_rule():
+    """The exported split rule, host-only, at the defaults (8 MiB parts, 128 KiB
+    minimum, so 1 MiB units while not saturated) on 148 CTAs."""
+    MiB = 1 << 20
+    P = lk.lk_serve_parts
+    # add of 512 MiB input: 1 MiB units unless the backlog saturates the queue
+    assert P(lk.LK_OP_ADD_I32, 64 * MiB, 148) == 512
+    assert P(lk.LK_OP_ADD_I32, 64 * MiB, 148, 10, 148 * 8 * MiB) == 138        # saturated: max(64, 138 idle)
+    assert P(lk.LK_OP_ADD_I32, 64 * MiB, 148, 500, 148 * 8 * MiB) == 64        # and no idle CTA
+    assert P(lk.LK_OP_ADD_I32, 64 * MiB, 148, 500, 148 * 8 * MiB - 1) == 512   # just below saturation
+    # a sum's width ignores the backlog: max(ceil(B / 8 MiB), min(148, ceil(B / 128 KiB)))
+    for bu, bb in ((0, 0), (500, 1 << 40)):
+        assert P(lk.LK_OP_SUM_F32, 1 << 20, 148, bu, bb) == 32
+        assert P(lk.LK_OP_SUM_F32, 1 << 26, 148, bu, bb) == 148
+        assert P(lk.LK_OP_SUM_F32, 1 << 30, 148, bu, bb) == 512
+    # a 1 MiB histogram behind 200 queued units: one unit
+    assert P(lk.LK_OP_HIST_U8, MiB, 148, 200, 0) == 1
+    # GEMM: whole tiles
+    assert P(lk.LK_OP_GEMM64_F32, 3, 148) == 1
+    assert P(lk.LK_OP_GEMM64_F32, 1000, 148) == 148
+    assert P(lk.LK_OP_GEMM64_F32, 1000, 148, 140, 0) == 32
+    # refused
+    for args in ((lk.LK_OP_NOP, 1, 148), (lk.LK_OP_SPIN, 1, 148), (lk.LK_OP_ADD_I32, 1, 0)):
+        assert P(*args) == 0
+    assert P(lk.LK_OP_ADD_I32, 1, 148, 0, 0, 8 * MiB, 1000) == 0
+
+
 def test_queue_split_rule(fake_env):
     """A sum gets exactly max(ceil(B / part), min(CTAs, ceil(B / min_part)))
     units, whatever else runs; another op spreads over the CTAs no unclaimed
@@ -760,6 +787,8 @@ def test_queue_split_rule(fake_env):
         # most 512 KiB (part / 8): max(72, min(6, 576)) = 72
         # hist 1 MiB -> 6; gemm 3 tiles (96 KiB) -> min(6, 2, 3 tiles) = 2
         assert got == [1, 6, 9, 6, 72, 6, 2], got
+        # lk_serve_parts states the same rule
+        assert got == [lk.lk_serve_parts(o, n, 6, 0, 0, 4 << 20, 64 << 10) for o, n in zip(ops, ns)]
 
 
 def test_queue_serves_twice_and_empty(fake_env):
