@@ -100,6 +100,10 @@ def test_each_result_same_alone_and_in_the_mix(served):
             # spreads other ops over idle CTAs, which cannot change them
             if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32 or kw["mode"] == lk.LK_SERVE_CHUNKS:
                 assert r1["chunks"][0] == res["chunks"][i]
+            if kw["mode"] == lk.LK_SERVE_QUEUE:
+                # alone, nothing is queued: the split is the rule's with no backlog
+                assert r1["chunks"][0] == lk.lk_serve_parts(int(reqs[i]["op"]), int(reqs[i]["n"]), 32, 0, 0,
+                                                            kw["part_bytes"], 0)
             a, m = host(alone_out), host(outs[i])
             if int(reqs[i]["op"]) == lk.LK_OP_SUM_F32:
                 a, m = a[:1], m[:1]   # the result; the rest of the 16-byte slot is padding
