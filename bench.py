@@ -388,9 +388,15 @@ def e2e_parts(res) -> dict:
     cout = (res["t_complete_ns"].astype(np.int64) - res["t_observed_ns"].astype(np.int64)) / 1000.0
     tot = (res["t_complete_ns"].astype(np.int64) - res["t_submit_ns"].astype(np.int64)) / 1000.0
     top = np.argsort(tot)[::-1][: max(1, tot.size // 100)]   # the slowest 1 %: where their time went
+    # when the slow copies happen: submit time (ms into the trace) and worker
+    # thread of the 12 slowest copies, to tell a periodic host event from a
+    # steady rate
+    slow = np.argsort(np.maximum(cin, cout))[::-1][:12]
     return {"copy_in": lat_summary(cin), "dispatch": lat_summary(dis), "copy_out": lat_summary(cout),
             "slowest_1pct_mean": {"copy_in": float(np.mean(cin[top])), "dispatch": float(np.mean(dis[top])),
-                                  "copy_out": float(np.mean(cout[top]))}}
+                                  "copy_out": float(np.mean(cout[top]))},
+            "slowest_copies": [[round(float(res["t_submit_ns"][i]) / 1e6, 3), int(res["thread"][i]),
+                                round(float(cin[i]), 1), round(float(cout[i]), 1)] for i in slow]}
 
 
 def exec_log_phases(log) -> dict:
