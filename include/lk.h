@@ -380,7 +380,8 @@ typedef struct {
   uint32_t mode;              /* LK_SERVE_CHUNKS or LK_SERVE_QUEUE                  */
   uint32_t max_inflight;      /* QUEUE: admitted, unfinished requests at most;     */
                               /* 0 -> 4096                                        */
-  uint64_t part_bytes;        /* QUEUE: largest unit (input bytes); 0 -> 8 MiB     */
+  uint64_t part_bytes;        /* QUEUE: largest unit (input bytes); 0 -> 8 MiB;    */
+                              /* at most 2^40                                      */
   uint64_t min_part_bytes;    /* QUEUE: smallest unit when a request is spread      */
                               /* wider; 0 -> 128 KiB; 64 KiB <= it <= part_bytes   */
 } lk_serve_params;
@@ -405,7 +406,8 @@ typedef struct {
  * `backlog_bytes` input bytes wait unclaimed; part_bytes and
  * min_part_bytes as in lk_serve_params (0 -> the defaults).  Host-only:
  * no device or context is touched.  Returns 0 for an op outside that set,
- * ctas = 0 or parts sizes lk_serve would refuse. */
+ * ctas = 0 or parts sizes lk_serve would refuse (min_part_bytes below
+ * 64 KiB or above part_bytes, part_bytes above 2^40). */
 uint32_t lk_serve_parts(uint32_t op, uint64_t n, uint32_t ctas, uint64_t backlog_units, uint64_t backlog_bytes,
                         uint64_t part_bytes, uint64_t min_part_bytes);
 

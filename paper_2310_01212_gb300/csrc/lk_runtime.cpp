@@ -1107,7 +1107,7 @@ extern "C" uint32_t lk_serve_parts(uint32_t op, uint64_t n, uint32_t ctas, uint6
   if (op < LK_OP_ADD_I32 || op > LK_OP_COPY_I32 || ctas == 0) return 0;
   const uint64_t part = part_bytes ? part_bytes : (8ull << 20);
   const uint64_t min_part = min_part_bytes ? min_part_bytes : (128ull << 10);
-  if (min_part < 65536 || part < min_part) return 0;
+  if (min_part < 65536 || part < min_part || part > (1ull << 40)) return 0;
   return split_parts(op, n, ctas, backlog_units, backlog_bytes, part, min_part);
 }
 
@@ -1131,7 +1131,8 @@ static int serve_queue(lk_ctx* ctx, const lk_request* reqs, size_t count, const 
   const uint64_t timeout = p->timeout_ns ? p->timeout_ns : 120000000000ull;
   const int window = p->window > 0 ? p->window : 2;
   const uint64_t W = std::min<uint64_t>((uint64_t)window * (uint64_t)ctx->total, ctx->qn / 2);
-  if (nslots > ctx->qn || min_part < 65536 || part_bytes < min_part || ((uintptr_t)p->arena & 255u) || !p->arena)
+  if (nslots > ctx->qn || min_part < 65536 || part_bytes < min_part || part_bytes > (1ull << 40) ||
+      ((uintptr_t)p->arena & 255u) || !p->arena)
     return LK_EINVAL;
   const uint64_t sbytes = queue_state_bytes(nslots);
   if (p->arena_bytes < sbytes) return LK_ENOMEM;

@@ -767,6 +767,7 @@ def test_serve_parts_rule():
     for args in ((lk.LK_OP_NOP, 1, 148), (lk.LK_OP_SPIN, 1, 148), (lk.LK_OP_ADD_I32, 1, 0)):
         assert P(*args) == 0
     assert P(lk.LK_OP_ADD_I32, 1, 148, 0, 0, 8 * MiB, 1000) == 0
+    assert P(lk.LK_OP_ADD_I32, 1, 148, 0, 0, (1 << 40) + 1, 0) == 0
 
 
 def test_queue_split_rule(fake_env):
