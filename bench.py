@@ -597,7 +597,8 @@ def main():
     ap.add_argument("--impl", default="lk", choices=["lk", "reference"])
     ap.add_argument("--items", type=int, default=ITEMS_PER_STEP)
     ap.add_argument("--iso-periods", type=int, default=60_000,
-                    help="critical periods (1 ms each) of the disjoint-layout isolation run, alone and loaded")
+                    help="critical periods (1 ms each) of the disjoint-layout isolation run: alone, loaded, "
+                         "and loaded with the best effort yielding")
     ap.add_argument("--iso-sweep-periods", type=int, default=2000,
                     help="critical periods of each co-resident and rate-capped isolation run")
     ap.add_argument("--batch-items", type=int, default=1_000_000,
@@ -1061,8 +1062,9 @@ def main():
                                "load_covered_critical_run": pr["load_covered_critical_run"]}
     # load yielding: the best-effort cluster holds its loads while a critical
     # descriptor runs (lk_set_role), instead of a standing cap
-    yr = iso_run({"sizes": iso["sizes"]}, args.iso_sweep_periods, alone=False, roles=True)
-    iso_res["best_effort_yield"] = {"loaded_us": yr["loaded_us"], "best_effort_gbs": yr["best_effort_gbs"],
+    yr = iso_run({"sizes": iso["sizes"]}, args.iso_periods, alone=False, roles=True)
+    iso_res["best_effort_yield"] = {"periods": yr["periods"], "loaded_us": yr["loaded_us"],
+                                    "best_effort_gbs": yr["best_effort_gbs"],
                                     "inflation_p999": yr["loaded_us"]["p999"] / iso_res["alone_us"]["p999"],
                                     "load_covered_critical_run": yr["load_covered_critical_run"]}
     iso_res["inflation_p999"] = iso_res["loaded_us"]["p999"] / iso_res["alone_us"]["p999"]
