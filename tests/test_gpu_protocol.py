@@ -85,8 +85,9 @@ def test_explicit_smid_lists(torch_ready, oracle_lib):
             assert r["smid"] == lists[r["cluster"]][r["rank"]]
 
 
+@pytest.mark.parametrize("roles", [False, True], ids=["no_roles", "critical_and_yield"])
 @pytest.mark.parametrize("flags", [0, lk.LK_INIT_DIRECT, lk.LK_INIT_MAILBOX])
-def test_many_producers_mixed_bodies(torch_ready, oracle_lib, flags):
+def test_many_producers_mixed_bodies(torch_ready, oracle_lib, flags, roles):
     torch = torch_ready
     sizes = [8, 8, 8, 8]
     n = 65536
@@ -102,6 +103,11 @@ def test_many_producers_mixed_bodies(torch_ready, oracle_lib, flags):
     posted = {}
     lock = threading.Lock()
     with lk.lk_init(sizes, exec_log_cap=1024, idle_lease_ns=5_000_000_000, flags=flags) as c:
+        if roles:   # the role bits ride on every descriptor; the protocol and results stay the same
+            lk.lk_set_role(c, 0, lk.LK_ROLE_CRITICAL)
+            for k in (1, 2, 3):
+                lk.lk_set_role(c, k, lk.LK_ROLE_YIELD)
+
         def producer(p):
             for j in range(J):
                 cl = (p + j) % 4
