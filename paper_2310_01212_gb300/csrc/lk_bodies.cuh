@@ -1156,8 +1156,11 @@ __device__ __forceinline__ bool body_gemm(const lk_slot& d, int r, int S, float*
                                           uint32_t& phase, Pace pace, bool tensor_cores) {
   const uint64_t tiles = d.n;
   const uint32_t U = gemm_row_split(tiles, S);
-  if (P == 1 && tensor_cores && U == 1 && blockDim.x == 256)
-    return body_gemm_tc(d, r, S, reinterpret_cast<unsigned char*>(sm), bars, phase, pace);
+  /* FULL_UNROLL holds only in the kernels built for 256 threads and one CTA
+   * per SM, the only ones that can take the tensor-core path */
+  if constexpr (FULL_UNROLL)
+    if (P == 1 && tensor_cores && U == 1 && blockDim.x == 256)
+      return body_gemm_tc(d, r, S, reinterpret_cast<unsigned char*>(sm), bars, phase, pace);
   const uint32_t rows = 64 / U;
   uint64_t beg, end;
   share(tiles * U, r, S, beg, end);
