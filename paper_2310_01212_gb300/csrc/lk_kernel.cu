@@ -718,10 +718,10 @@ __device__ __forceinline__ void persistent_main(const lk_kargs& a) {
       lk_slot& dsc = s_desc;   /* written in place: no copy through local memory */
       const lk_wire* w = ring + (k & a.ring_mask);
       const uint64_t tag = lk_lap_tag(k, a.ring_log2);
-      /* slot k mod D (relay copy, partials, histogram accumulator, arrival
+      /* slot k mod D (relay copy, partials, histogram-clear word, arrival
        * counter) is free once descriptor k+1-D, its previous user, finished */
       const uint64_t need = k + 1 > LK_BCAST_DEPTH ? k + 1 - LK_BCAST_DEPTH : 0;
-      s_slot_seen = 0;   /* shared, not local: the probe functions are out of line */
+      s_slot_seen = 0;   /* shared, not local: the take functions write it through a pointer */
       if (master && mailbox) {
         err = take_from_mailbox(a, c, k, dsc);
         s_slot_seen = known_done;   /* the mailbox master completes each descriptor itself */

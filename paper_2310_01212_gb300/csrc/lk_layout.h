@@ -21,7 +21,7 @@
  *   dcl[c]          relay ring (D slots), generation, per-slot completion
  *                   words and arrival counters, per-rank finished counts
  *                   (one-deep mailbox mode), per-rank partial sums,
- *                   histogram accumulators.
+ *                   histogram-clear words.
  *   log[g][cap]     execution-log records (lk_exec_rec) of CTA g.
  */
 #ifndef LK_LAYOUT_H
